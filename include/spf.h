@@ -1,0 +1,212 @@
+/*
+ * spf.h -- C ABI of the GB300 M-TIP slice / match / merge library.
+ *
+ * The library computes the data-parallel path of the Cartesian-NUFFT M-TIP
+ * reconstruction (arXiv 2109.05339, Sec. II): slicing a 3D model with a
+ * type-2 NUFFT (Sec. II-A), matching every experimental image to its nearest
+ * model image (Sec. II-B), and merging the oriented images through the
+ * Tikhonov normal equations of Eq. 2 solved by conjugate gradient on the
+ * Toeplitz form of A*DA (Sec. II-C).
+ *
+ * Conventions shared by every call
+ *   - Model grid: N odd, modes n in {-M..M}^3, M = (N-1)/2, stored as float
+ *     [n_z+M][n_y+M][n_x+M] (x fastest), N^3 values.
+ *   - q-points: the NUFFT coordinate of a physical q is t = 2 pi dr q with
+ *     dr = 1/(N dq), dq = qmax/M, so grid point q = m dq has t = 2 pi m / N.
+ *   - Quaternions: 4 floats (w, x, y, z) per orientation, unit norm, active
+ *     rotation; a detector point q_lab[p] is rotated to R(quat) q_lab[p].
+ *   - q_lab: 3 floats (x, y, z) per detector pixel, P2 pixels.
+ *   - Images / slices: row-major [orientation or image][pixel], float.
+ *   - Every array pointer is a DEVICE pointer owned by the caller unless the
+ *     argument says "host". The library never frees caller memory.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) unless it says otherwise, and returns an int
+ *     status: SPF_OK or a negative SPF_ERR_* code. spf_last_error_string()
+ *     gives a message for the last failure on the calling thread.
+ *   - A plan or matcher is used by one stream at a time and is not thread
+ *     safe; after any error it stays usable.
+ *   - No call allocates device memory except the *_create functions.
+ */
+#ifndef SPF_H
+#define SPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPF_OK 0
+#define SPF_ERR_ARG (-1)         /* bad argument (size, pointer, limit)          */
+#define SPF_ERR_OOM (-2)         /* device allocation failed at create           */
+#define SPF_ERR_CUDA (-3)        /* a CUDA runtime call or launch failed         */
+#define SPF_ERR_TIMEOUT (-4)     /* a bounded device wait gave up                */
+#define SPF_ERR_UNSUPPORTED (-5) /* option not built for this device             */
+
+#define SPF_FP32 0 /* cross term in FP32 on the CUDA cores                      */
+#define SPF_BF16 1 /* cross term in BF16 on the tensor cores, FP32 accumulate  */
+#define SPF_FP8 2  /* cross term in FP8 e4m3 with per-row scales, FP32 acc.   */
+
+#define SPF_MAX_TOPK 8
+
+typedef struct spf_plan spf_plan;
+typedef struct spf_matcher spf_matcher;
+
+/* Message for the last failing call on this thread ("" if none). Host. */
+const char* spf_last_error_string(void);
+
+/* Library ABI version (increments on any signature change). Host. */
+int spf_version(void);
+
+/* ---------------------------------------------------------------------------
+ * NUFFT plan (Sec. II-A and II-C: type-2 slicing, type-1 merging).
+ *
+ * N         model grid side (odd, 3..1023).
+ * qmax      largest |q| of the model grid (> 0).
+ * eps       NUFFT tolerance (1e-7 .. 1e-2); sets the exponential-of-semicircle
+ *           kernel width w = ceil(log10(1/eps)) + 1 and shape beta = 2.3 w,
+ *           with upsampling 2.
+ * max_points  the most nonuniform points one call may pass (images x pixels,
+ *           or orientations x pixels); sizes the sort buffers of type-1 calls.
+ * device    CUDA device ordinal; the plan allocates its scratch there.
+ * Allocates the fine grids (n_f^3 for N modes, n_fT^3 for the 2N-1 modes of
+ * the Toeplitz kernel, P_T^3 for the circulant embedding), sort buffers of
+ * 4 * max_points bytes, and the CG vectors. Synchronous. *out owns them.
+ * ------------------------------------------------------------------------- */
+int spf_plan_create(spf_plan** out, int N, double qmax, double eps, int64_t max_points,
+                    int device);
+int spf_plan_destroy(spf_plan* plan);
+
+/* Device-side error word of the plan (bounds checks inside kernels): waits
+ * for the device (cudaDeviceSynchronize on the plan's device), returns SPF_OK
+ * or SPF_ERR_ARG if a kernel found an inconsistent point, then clears it. */
+int spf_plan_status(spf_plan* plan);
+
+/* Sizes chosen by the plan (host): fine grid n_f, Toeplitz fine grid n_fT,
+ * embedding P_T, kernel width w. Any pointer may be NULL. */
+int spf_plan_sizes(const spf_plan* plan, int* nf, int* nfT, int* PT, int* w);
+
+/* Slicing, Sec. II-A: the type-2 NUFFT of the model at rotated detector points.
+ *   slices[j*P2 + p] = Re sum_n A[n] exp(-i n . t_jp),
+ *   t_jp = 2 pi dr R(quats[j]) q_lab[p],   j < M, p < P2.
+ * A: N^3 floats (only its even part contributes to the real part).
+ * quats: M x 4, q_lab: P2 x 3, slices: M x P2 (written). M*P2 < 2^32. */
+int spf_slice_model(spf_plan* plan, const float* A, const float* quats, int M,
+                    const float* q_lab, int P2, float* slices, void* stream);
+
+/* Adjoint of spf_slice_model (Sec. II-C type 1), the backward of slicing:
+ *   gradA[n] (+)= Re sum_{j,p} g[j*P2 + p] exp(+i n . t_jp).
+ * accumulate = 0 overwrites gradA, 1 adds to it. M*P2 <= max_points. */
+int spf_slice_adjoint(spf_plan* plan, const float* g, const float* quats, int M,
+                      const float* q_lab, int P2, float* gradA, int accumulate,
+                      void* stream);
+
+/* Type-2 / type-1 at explicit points t (npts x 3 floats, radians, any real
+ * value; taken mod 2 pi). type2: out[j] = Re sum_n A[n] exp(-i n.t_j).
+ * type1: out[n] (+)= Re sum_j v[j] exp(+i n.t_j), npts <= max_points. */
+int spf_nufft_type2(spf_plan* plan, const float* A, const float* pts, int64_t npts,
+                    float* out, void* stream);
+int spf_nufft_type1(spf_plan* plan, const float* v, const float* pts, int64_t npts,
+                    float* out, int accumulate, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Merge, Sec. II-C (Eq. 2 with the Toeplitz method): from one chunk of
+ * oriented images build
+ *   rhs[n]        (+)= Re sum_{i,p} D[p] b_scale images[i*P2+p] exp(+i n.t_ip)
+ *   kernel_hat[k] (+)= FFT_{P_T}( embed K )[k],
+ *        K(d) = Re sum_{i,p} D[p] exp(+i d.t_ip),  d in {-(N-1)..N-1}^3,
+ * t_ip from the orientation of image i and q_lab[p]: quats[orient_idx[i]] when
+ * orient_idx (n_img int32, e.g. the matcher's best indices) is given, else
+ * quats[i]; quats holds n_quats rows. An index outside [0, n_quats) sets the
+ * plan's error word (spf_plan_status) and is clamped.
+ * K is embedded circulantly in P_T^3 (P_T = smallest even 2/3/5-smooth
+ * >= 2N-1); kernel_hat is real, P_T^3 floats, layout [z][y][x].
+ * D: P2 per-pixel weights (1 valid, 0 masked) or NULL for all ones.
+ * Linear in the images: chunks are summed with accumulate = 1 (the paper's
+ * per-node type-1 NUFFTs followed by a sum reduction).
+ * n_img*P2 <= max_points. */
+int spf_merge_images(spf_plan* plan, const float* images, const float* quats, int n_quats,
+                     const int32_t* orient_idx, int n_img, const float* q_lab, int P2,
+                     const float* D, float b_scale, float* rhs, float* kernel_hat, int accumulate,
+                     void* stream);
+
+/* Conjugate gradient on H x = rhs + lambda x0, H = Re(A^H D A) + lambda I
+ * applied as crop(IFFT(kernel_hat * FFT(pad x))) + lambda x (Eq. 2, Sec. II-C).
+ * spf_cg_begin: x = x0, r = rhs + lambda x0 - H x0, p = r (state in the plan).
+ * spf_cg_merge_step: one CG iteration updating x in place. The step length
+ * and direction update are computed on the device from FP64 inner products;
+ * no host synchronisation. res_norm (device, may be NULL) receives |r| after
+ * the step as a double. x, rhs, x0: N^3 floats; kernel_hat: P_T^3 floats. */
+int spf_cg_begin(spf_plan* plan, const float* kernel_hat, double lambda, const float* rhs,
+                 const float* x0, float* x, double* res_norm, void* stream);
+int spf_cg_merge_step(spf_plan* plan, const float* kernel_hat, double lambda, float* x,
+                      double* res_norm, void* stream);
+
+/* H x without the CG state (Toeplitz form): out = crop(IFFT(kernel_hat *
+ * FFT(pad x))) + lambda x. Used to check the operator. */
+int spf_toeplitz_apply(spf_plan* plan, const float* kernel_hat, double lambda,
+                       const float* x, float* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Orientation matching, Sec. II-B: for every image the model image nearest in
+ * Euclidean distance d_ij = |x_i|^2 + |y_j|^2 - 2 x_i . y_j (x_i = img_scale *
+ * image i). The cross term runs in `precision`; the best `topk` candidates per
+ * image are then re-ranked with exact FP32 distances sum_p (x_ip - y_jp)^2,
+ * so the returned argmin and distances are FP32-exact over the candidates.
+ * Ties go to the lower orientation index. Model images can be streamed in
+ * chunks: orient_offset is added to the indices of each chunk, and the
+ * running best-topk list per image survives across calls.
+ *
+ * spf_matcher_create: max_images, max_orient_chunk bound later calls; P2 is
+ *   fixed; precision SPF_FP32 / SPF_BF16 / SPF_FP8; 2 <= topk <= 8.
+ *   Allocates quantised copies and candidate buffers. Synchronous.
+ * spf_matcher_set_images: computes norms and quantised copies of the images
+ *   and resets the running lists. images: n_img x P2 floats; the matcher keeps
+ *   the pointer, which must stay valid until the last add_slices.
+ * spf_matcher_add_slices: matches one chunk of n_orient model images
+ *   (n_orient x P2 floats, valid until the call's work completes).
+ * spf_matcher_results: best_idx, best_d, second_d: n_img each (may be NULL);
+ *   topk_idx, topk_d: n_img x topk (may be NULL). Distances are in the units
+ *   of img_scale * images.
+ * ------------------------------------------------------------------------- */
+int spf_matcher_create(spf_matcher** out, int max_images, int max_orient_chunk, int P2,
+                       int precision, int topk, int device);
+int spf_matcher_destroy(spf_matcher* m);
+/* Device-side error word of the matcher: waits for the device, returns SPF_OK,
+ * SPF_ERR_TIMEOUT (a bounded pipeline wait in a tensor-core kernel gave up;
+ * its results are not valid) or SPF_ERR_CUDA (tensor memory could not be
+ * allocated), then clears it. */
+int spf_matcher_status(spf_matcher* m);
+int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float img_scale,
+                           void* stream);
+int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient,
+                           int orient_offset, void* stream);
+int spf_matcher_results(spf_matcher* m, int32_t* best_idx, float* best_d, float* second_d,
+                        int32_t* topk_idx, float* topk_d, void* stream);
+
+/* One-shot Sec. II-B matching of n_img images against n_orient model images
+ * with the matcher's buffers: set_images, add_slices (offset 0), results.
+ * best_idx, best_d, second_d: n_img each (device). */
+int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float img_scale,
+                           const float* slices, int n_orient, int32_t* best_idx,
+                           float* best_d, float* second_d, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Tracing (no counterpart in the paper; it backs the per-stage timings of
+ * its Fig. 5 style breakdown). Host calls.
+ * spf_profile_enable(1) clears the counters and starts recording a CUDA event
+ *   pair around every kernel launch on the launching stream; 0 stops.
+ * spf_profile_read: for kernel number `index` (0 ..), its name (copied into
+ *   name[0..name_len-1]), launches and summed device milliseconds since the
+ *   last enable. Waits for the recorded events. SPF_ERR_ARG past the last.
+ * spf_launch_count: kernels launched by this library since the process began.
+ * ------------------------------------------------------------------------- */
+int spf_profile_enable(int on);
+int spf_profile_read(int index, char* name, int name_len, long long* launches, double* total_ms);
+long long spf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPF_H */

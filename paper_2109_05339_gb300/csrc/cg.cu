@@ -1,0 +1,194 @@
+// Toeplitz normal operator and conjugate gradient (Sec. II-C, Eq. 2).
+//
+// H x = crop(IFFT(K^ * FFT(pad x))) / P_T^3 + lambda x, with K^ the FFT of
+// the circulant embedding of the "type-1 with ones" kernel. The FFT of the
+// zero-padded vector skips the lines that stay zero, the multiply by K^ is
+// fused into the last forward pass, and the inverse skips lines that cannot
+// reach the cropped N^3 output. Inner products and residual norms are
+// accumulated in FP64 (per-block partials reduced in a fixed order, so the
+// result is deterministic); alpha and beta are computed on the device and
+// never read by the host.
+#include <cmath>
+
+#include "plan.h"
+
+namespace spf {
+
+namespace {
+
+constexpr int kRedBlocks = 296;   // fixed grid for deterministic reductions
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__device__ double block_sum(double v) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
+}
+
+// cube (PT^3 complex) = x at n mod PT (|n| <= Mh), zero elsewhere.
+__global__ void pad_kernel(const float* __restrict__ x, int N, int PT, float2* __restrict__ cube) {
+  int64_t total = (int64_t)PT * PT * PT;
+  int Mh = (N - 1) / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(i % PT), b = (int)((i / PT) % PT), c = (int)(i / ((int64_t)PT * PT));
+    int kx = a <= Mh ? a : a - PT, ky = b <= Mh ? b : b - PT, kz = c <= Mh ? c : c - PT;
+    float v = 0.f;
+    if (kx >= -Mh && kx <= Mh && ky >= -Mh && ky <= Mh && kz >= -Mh && kz <= Mh)
+      v = x[((kz + Mh) * N + (ky + Mh)) * N + (kx + Mh)];
+    cube[i] = make_float2(v, 0.f);
+  }
+}
+
+// out = Re(cube[n mod PT]) / PT^3 + lambda x; partial sums of x . out.
+__global__ void crop_apply_kernel(const float2* __restrict__ cube, int N, int PT, float inv_n,
+                                  float lambda, const float* __restrict__ x, float* __restrict__ out,
+                                  double* __restrict__ part) {
+  int64_t n3 = (int64_t)N * N * N;
+  int Mh = (N - 1) / 2;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(i % N), b = (int)((i / N) % N), c = (int)(i / ((int64_t)N * N));
+    int gx = wrapi(a - Mh, PT), gy = wrapi(b - Mh, PT), gz = wrapi(c - Mh, PT);
+    float v = cube[((size_t)gz * PT + gy) * PT + gx].x * inv_n + lambda * x[i];
+    out[i] = v;
+    acc += (double)x[i] * (double)v;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
+}
+
+// x = x0; r = rhs + lambda x0 - Hx0; p = r; partial |r|^2.
+__global__ void cg_init_kernel(const float* __restrict__ rhs, const float* __restrict__ x0,
+                               const float* __restrict__ Hx0, float lambda, int64_t n,
+                               float* __restrict__ x, float* __restrict__ r, float* __restrict__ p,
+                               double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float xv = x0[i];
+    float rv = rhs[i] + lambda * xv - Hx0[i];
+    x[i] = xv;
+    r[i] = rv;
+    p[i] = rv;
+    acc += (double)rv * (double)rv;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// sc = [rr, pAp, alpha, beta, rr_new, res]
+// mode 0: rr = sum; mode 1: pAp = sum, alpha = rr / pAp;
+// mode 2: rr_new = sum, beta = rr_new / rr, rr = rr_new. res = sqrt(rr).
+__global__ void finalize_kernel(const double* __restrict__ part, int nparts, double* __restrict__ sc,
+                                int mode, double* __restrict__ res_out) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
+  double s = block_sum(v);
+  if (threadIdx.x == 0) {
+    if (mode == 0) {
+      sc[0] = s;
+    } else if (mode == 1) {
+      sc[1] = s;
+      sc[2] = s > 0.0 ? sc[0] / s : 0.0;
+    } else {
+      sc[4] = s;
+      sc[3] = sc[0] > 0.0 ? s / sc[0] : 0.0;
+      sc[0] = s;
+    }
+    sc[5] = sqrt(sc[0]);
+    if (res_out) *res_out = sc[5];
+  }
+}
+
+// x += alpha p; r -= alpha Ap; partial |r|^2.
+__global__ void cg_update_kernel(float* __restrict__ x, float* __restrict__ r,
+                                 const float* __restrict__ p, const float* __restrict__ Ap,
+                                 const double* __restrict__ sc, int64_t n, double* __restrict__ part) {
+  const float alpha = (float)sc[2];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fmaf(alpha, p[i], x[i]);
+    float rv = fmaf(-alpha, Ap[i], r[i]);
+    r[i] = rv;
+    acc += (double)rv * (double)rv;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// p = r + beta p
+__global__ void cg_dir_kernel(const float* __restrict__ r, float* __restrict__ p,
+                              const double* __restrict__ sc, int64_t n) {
+  const float beta = (float)sc[3];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(beta, p[i], r[i]);
+}
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>(ceil_div(n, 256), 152 * 32); }
+
+}  // namespace
+
+// out = H x, and (optionally) per-block partials of x . out.
+int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x, float* out,
+                   double* part, cudaStream_t s) {
+  const int N = P->N, PT = P->PT;
+  int64_t PT3 = (int64_t)PT * PT * PT;
+  SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for(PT3), 256, 0, s>>>(x, N, PT, P->cubeP); }));
+  SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, nullptr, khat, -1, P->Mh + 1, 0, s));
+  SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, nullptr, nullptr, +1, 0, P->Mh + 1, s));
+  SPF_TRY(launch("crop_apply_kernel", s, [&] { crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3),
+                                                       (float)lambda, x, out, part); }));
+  return SPF_OK;
+}
+
+int cg_begin(spf_plan* P, const float* khat, double lambda, const float* rhs, const float* x0,
+             float* x, double* res, cudaStream_t s) {
+  int64_t n3 = (int64_t)P->N * P->N * P->N;
+  SPF_TRY(toeplitz_apply(P, khat, lambda, x0, P->cg_Ap, nullptr, s));
+  SPF_TRY(launch("cg_init_kernel", s, [&] { cg_init_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(rhs, x0, P->cg_Ap, (float)lambda, n3, x,
+                                                    P->cg_r, P->cg_p, P->cg_part); }));
+  SPF_TRY(launch("finalize_kernel", s, [&] { finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks, P->cg_sc, 0, res); }));
+  return SPF_OK;
+}
+
+int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res, cudaStream_t s) {
+  int64_t n3 = (int64_t)P->N * P->N * P->N;
+  SPF_TRY(toeplitz_apply(P, khat, lambda, P->cg_p, P->cg_Ap, P->cg_part, s));
+  SPF_TRY(launch("finalize_kernel", s, [&] { finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks, P->cg_sc, 1, nullptr); }));
+  SPF_TRY(launch("cg_update_kernel", s, [&] { cg_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, P->cg_r, P->cg_p, P->cg_Ap, P->cg_sc, n3,
+                                                      P->cg_part); }));
+  SPF_TRY(launch("finalize_kernel", s, [&] { finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks, P->cg_sc, 2, res); }));
+  SPF_TRY(launch("cg_dir_kernel", s, [&] { cg_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, n3); }));
+  return SPF_OK;
+}
+
+int cg_alloc(spf_plan* P) {
+  size_t n3 = (size_t)P->N * P->N * P->N;
+  SPF_TRY(dev_alloc((void**)&P->cg_r, sizeof(float) * n3, "cg r"));
+  SPF_TRY(dev_alloc((void**)&P->cg_p, sizeof(float) * n3, "cg p"));
+  SPF_TRY(dev_alloc((void**)&P->cg_Ap, sizeof(float) * n3, "cg Ap"));
+  SPF_TRY(dev_alloc((void**)&P->cg_sc, sizeof(double) * 8, "cg scalars"));
+  SPF_TRY(dev_alloc((void**)&P->cg_part, sizeof(double) * kRedBlocks, "cg partials"));
+  SPF_CUDA(cudaMemset(P->cg_sc, 0, sizeof(double) * 8));
+  return SPF_OK;
+}
+
+}  // namespace spf

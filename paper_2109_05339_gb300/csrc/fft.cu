@@ -1,0 +1,393 @@
+// Hand-written batched 3D FFT for 2/3/5-smooth cube sides (sm_103a).
+//
+// The uniform FFT inside the NUFFT (the cuFINUFFT calls of Sec. III-A) and
+// the circulant convolution of the Toeplitz method (Sec. II-C) both need
+// complex 3D transforms of sides 36..640. One kernel transforms a batch of
+// 1D lines along one axis: the lines are staged through shared memory with
+// coalesced global accesses (whole rows for the contiguous axis; tiles of 8
+// or 16 neighbouring lines for the strided axes), transformed there by
+// self-sorting (Stockham) radix-2/3/4/5 passes with twiddles from an FP64-
+// built table, and written back in natural order. Three launches make a 3D
+// transform. Lines known to be all zero (zero-padded input) or whose output
+// is not needed (cropped output) are skipped.
+#include <cmath>
+#include <vector>
+
+#include "common.h"
+
+namespace spf {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxElems = 4096;                       // elements per CTA tile
+constexpr int kEPT = kMaxElems / kThreads;            // 16 per thread
+
+struct LineSet {
+  // Lines of one pass are indexed by (a, b); b is the fast line coordinate.
+  // Each coordinate runs over at most two half-open ranges.
+  int a_lo[2], a_hi[2];
+  int b_lo[2], b_hi[2];
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by sign * i
+__device__ __forceinline__ float2 mul_si(float2 a, float sign) { return make_float2(-sign * a.y, sign * a.x); }
+
+template <int R>
+__device__ __forceinline__ void dft(float2* v, float sign);
+
+template <>
+__device__ __forceinline__ void dft<2>(float2* v, float) {
+  float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void dft<3>(float2* v, float sign) {
+  const float h = 0.86602540378443864676f;  // sqrt(3)/2
+  float2 s = cadd(v[1], v[2]);
+  float2 d = csub(v[1], v[2]);
+  float2 m = make_float2(v[0].x - 0.5f * s.x, v[0].y - 0.5f * s.y);
+  float2 t = mul_si(make_float2(h * d.x, h * d.y), sign);
+  v[0] = cadd(v[0], s);
+  v[1] = cadd(m, t);
+  v[2] = csub(m, t);
+}
+
+template <>
+__device__ __forceinline__ void dft<4>(float2* v, float sign) {
+  float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  float2 c = cadd(v[1], v[3]), d = mul_si(csub(v[1], v[3]), sign);
+  v[0] = cadd(a, c);
+  v[2] = csub(a, c);
+  v[1] = cadd(b, d);
+  v[3] = csub(b, d);
+}
+
+template <>
+__device__ __forceinline__ void dft<5>(float2* v, float sign) {
+  const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+  const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+  const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+  const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+  float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+  float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+  float2 x0 = v[0];
+  float2 r1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+  float2 r2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+  float2 i1 = mul_si(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y), sign);
+  float2 i2 = mul_si(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y), sign);
+  v[0] = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+  v[1] = cadd(r1, i1);
+  v[4] = csub(r1, i1);
+  v[2] = cadd(r2, i2);
+  v[3] = csub(r2, i2);
+}
+
+// One self-sorting pass of radix R over `lines` lines of length n in `buf`.
+// Butterfly j of a line reads elements j + r n/R, multiplies by
+// w^{k r} (k = j mod Ns, w = exp(sign 2 pi i / (Ns R))), transforms, and
+// writes to (j / Ns) Ns R + k + r Ns.
+template <int R>
+__device__ void stockham_pass(float2* buf, int n, int lines, int Ns, const float2* __restrict__ tw,
+                              float sign) {
+  constexpr int Q = (kEPT + R - 1) / R;
+  const int nb_line = n / R;
+  const int nb = lines * nb_line;
+  const int tstep = n / (Ns * R);
+  float2 v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int b = threadIdx.x + q * kThreads;
+    if (b < nb) {
+      int line = b / nb_line, j = b - line * nb_line;
+      const float2* src = buf + line * n + j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = src[r * nb_line];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int b = threadIdx.x + q * kThreads;
+    if (b < nb) {
+      int line = b / nb_line, j = b - line * nb_line;
+      int k = j % Ns;
+      if (k != 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = __ldg(&tw[(k * r * tstep) % n]);
+          w.y *= -sign;  // table holds exp(-2 pi i m / n); sign=+1 conjugates
+          v[q][r] = cmul(v[q][r], make_float2(w.x, w.y));
+        }
+      }
+      dft<R>(v[q], sign);
+      float2* dst = buf + line * n + (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * Ns] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+struct PassArgs {
+  float2* data;          // complex cube (in place) unless in_real / out_real
+  const float* in_real;  // optional real input (imaginary part zero)
+  float* out_real;       // optional real-part output
+  const float* post_mul; // optional real factor applied to outputs (same layout)
+  int n;                 // line length
+  int64_t es;            // element stride along the line
+  int64_t sa, sb;        // strides of the line coordinates a and b
+  LineSet ls;
+  int lines_per_cta;     // contiguous: lines per CTA; strided: b-lines per CTA
+  int nrad;
+  int radix[16];
+  const float2* tw;
+  float sign;
+};
+
+__device__ __forceinline__ int range_count(int lo, int hi) { return hi > lo ? hi - lo : 0; }
+
+// Map the i-th selected coordinate to its value, over two ranges.
+__device__ __forceinline__ int pick(int i, const int* lo, const int* hi) {
+  int c0 = range_count(lo[0], hi[0]);
+  return i < c0 ? lo[0] + i : lo[1] + (i - c0);
+}
+
+__device__ void run_passes(const PassArgs& A, float2* buf, int lines) {
+  int Ns = 1;
+  for (int p = 0; p < A.nrad; ++p) {
+    int R = A.radix[p];
+    if (R == 4) stockham_pass<4>(buf, A.n, lines, Ns, A.tw, A.sign);
+    else if (R == 2) stockham_pass<2>(buf, A.n, lines, Ns, A.tw, A.sign);
+    else if (R == 3) stockham_pass<3>(buf, A.n, lines, Ns, A.tw, A.sign);
+    else stockham_pass<5>(buf, A.n, lines, Ns, A.tw, A.sign);
+    Ns *= R;
+  }
+}
+
+// Lines along a stride-es axis, tile of `lines_per_cta` consecutive b values
+// (b stride 1 = x) for one a; global accesses coalesced across b.
+__global__ void __launch_bounds__(kThreads) fft_strided_kernel(PassArgs A) {
+  extern __shared__ float2 sbuf[];
+  const int n = A.n, T = A.lines_per_cta;
+  int nb_sel = range_count(A.ls.b_lo[0], A.ls.b_hi[0]) + range_count(A.ls.b_lo[1], A.ls.b_hi[1]);
+  int tiles_b = (nb_sel + T - 1) / T;
+  int tile = blockIdx.x % tiles_b;
+  int ai = blockIdx.x / tiles_b;
+  int a = pick(ai, A.ls.a_lo, A.ls.a_hi);
+  int first = tile * T;
+  int nlines = min(T, nb_sel - first);
+  const int64_t base_a = (int64_t)a * A.sa;
+  // load: element (line l, position i) -> sbuf[l * n + i]
+  for (int e = threadIdx.x; e < nlines * n; e += kThreads) {
+    int l = e % nlines, i = e / nlines;
+    int b = pick(first + l, A.ls.b_lo, A.ls.b_hi);
+    int64_t g = base_a + (int64_t)b * A.sb + (int64_t)i * A.es;
+    sbuf[l * n + i] = A.in_real ? make_float2(A.in_real[g], 0.f) : A.data[g];
+  }
+  __syncthreads();
+  run_passes(A, sbuf, nlines);
+  for (int e = threadIdx.x; e < nlines * n; e += kThreads) {
+    int l = e % nlines, i = e / nlines;
+    int b = pick(first + l, A.ls.b_lo, A.ls.b_hi);
+    int64_t g = base_a + (int64_t)b * A.sb + (int64_t)i * A.es;
+    float2 v = sbuf[l * n + i];
+    if (A.post_mul) {
+      float f = A.post_mul[g];
+      v.x *= f;
+      v.y *= f;
+    }
+    if (A.out_real) A.out_real[g] = v.x;
+    else A.data[g] = v;
+  }
+}
+
+// Lines along the contiguous axis; lines indexed by (a, b) with both strided.
+__global__ void __launch_bounds__(kThreads) fft_contig_kernel(PassArgs A) {
+  extern __shared__ float2 sbuf[];
+  const int n = A.n, L = A.lines_per_cta;
+  int na = range_count(A.ls.a_lo[0], A.ls.a_hi[0]) + range_count(A.ls.a_lo[1], A.ls.a_hi[1]);
+  int nbs = range_count(A.ls.b_lo[0], A.ls.b_hi[0]) + range_count(A.ls.b_lo[1], A.ls.b_hi[1]);
+  int total = na * nbs;
+  int first = blockIdx.x * L;
+  int nlines = min(L, total - first);
+  for (int e = threadIdx.x; e < nlines * n; e += kThreads) {
+    int l = e / n, i = e - l * n;
+    int li = first + l;
+    int a = pick(li / nbs, A.ls.a_lo, A.ls.a_hi);
+    int b = pick(li % nbs, A.ls.b_lo, A.ls.b_hi);
+    int64_t g = (int64_t)a * A.sa + (int64_t)b * A.sb + i;
+    sbuf[e] = A.in_real ? make_float2(A.in_real[g], 0.f) : A.data[g];
+  }
+  __syncthreads();
+  run_passes(A, sbuf, nlines);
+  for (int e = threadIdx.x; e < nlines * n; e += kThreads) {
+    int l = e / n, i = e - l * n;
+    int li = first + l;
+    int a = pick(li / nbs, A.ls.a_lo, A.ls.a_hi);
+    int b = pick(li % nbs, A.ls.b_lo, A.ls.b_hi);
+    int64_t g = (int64_t)a * A.sa + (int64_t)b * A.sb + i;
+    float2 v = sbuf[e];
+    if (A.post_mul) {
+      float f = A.post_mul[g];
+      v.x *= f;
+      v.y *= f;
+    }
+    if (A.out_real) A.out_real[g] = v.x;
+    else A.data[g] = v;
+  }
+}
+
+int factorize(int n, int* radix) {
+  int k = 0;
+  while (n % 4 == 0) { radix[k++] = 4; n /= 4; }
+  while (n % 2 == 0) { radix[k++] = 2; n /= 2; }
+  while (n % 3 == 0) { radix[k++] = 3; n /= 3; }
+  while (n % 5 == 0) { radix[k++] = 5; n /= 5; }
+  return n == 1 ? k : -1;
+}
+
+void full_range(int n, int* lo, int* hi) {
+  lo[0] = 0; hi[0] = n; lo[1] = 0; hi[1] = 0;
+}
+
+// Wrapped range {0..h-1} U {n-h+1..n-1} (h = half width incl. zero).
+void wrapped_range(int n, int h, int* lo, int* hi) {
+  if (h <= 0 || 2 * h - 1 >= n) { full_range(n, lo, hi); return; }
+  lo[0] = 0; hi[0] = h; lo[1] = n - h + 1; hi[1] = n;
+}
+
+int count(const int* lo, const int* hi) {
+  return std::max(0, hi[0] - lo[0]) + std::max(0, hi[1] - lo[1]);
+}
+
+int launch_pass(PassArgs A, bool contiguous, cudaStream_t s) {
+  int na = count(A.ls.a_lo, A.ls.a_hi), nb = count(A.ls.b_lo, A.ls.b_hi);
+  if (na == 0 || nb == 0) return SPF_OK;
+  if (contiguous) {
+    A.lines_per_cta = std::max(1, kMaxElems / A.n);
+    int64_t total = (int64_t)na * nb;
+    int grid = (int)ceil_div(total, A.lines_per_cta);
+    size_t smem = (size_t)A.lines_per_cta * A.n * sizeof(float2);
+    return launch("fft_contig_kernel", s,
+                  [&] { fft_contig_kernel<<<grid, kThreads, smem, s>>>(A); });
+  } else {
+    A.lines_per_cta = std::max(1, std::min(16, kMaxElems / A.n));
+    int tiles_b = (int)ceil_div(nb, A.lines_per_cta);
+    int64_t grid = (int64_t)tiles_b * na;
+    size_t smem = (size_t)A.lines_per_cta * A.n * sizeof(float2);
+    return launch("fft_strided_kernel", s,
+                  [&] { fft_strided_kernel<<<(unsigned)grid, kThreads, smem, s>>>(A); });
+  }
+}
+
+}  // namespace
+
+int fft3_create(FFT3* p, int n0, int n1, int n2) {
+  p->n0 = n0; p->n1 = n1; p->n2 = n2;
+  int ns[3] = {n0, n1, n2};
+  for (int a = 0; a < 3; ++a) {
+    FFTAxisPlan& ax = p->ax[a];
+    ax.n = ns[a];
+    ax.nrad = factorize(ns[a], ax.radix);
+    SPF_CHECK_ARG(ax.nrad >= 0, "fft: side %d is not 2/3/5-smooth", ns[a]);
+    SPF_CHECK_ARG(ns[a] <= kMaxElems, "fft: side %d too large", ns[a]);
+    std::vector<float2> tw(ns[a]);
+    for (int m = 0; m < ns[a]; ++m) {
+      double ang = -2.0 * M_PI * (double)m / (double)ns[a];
+      tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    SPF_TRY(dev_alloc((void**)&ax.twiddle, ns[a] * sizeof(float2), "fft twiddles"));
+    SPF_CUDA(cudaMemcpy(ax.twiddle, tw.data(), ns[a] * sizeof(float2), cudaMemcpyHostToDevice));
+  }
+  // the largest tile needs 32 KB of dynamic shared memory
+  SPF_CUDA(cudaFuncSetAttribute(fft_strided_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxElems * (int)sizeof(float2)));
+  SPF_CUDA(cudaFuncSetAttribute(fft_contig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxElems * (int)sizeof(float2)));
+  return SPF_OK;
+}
+
+void fft3_destroy(FFT3* p) {
+  for (int a = 0; a < 3; ++a) {
+    if (p->ax[a].twiddle) cudaFree(p->ax[a].twiddle);
+    p->ax[a].twiddle = nullptr;
+  }
+}
+
+// Generic pass launcher over axis `axis` (0 = x, 1 = y, 2 = z).
+static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real, float* out_real,
+                     const float* post_mul, int sign, const int* a_lo, const int* a_hi,
+                     const int* b_lo, const int* b_hi, cudaStream_t s) {
+  PassArgs A;
+  A.data = data;
+  A.in_real = in_real;
+  A.out_real = out_real;
+  A.post_mul = post_mul;
+  const FFTAxisPlan& ax = p->ax[axis];
+  A.n = ax.n;
+  A.nrad = ax.nrad;
+  for (int i = 0; i < ax.nrad; ++i) A.radix[i] = ax.radix[i];
+  A.tw = ax.twiddle;
+  A.sign = (float)sign;
+  const int64_t n0 = p->n0, n1 = p->n1;
+  for (int i = 0; i < 2; ++i) {
+    A.ls.a_lo[i] = a_lo[i]; A.ls.a_hi[i] = a_hi[i];
+    A.ls.b_lo[i] = b_lo[i]; A.ls.b_hi[i] = b_hi[i];
+  }
+  if (axis == 0) {          // lines (z, y): a = z, b = y
+    A.es = 1; A.sa = n1 * n0; A.sb = n0;
+    return launch_pass(A, true, s);
+  } else if (axis == 1) {   // lines (z, x): a = z, b = x
+    A.es = n0; A.sa = n1 * n0; A.sb = 1;
+    return launch_pass(A, false, s);
+  } else {                  // lines (y, x): a = y, b = x
+    A.es = n1 * n0; A.sa = n0; A.sb = 1;
+    return launch_pass(A, false, s);
+  }
+}
+
+// Exposed pass with real input / output and a real post-multiplier, used by
+// the NUFFT and Toeplitz code to fuse the first read and last write.
+int fft3_exec_ex(const FFT3* p, float2* data, const float* in_real, float* out_real,
+                 const float* post_mul, int sign, int zero_hw_in, int need_hw_out,
+                 cudaStream_t s) {
+  // A real input is read by the first pass only; with zero-line pruning the
+  // skipped lines would never be written, so the two do not combine.
+  SPF_CHECK_ARG(!(in_real && zero_hw_in > 0), "fft: real input with pruned input lines");
+  int fx_lo[2], fx_hi[2], fy_lo[2], fy_hi[2], fz_lo[2], fz_hi[2];
+  full_range(p->n0, fx_lo, fx_hi);
+  full_range(p->n1, fy_lo, fy_hi);
+  full_range(p->n2, fz_lo, fz_hi);
+  int rx_lo[2], rx_hi[2], ry_lo[2], ry_hi[2];
+  if (zero_hw_in > 0) {
+    wrapped_range(p->n0, zero_hw_in, rx_lo, rx_hi);
+    wrapped_range(p->n1, zero_hw_in, ry_lo, ry_hi);
+    SPF_TRY(axis_pass(p, 2, data, nullptr, nullptr, nullptr, sign, ry_lo, ry_hi, rx_lo, rx_hi, s));
+    SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, sign, fz_lo, fz_hi, rx_lo, rx_hi, s));
+    SPF_TRY(axis_pass(p, 0, data, nullptr, out_real, post_mul, sign, fz_lo, fz_hi, fy_lo, fy_hi, s));
+    return SPF_OK;
+  }
+  wrapped_range(p->n0, need_hw_out, rx_lo, rx_hi);
+  wrapped_range(p->n1, need_hw_out, ry_lo, ry_hi);
+  SPF_TRY(axis_pass(p, 0, data, in_real, nullptr, nullptr, sign, fz_lo, fz_hi, fy_lo, fy_hi, s));
+  SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, sign, fz_lo, fz_hi, rx_lo, rx_hi, s));
+  SPF_TRY(axis_pass(p, 2, data, nullptr, out_real, post_mul, sign, ry_lo, ry_hi, rx_lo, rx_hi, s));
+  return SPF_OK;
+}
+
+}  // namespace spf
+
+namespace spf {
+int fft3_exec(const FFT3* p, float2* data, int sign, int zero_hw_in, int need_hw_out,
+              cudaStream_t s) {
+  return fft3_exec_ex(p, data, nullptr, nullptr, nullptr, sign, zero_hw_in, need_hw_out, s);
+}
+}  // namespace spf

@@ -1,0 +1,34 @@
+// Internal layout of an orientation matcher (Sec. II-B).
+#pragma once
+
+#include "common.h"
+
+constexpr int kCand = 8;          // approximate candidates kept per (image, split)
+constexpr int kMaxSplits = 64;    // orientation splits of one GEMM launch
+
+struct spf_matcher {
+  int device = 0;
+  int max_images = 0, max_orient = 0, P2 = 0;
+  int precision = SPF_FP32, topk = 8;
+  int Kpad = 0;                   // padded row length of quantised copies
+  int n_img = 0;
+  float img_scale = 1.f;
+  const float* images = nullptr;
+  float* x2 = nullptr;            // |img_scale * x_i|^2
+  float* y2 = nullptr;            // |y_j|^2 of the current chunk
+  void* xq = nullptr;             // quantised images  (max_images x Kpad)
+  void* yq = nullptr;             // quantised slices  (max_orient x Kpad)
+  float* xs = nullptr;            // FP8 per-image scales
+  float* ys = nullptr;            // FP8 per-slice scales
+  float* cand_v = nullptr;        // max_images x kMaxSplits x kCand approx scores
+  int* cand_i = nullptr;          // ... orientation indices (-1 empty)
+  float* st_d = nullptr;          // max_images x topk exact distances (running)
+  int* st_i = nullptr;            // max_images x topk indices
+  int* err = nullptr;             // device error word (bounded waits, bounds)
+  int n_sms = 152;
+};
+
+namespace spf {
+int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit, cudaStream_t s);
+int match_tc_supported(int device);
+}  // namespace spf

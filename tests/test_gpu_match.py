@@ -1,0 +1,95 @@
+"""GPU orientation matching (Sec. II-B) against the FP64 brute-force oracle:
+identical argmin on noise-free images and on every image whose oracle margin
+exceeds 1e-4; distances of the returned candidates exact to FP32 rounding."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import matching, slicing
+from tests.gpu_util import f32, problem, to_dev
+
+pytestmark = pytest.mark.gpu
+MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module")
+def c1_data():
+    pb = problem("c1")
+    slices = slicing.slice_model(pb.A, pb.quats, pb.q_lab, 1.0).astype(np.float32)
+    clean = slices[pb.img_pick]
+    rng = np.random.default_rng(101)
+    counts = synth.poisson_counts(rng, pb.cfg.photons * clean.astype(np.float64))
+    return pb, slices, clean, counts
+
+
+def _run(precision, images, slices, scale, topk=8, chunk=None):
+    import torch
+    from paper_2109_05339_gb300 import Matcher
+    n, P2 = images.shape
+    M = slices.shape[0]
+    chunk = chunk or M
+    m = Matcher(n, chunk, P2, precision, topk)
+    X = to_dev(images)
+    m.set_images(X, scale)
+    for c0 in range(0, M, chunk):
+        m.add_slices(to_dev(slices[c0:c0 + chunk]), orient_offset=c0)
+    r = m.results(with_topk=True)
+    m.status()
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+def _check(r, ref, X, Y):
+    ok = ref["margin"] > MARGIN
+    np.testing.assert_array_equal(r["best"][ok], ref["best"][ok])
+    # the returned distance is the exact FP32 distance to the returned index
+    scale = np.sum(X * X, 1) + np.sum(Y[r["best"]] ** 2, 1)
+    d_true = np.sum((X - Y[r["best"]]) ** 2, axis=1)
+    assert np.all(np.abs(r["d1"] - d_true) <= 1e-5 * scale + 1e-30)
+    assert np.all(r["d1"] <= r["d2"])
+    return ok
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_noise_free_images_recover_exactly(c1_data, precision):
+    pb, slices, clean, _ = c1_data
+    r = _run(precision, clean, slices, 1.0)
+    np.testing.assert_array_equal(r["best"], pb.img_pick)
+    ref = matching.match(f32(clean), f32(slices))
+    np.testing.assert_array_equal(r["best"], ref["best"])
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_poisson_images_above_margin(c1_data, precision):
+    pb, slices, _, counts = c1_data
+    s = 1.0 / pb.cfg.photons
+    X = f32(counts) * np.float64(np.float32(s))
+    ref = matching.match(X, f32(slices))
+    r = _run(precision, counts, slices, np.float32(s))
+    ok = _check(r, ref, X, f32(slices))
+    assert ok.sum() >= 1
+
+
+@pytest.mark.parametrize("topk,chunk", [(2, 500), (8, 128), (5, 77)])
+def test_chunked_streaming_equals_one_shot(c1_data, topk, chunk):
+    pb, slices, clean, counts = c1_data
+    X = counts[:37]                                    # ragged image count
+    one = _run("fp32", X, slices, 1e-3, topk=topk)
+    many = _run("fp32", X, slices, 1e-3, topk=topk, chunk=chunk)
+    np.testing.assert_array_equal(one["best"], many["best"])
+    np.testing.assert_allclose(one["d1"], many["d1"], rtol=1e-6)
+    Xd = f32(X) * np.float64(np.float32(1e-3))
+    ref = matching.match(Xd, f32(slices), k=topk)
+    ok = ref["margin"] > MARGIN
+    np.testing.assert_array_equal(many["best"][ok], ref["best"][ok])
+
+
+def test_ties_resolve_to_lowest_index():
+    rng = np.random.default_rng(5)
+    Y = rng.uniform(0, 1, (300, 64)).astype(np.float32)
+    Y[200] = Y[17]
+    Y[299] = Y[17]
+    X = np.stack([Y[17], Y[200], Y[5]])
+    r = _run("fp32", X, Y, 1.0, topk=4)
+    assert list(r["best"]) == [17, 17, 5]
+    assert list(r["topk_idx"][0][:3]) == [17, 200, 299]

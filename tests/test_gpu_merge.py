@@ -1,0 +1,88 @@
+"""GPU merge (Sec. II-C, Eq. 2): type-1 right-hand side, Toeplitz kernel,
+Toeplitz operator and CG against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import merge, rotation
+from tests.gpu_util import f32, problem, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c1_merge():
+    import torch
+    from paper_2109_05339_gb300 import Plan
+    pb = problem("c1")
+    N = pb.cfg.N
+    rng = np.random.default_rng(77)
+    n_img = 100
+    quats = pb.quats.astype(np.float32)
+    best = pb.img_pick.astype(np.int32)
+    images = rng.poisson(30.0, (n_img, pb.q_lab.shape[0])).astype(np.float32)
+    qlab = pb.q_lab.astype(np.float32)
+    D = (rng.uniform(size=qlab.shape[0]) > 0.05).astype(np.float32)
+    b_scale = np.float32(1e-3)
+    plan = Plan(N, 1.0, 1e-6, max_points=n_img * qlab.shape[0])
+    rhs, khat = plan.merge_images(to_dev(images), to_dev(quats), to_dev(qlab), D=to_dev(D),
+                                  b_scale=float(b_scale), orient_idx=to_dev(best, torch.int32))
+    t = rotation.nufft_points(f32(quats)[best], f32(qlab), N, 1.0).reshape(-1, 3)
+    Dall = np.tile(f32(D), n_img)
+    b = f32(images).reshape(-1) * np.float64(b_scale)
+    ref_rhs = merge.rhs(b, t, Dall, N)
+    K = merge.toeplitz_kernel(t, Dall, N)
+    ref_khat = merge.kernel_hat(K, N)
+    return dict(plan=plan, rhs=rhs, khat=khat, ref_rhs=ref_rhs, ref_khat=ref_khat, t=t, Dall=Dall,
+                N=N, images=images, quats=quats, best=best, qlab=qlab, D=D, b_scale=b_scale)
+
+
+def test_rhs_and_kernel(c1_merge):
+    c = c1_merge
+    assert rel_l2(c["rhs"].cpu().numpy(), c["ref_rhs"]) < 1e-5
+    assert rel_l2(c["khat"].cpu().numpy(), c["ref_khat"]) < 1e-5
+    c["plan"].status()
+
+
+def test_chunks_accumulate_to_whole(c1_merge):
+    import torch
+    c = c1_merge
+    plan = c["plan"]
+    rhs = torch.zeros_like(c["rhs"])
+    kh = torch.zeros_like(c["khat"])
+    for c0, c1 in [(0, 33), (33, 34), (34, 100)]:
+        plan.merge_images(to_dev(c["images"][c0:c1]), to_dev(c["quats"]), to_dev(c["qlab"]),
+                          D=to_dev(c["D"]), b_scale=float(c["b_scale"]), rhs=rhs, kernel_hat=kh,
+                          accumulate=c0 > 0, orient_idx=to_dev(c["best"][c0:c1], torch.int32))
+    assert rel_l2(rhs.cpu().numpy(), c["rhs"].cpu().numpy()) < 1e-6
+    assert rel_l2(kh.cpu().numpy(), c["khat"].cpu().numpy()) < 1e-6
+
+
+def test_toeplitz_operator(c1_merge):
+    c = c1_merge
+    N = c["N"]
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((N, N, N)).astype(np.float32)
+    lam = 0.7 * float(c["Dall"].sum()) * 1e-3
+    y = c["plan"].toeplitz_apply(c["khat"], lam, to_dev(x)).cpu().numpy()
+    ref = merge.apply_toeplitz(f32(x), c["ref_khat"], N, lam)
+    assert rel_l2(y, ref) < 1e-5
+    # and equals the direct operator Re(type1(D type2 x)) + lam x (oracle, Sec. III-A)
+    ref_direct = merge.apply_direct(f32(x), c["t"], c["Dall"], lam)
+    assert rel_l2(y, ref_direct) < 1e-5
+
+
+@pytest.mark.parametrize("iters", [1, 5])
+def test_cg_matches_oracle(c1_merge, iters):
+    import torch
+    c = c1_merge
+    N = c["N"]
+    plan = c["plan"]
+    lam = 1e-3 * float(c["Dall"].sum())
+    rng = np.random.default_rng(10)
+    x0 = (rng.standard_normal((N, N, N)) * 0.01).astype(np.float32)
+    hist = torch.zeros(iters + 1, dtype=torch.float64, device="cuda")
+    x = plan.cg_solve(c["khat"], lam, c["rhs"], to_dev(x0), iters, res_hist=hist).cpu().numpy()
+    bt = c["ref_rhs"] + lam * f32(x0)
+    xr, hr = merge.cg(lambda v: merge.apply_toeplitz(v, c["ref_khat"], N, lam), bt, f32(x0), iters)
+    assert rel_l2(x, xr) < 1e-4
+    np.testing.assert_allclose(hist.cpu().numpy(), hr, rtol=1e-4)
