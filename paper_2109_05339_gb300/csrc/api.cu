@@ -471,7 +471,8 @@ int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient, in
     SPF_TRY(simt_launch(m, slices, n_orient, orient_offset, nsplit, s));
   } else {
     SPF_TRY(quantize_rows(m, slices, n_orient, 1.f, m->yq, m->ys, s));
-    nsplit = choose_splits(m, n_orient, 256, 256);
+    int grid;
+    tc_geometry(m->n_img, n_orient, m->n_sms, &grid, &nsplit);
     SPF_TRY(match_tc_launch(m, n_orient, orient_offset, nsplit, s));
   }
   return rerank_launch(m, slices, n_orient, orient_offset, nsplit, s);

@@ -31,4 +31,5 @@ struct spf_matcher {
 namespace spf {
 int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit, cudaStream_t s);
 int match_tc_supported(int device);
+void tc_geometry(int n_img, int n_orient, int n_sms, int* grid, int* nsplit);
 }  // namespace spf

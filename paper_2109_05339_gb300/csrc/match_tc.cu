@@ -1,10 +1,28 @@
 // Tensor-core orientation matching (Sec. II-B) on sm_103a: quantisation of
 // images and model images to BF16 / FP8 e4m3, and the fused cross-term +
 // top-8 kernel.
+//
+// The cross term X Y^T (images x model images, K = pixels) is the dense
+// contraction of the matching step, so it runs on the 5th-generation tensor
+// cores: tcgen05.mma with both operands K-major in shared memory (128-byte
+// swizzle, staged by TMA through a 3-deep mbarrier ring) and FP32
+// accumulators in tensor memory. A CTA owns a 256-image x 256-orientation
+// tile as two 128 x 256 accumulators, i.e. all 512 TMEM columns. Warp roles:
+// warp 0 issues TMA loads, warp 1 issues MMAs (one elected lane each), warp 2
+// owns the TMEM allocation, warps 4..11 are the epilogue: each thread reads
+// one image row of an accumulator with tcgen05.ld, forms |y|^2 - 2 x.y (times
+// the FP8 row scales) and keeps a running top-8 in registers while the CTA
+// walks its contiguous range of tiles, so no distance ever reaches HBM.
+// Every mbarrier wait is bounded by wall-clock time; on expiry the CTA sets
+// an error bit, drains its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cfloat>
+#include <vector>
 
 #include "match.h"
 
@@ -83,10 +101,435 @@ int match_tc_supported(int device) {
   return major == 10 && minor == 3;
 }
 
+namespace {
+
+constexpr int kTcTile = 256;                 // images and orientations per tile
+constexpr int kTcStages = 3;
+constexpr uint32_t kTcHalf = 32 * 1024;      // one operand tile per stage (256 rows x 128 B)
+constexpr uint32_t kTcStage = 2 * kTcHalf;
+constexpr int kTcThreads = 384;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+struct TcParams {
+  int n_img, n_orient, orient_offset, nkb;
+  int n_it, n_ot, total, grid;
+  const float* y2;
+  const float* xs;   // FP8 image scales (nullptr for BF16)
+  const float* ys;   // FP8 slice scales
+  float* cand_v;
+  int* cand_i;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete. Gives up (returns false) when
+// the CTA's abort flag is raised or after kWaitNs; a timeout raises the flag
+// and sets error bit 2.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                          bool honour_abort = true) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 0) {
+      if (honour_abort && *abort_flag) return false;
+      if (global_ns() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        atomicOr(err, 2);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1, tile base 1024-aligned.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                  // version
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B format code, K-major A and B,
+// N = 256, M = 128.
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab_format) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  if constexpr (FP8) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc(0)), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int K>
+__device__ __forceinline__ void tc_insert(float* tv, int* ti, float s, int j) {
+  if (!(s < tv[K - 1])) return;
+  bool placed = false;
+#pragma unroll
+  for (int q = K - 1; q > 0; --q) {
+    bool shift = s < tv[q - 1];
+    float nv = shift ? tv[q - 1] : s;
+    int ni = shift ? ti[q - 1] : j;
+    if (!placed) {
+      tv[q] = nv;
+      ti[q] = ni;
+    }
+    placed = placed || !shift;
+  }
+  if (!placed) {
+    tv[0] = s;
+    ti[0] = j;
+  }
+}
+
+__host__ __device__ inline int work_start(int c, int total, int grid) {
+  return (int)((long long)c * total / grid);
+}
+
+// First CTA whose contiguous work range contains item q.
+__host__ __device__ inline int owner_cta(int q, int total, int grid) {
+  int c = (int)(((long long)q * grid) / total);
+  while (c + 1 < grid && work_start(c + 1, total, grid) <= q) ++c;
+  while (c > 0 && work_start(c, total, grid) > q) --c;
+  return c;
+}
+
+template <bool FP8>
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_match_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kTcStages * kTcStage);
+  uint64_t* empty = full + kTcStages;
+  uint64_t* tfull = empty + kTcStages;
+  uint64_t* tempty = tfull + 1;
+  uint64_t* done = tempty + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x;
+  const int q0 = work_start(c, p.total, p.grid), q1 = work_start(c + 1, p.total, p.grid);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 8);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tslot)), "r"(512) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- producer --
+    if (lane == 0) {
+      uint32_t last_phase[kTcStages];
+      bool used[kTcStages];
+      for (int s = 0; s < kTcStages; ++s) used[s] = false;
+      uint32_t it = 0;
+      bool ok = true;
+      for (int q = q0; q < q1 && ok; ++q) {
+        const int ti_ = q / p.n_ot, to_ = q - ti_ * p.n_ot;
+        for (int kb = 0; kb < p.nkb; ++kb, ++it) {
+          const int s = it % kTcStages;
+          const uint32_t ph = (it / kTcStages) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) { ok = false; break; }
+          uint8_t* a = smem + s * kTcStage;
+          mbar_arrive_expect_tx(&full[s], kTcStage);
+          const int kx = kb * (FP8 ? 128 : 64);
+          tma_load_2d(a, &tmA, kx, ti_ * kTcTile, &full[s]);
+          tma_load_2d(a + kTcHalf, &tmB, kx, to_ * kTcTile, &full[s]);
+          last_phase[s] = ph;
+          used[s] = true;
+        }
+      }
+      // never leave with copies in flight
+      for (int s = 0; s < kTcStages; ++s)
+        if (used[s]) mbar_wait(&full[s], last_phase[s], abort_flag, p.err, false);
+    }
+  } else if (warp == 1) {
+    // --------------------------------------------------------- MMA issue --
+    if (lane == 0) {
+      uint32_t it = 0, t = 0;
+      bool ok = true;
+      for (int q = q0; q < q1 && ok; ++q, ++t) {
+        if (!mbar_wait(tempty, (t & 1u) ^ 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        for (int kb = 0; kb < p.nkb; ++kb, ++it) {
+          const int s = it % kTcStages;
+          const uint32_t ph = (it / kTcStages) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + s * kTcStage);
+          const uint32_t b = a + kTcHalf;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t bd = sdesc(b + kk * 32);
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+              mma<FP8>(tmem + g * 256, sdesc(a + g * (kTcHalf / 2) + kk * 32), bd,
+                       (kb | kk) != 0 ? 1u : 0u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(tfull);
+      }
+      // all issued MMAs complete before the CTA frees TMEM
+      mma_commit(done);
+      mbar_wait(done, 0, abort_flag, p.err, false);
+    }
+  } else if (warp >= 4) {
+    // ---------------------------------------------------------- epilogue --
+    const int g = (warp - 4) >> 2;          // accumulator: image rows 0..127 or 128..255
+    const int quarter = warp & 3;           // TMEM lanes 32*quarter .. +31
+    const int row = g * 128 + quarter * 32 + lane;
+    float tv[kCand];
+    int tix[kCand];
+    int cur_it = -1;
+    uint32_t t = 0;
+    auto flush = [&](int it_) {
+      const int i = it_ * kTcTile + row;
+      if (i < p.n_img) {
+        const int slot = c - owner_cta(it_ * p.n_ot, p.total, p.grid);
+        const size_t o = ((size_t)i * kMaxSplits + slot) * kCand;
+#pragma unroll
+        for (int k = 0; k < kCand; ++k) {
+          p.cand_v[o + k] = tv[k];
+          p.cand_i[o + k] = tix[k];
+        }
+      }
+    };
+    for (int q = q0; q < q1; ++q, ++t) {
+      const int it_ = q / p.n_ot, to_ = q - it_ * p.n_ot;
+      if (it_ != cur_it) {
+        if (cur_it >= 0) flush(cur_it);
+#pragma unroll
+        for (int k = 0; k < kCand; ++k) {
+          tv[k] = FLT_MAX;
+          tix[k] = -1;
+        }
+        cur_it = it_;
+      }
+      if (!mbar_wait(tfull, t & 1u, abort_flag, p.err)) break;
+      tc_fence_after();
+      const int i = it_ * kTcTile + row;
+      const float xs = FP8 ? (i < p.n_img ? -2.f * p.xs[i] : 0.f) : -2.f;
+      const int j0 = to_ * kTcTile;
+#pragma unroll 1
+      for (int ch = 0; ch < 8; ++ch) {
+        float acc[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * 256 + ch * 32), acc);
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+          const int j = j0 + ch * 32 + cc;
+          if (j < p.n_orient) {
+            const float f = FP8 ? xs * __ldg(p.ys + j) : xs;
+            tc_insert<kCand>(tv, tix, fmaf(f, acc[cc], __ldg(p.y2 + j)), p.orient_offset + j);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+    if (cur_it >= 0 && !*abort_flag) flush(cur_it);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+int make_map(CUtensorMap* map, void* base, int rows, int Kpad, bool fp8) {
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return SPF_ERR_UNSUPPORTED;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kpad * (fp8 ? 1 : 2)};
+  const cuuint32_t box[2] = {fp8 ? 128u : 64u, (cuuint32_t)kTcTile};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for %d x %d", (int)r, rows, Kpad);
+    return SPF_ERR_CUDA;
+  }
+  return SPF_OK;
+}
+
+}  // namespace
+
+// Grid and the number of candidate slots per image that one launch writes.
+void tc_geometry(int n_img, int n_orient, int n_sms, int* grid, int* nsplit) {
+  const int n_it = (int)ceil_div(n_img, kTcTile), n_ot = (int)ceil_div(n_orient, kTcTile);
+  const int total = n_it * n_ot;
+  int G = std::min({n_sms, total, n_it * (kMaxSplits - 1)});
+  G = std::max(G, 1);
+  int ns = 1;
+  for (int it = 0; it < n_it; ++it) {
+    int a = owner_cta(it * n_ot, total, G), b = owner_cta(it * n_ot + n_ot - 1, total, G);
+    ns = std::max(ns, b - a + 1);
+  }
+  *grid = G;
+  *nsplit = ns;
+}
+
 int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit, cudaStream_t s) {
-  (void)m; (void)n_orient; (void)orient_offset; (void)nsplit; (void)s;
-  set_error("tensor-core matching kernel not built yet");
-  return SPF_ERR_UNSUPPORTED;
+  const bool fp8 = m->precision == SPF_FP8;
+  CUtensorMap ta, tb;
+  SPF_TRY(make_map(&ta, m->xq, m->n_img, m->Kpad, fp8));
+  SPF_TRY(make_map(&tb, m->yq, n_orient, m->Kpad, fp8));
+  int G, ns;
+  tc_geometry(m->n_img, n_orient, m->n_sms, &G, &ns);
+  if (ns != nsplit) {
+    set_error("internal: split count %d != %d", ns, nsplit);
+    return SPF_ERR_ARG;
+  }
+  TcParams p;
+  p.n_img = m->n_img;
+  p.n_orient = n_orient;
+  p.orient_offset = orient_offset;
+  p.nkb = m->Kpad / (fp8 ? 128 : 64);
+  p.n_it = (int)ceil_div(m->n_img, kTcTile);
+  p.n_ot = (int)ceil_div(n_orient, kTcTile);
+  p.total = p.n_it * p.n_ot;
+  p.grid = G;
+  p.y2 = m->y2;
+  p.xs = fp8 ? m->xs : nullptr;
+  p.ys = fp8 ? m->ys : nullptr;
+  p.cand_v = m->cand_v;
+  p.cand_i = m->cand_i;
+  p.err = m->err;
+  // slots a CTA range does not reach stay empty (index -1)
+  SPF_CUDA(cudaMemsetAsync(m->cand_i, 0xff, sizeof(int) * (size_t)m->n_img * kMaxSplits * kCand, s));
+  const size_t smem = kTcStages * kTcStage + 1024 + 256;
+  if (fp8) {
+    SPF_CUDA(cudaFuncSetAttribute(tc_match_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    return launch("tc_match_fp8", s, [&] { tc_match_kernel<true><<<G, kTcThreads, smem, s>>>(ta, tb, p); });
+  }
+  SPF_CUDA(cudaFuncSetAttribute(tc_match_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  return launch("tc_match_bf16", s, [&] { tc_match_kernel<false><<<G, kTcThreads, smem, s>>>(ta, tb, p); });
 }
 
 }  // namespace spf

@@ -50,7 +50,7 @@ def _check(r, ref, X, Y):
     return ok
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_noise_free_images_recover_exactly(c1_data, precision):
     pb, slices, clean, _ = c1_data
     r = _run(precision, clean, slices, 1.0)
@@ -59,7 +59,7 @@ def test_noise_free_images_recover_exactly(c1_data, precision):
     np.testing.assert_array_equal(r["best"], ref["best"])
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_poisson_images_above_margin(c1_data, precision):
     pb, slices, _, counts = c1_data
     s = 1.0 / pb.cfg.photons
@@ -93,3 +93,42 @@ def test_ties_resolve_to_lowest_index():
     r = _run("fp32", X, Y, 1.0, topk=4)
     assert list(r["best"]) == [17, 17, 5]
     assert list(r["topk_idx"][0][:3]) == [17, 200, 299]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("n_img,n_orient,P2", [(300, 700, 200), (1, 1, 64), (257, 513, 1000)])
+def test_tensor_core_ragged_tiles(precision, n_img, n_orient, P2):
+    """Several 256 x 256 tiles with ragged edges and K not a multiple of the
+    k-block; indices above the margin equal the FP64 oracle, and every returned
+    distance is the exact FP32 distance to the returned index."""
+    rng = np.random.default_rng(n_img + n_orient)
+    Y = rng.gamma(2.0, 1.0, (n_orient, P2)).astype(np.float32)
+    pick = rng.integers(0, n_orient, n_img)
+    X = (Y[pick] + rng.normal(0, 0.05, (n_img, P2))).astype(np.float32)
+    ref = matching.match(f32(X), f32(Y))
+    r = _run(precision, X, Y, 1.0)
+    ok = ref["margin"] > (MARGIN if precision == "bf16" else 1e-2)
+    np.testing.assert_array_equal(r["best"][ok], ref["best"][ok])
+    d_true = np.sum((f32(X) - f32(Y)[r["best"]]) ** 2, axis=1)
+    scale = np.sum(f32(X) ** 2, 1) + np.sum(f32(Y)[r["best"]] ** 2, 1)
+    assert np.all(np.abs(r["d1"] - d_true) <= 1e-5 * scale)
+
+
+def test_fp8_precision_study(c1_data):
+    """Config-3 study: FP8 e4m3 cross term with per-row scales and FP32 re-rank
+    of the top 8; agreement with the FP64 argmin must be complete wherever the
+    margin exceeds the FP8 error scale, and is reported below it."""
+    pb, slices, clean, counts = c1_data
+    s = np.float32(1.0 / pb.cfg.photons)
+    X = f32(counts) * np.float64(s)
+    ref = matching.match(X, f32(slices))
+    r8 = _run("fp8", counts, slices, s)
+    rb = _run("bf16", counts, slices, s)
+    for r in (r8, rb):
+        agree = r["best"] == ref["best"]
+        assert np.all(agree[ref["margin"] > 1e-2])
+    # noise-free images: the true orientation survives FP8 when its margin is clear
+    r8c = _run("fp8", clean, slices, 1.0)
+    refc = matching.match(f32(clean), f32(slices))
+    clear = refc["margin"] > 1e-3
+    np.testing.assert_array_equal(r8c["best"][clear], pb.img_pick[clear])
