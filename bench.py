@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--n-img", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--orient-chunk", type=int, default=None,
+                    help="orientations sliced and matched per chunk (default: all at once)")
+    ap.add_argument("--img-chunk", type=int, default=None,
+                    help="images merged per type-1 call (default: all at once)")
     ap.add_argument("--compare-fp32", action="store_true",
                     help="also time the matching stage on the FP32 CUDA-core path")
     return ap.parse_args()
@@ -172,13 +176,21 @@ def run_ours(args, rank, world):
     quats = torch.from_numpy(pb.quats.astype(np.float32)).to(dev)
     qlab = torch.from_numpy(pb.q_lab.astype(np.float32)).to(dev)
     iq = torch.from_numpy(pb.img_quats.astype(np.float32)).to(dev)
-    drv = MTIP(cfg.N, cfg.qmax, P2, Ni, M, eps=cfg.eps, precision=args.precision, device=dev)
-    clean = drv.plan.slice_model(A, iq, qlab)
-    s = cfg.photons / float(clean.double().sum(1).mean())
+    drv = MTIP(cfg.N, cfg.qmax, P2, Ni, M, orient_chunk=args.orient_chunk, img_chunk=args.img_chunk,
+               eps=cfg.eps, precision=args.precision, device=dev)
+    # noise-free slices at the image orientations, chunk by chunk
     gen = torch.Generator(device=dev)
     gen.manual_seed(cfg.seed * 1000 + rank)
-    images = torch.poisson(clean * s, generator=gen).contiguous()
-    del clean
+    images = torch.empty((Ni, P2), dtype=torch.float32, device=dev)
+    ch = drv.orient_chunk
+    tot = 0.0
+    for c0 in range(0, Ni, ch):
+        drv.plan.slice_model(A, iq[c0:c0 + ch], qlab, out=images[c0:c0 + ch])
+        tot += float(images[c0:c0 + ch].double().sum())
+    s = cfg.photons / (tot / Ni)
+    for c0 in range(0, Ni, ch):
+        blk = images[c0:c0 + ch]
+        blk.copy_(torch.poisson(blk * s, generator=gen))
     torch.cuda.synchronize()
     img_scale = 1.0 / s
 
@@ -236,12 +248,13 @@ def run_ours(args, rank, world):
             roof = r
     stage = {}
     for k, v in kern.items():
-        grp = ("slice" if k.startswith(("interp", "deconv_pad")) else
+        grp = ("slice" if k.startswith(("interp", "deconv_pad", "halo")) else
                "match" if k.startswith(("simt", "tc_", "rerank", "row_norms", "quantize", "state_reset",
                                         "results")) else
-               "merge" if k.startswith(("bin_", "build_subs", "spread", "crop_deconv", "crop_embed",
-                                        "accumulate")) else
-               "cg" if k.startswith(("pad_kernel", "crop_apply", "cg_", "finalize")) else "fft")
+               "sort" if k.startswith(("key_", "scan_", "build_subs")) else
+               "merge" if k.startswith(("spread", "crop_deconv", "crop_embed", "accumulate")) else
+               "cg" if k.startswith(("pad_kernel", "crop_apply", "cg_", "finalize")) else
+               "fft" if k.startswith("fft") else "other")
         stage[grp] = stage.get(grp, 0.0) + v["ms_per_step"]
 
     out = {

@@ -66,12 +66,15 @@ int spf_version(void);
  * eps       NUFFT tolerance (1e-7 .. 1e-2); sets the exponential-of-semicircle
  *           kernel width w = ceil(log10(1/eps)) + 1 and shape beta = 2.3 w,
  *           with upsampling 2.
- * max_points  the most nonuniform points one call may pass (images x pixels,
- *           or orientations x pixels); sizes the sort buffers of type-1 calls.
+ * max_points  the most nonuniform points one type-1 call may pass (images x
+ *           pixels), < 2^31; sizes the point-sort buffer. Type-2 calls sort
+ *           and interpolate in chunks of whole orientations of at most this
+ *           many points (unsorted if not even one orientation fits).
  * device    CUDA device ordinal; the plan allocates its scratch there.
  * Allocates the fine grids (n_f^3 for N modes, n_fT^3 for the 2N-1 modes of
- * the Toeplitz kernel, P_T^3 for the circulant embedding), sort buffers of
- * 4 * max_points bytes, and the CG vectors. Synchronous. *out owns them.
+ * the Toeplitz kernel, P_T^3 for the circulant embedding), a sort buffer of
+ * 4 * max_points bytes, per-cell sort counters (about 12 bytes per fine cell
+ * of each grid), and the CG vectors. Synchronous. *out owns them.
  * ------------------------------------------------------------------------- */
 int spf_plan_create(spf_plan** out, int N, double qmax, double eps, int64_t max_points,
                     int device);

@@ -87,7 +87,7 @@ int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_
 int results_launch(spf_matcher* m, int32_t* best_idx, float* best_d, float* second_d,
                    int32_t* topk_idx, float* topk_d, cudaStream_t s);
 int quantize_rows(spf_matcher* m, const float* src, int rows, float scale, void* dst, float* scales,
-                  cudaStream_t s);
+                  float* norms, cudaStream_t s);
 int tc_kpad(int P2, int precision);
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -156,7 +156,7 @@ int spf_plan_create(spf_plan** out, int N, double qmax, double eps, int64_t max_
   SPF_CHECK_ARG(N >= 3 && N <= 1023 && (N % 2) == 1, "N must be odd in 3..1023 (got %d)", N);
   SPF_CHECK_ARG(qmax > 0.0, "qmax must be positive");
   SPF_CHECK_ARG(eps >= 1e-7 && eps <= 1e-4, "eps must be in [1e-7, 1e-4] (got %g)", eps);
-  SPF_CHECK_ARG(max_points >= 0 && max_points <= 0xffffffffLL, "max_points must be in [0, 2^32)");
+  SPF_CHECK_ARG(max_points >= 0 && max_points <= 0x7fffffffLL, "max_points must be in [0, 2^31)");
   DeviceScope dev(device);
   if (dev.rc != SPF_OK) return dev.rc;
   spf_plan* P = new spf_plan();
@@ -438,9 +438,10 @@ int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float
   m->images = images;
   m->n_img = n_img;
   m->img_scale = img_scale;
-  SPF_TRY(row_norms(images, n_img, m->P2, img_scale, m->x2, s));
-  if (m->precision != SPF_FP32 && n_img > 0)
-    SPF_TRY(quantize_rows(m, images, n_img, img_scale, m->xq, m->xs, s));
+  if (m->precision == SPF_FP32)
+    SPF_TRY(row_norms(images, n_img, m->P2, img_scale, m->x2, s));
+  else
+    SPF_TRY(quantize_rows(m, images, n_img, img_scale, m->xq, m->xs, m->x2, s));
   return state_reset(m, s);
 }
 
@@ -464,13 +465,13 @@ int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient, in
   DeviceScope dev(m->device);
   if (dev.rc != SPF_OK) return dev.rc;
   cudaStream_t s = as_stream(stream);
-  SPF_TRY(row_norms(slices, n_orient, m->P2, 1.f, m->y2, s));
   int nsplit;
   if (m->precision == SPF_FP32) {
+    SPF_TRY(row_norms(slices, n_orient, m->P2, 1.f, m->y2, s));
     nsplit = choose_splits(m, n_orient, 128, 128);
     SPF_TRY(simt_launch(m, slices, n_orient, orient_offset, nsplit, s));
   } else {
-    SPF_TRY(quantize_rows(m, slices, n_orient, 1.f, m->yq, m->ys, s));
+    SPF_TRY(quantize_rows(m, slices, n_orient, 1.f, m->yq, m->ys, m->y2, s));
     int grid;
     tc_geometry(m->n_img, n_orient, m->n_sms, &grid, &nsplit);
     SPF_TRY(match_tc_launch(m, n_orient, orient_offset, nsplit, s));

@@ -245,6 +245,162 @@ __global__ void __launch_bounds__(kThreads) fft_contig_kernel(PassArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time variants for the sides the workloads use. The radix plan, the
+// lines per CTA and every index divisor are constants, so butterfly and
+// element index arithmetic is multiply-shift instead of integer division;
+// per-line global offsets are computed once per CTA.
+template <int... Rs>
+struct Rad {};
+
+template <int N>
+struct RadixPlan;
+template <> struct RadixPlan<36> { using type = Rad<4, 3, 3>; };
+template <> struct RadixPlan<72> { using type = Rad<4, 2, 3, 3>; };
+template <> struct RadixPlan<162> { using type = Rad<2, 3, 3, 3, 3>; };
+template <> struct RadixPlan<216> { using type = Rad<4, 2, 3, 3, 3>; };
+template <> struct RadixPlan<320> { using type = Rad<4, 4, 4, 5>; };
+template <> struct RadixPlan<324> { using type = Rad<4, 3, 3, 3, 3>; };
+template <> struct RadixPlan<432> { using type = Rad<4, 4, 3, 3, 3>; };
+template <> struct RadixPlan<640> { using type = Rad<4, 4, 4, 2, 5>; };
+
+template <int N, int LINES, int R, int Ns>
+__device__ __forceinline__ void pass_ct(float2* buf, int nlines, const float2* __restrict__ tw,
+                                        float sign) {
+  constexpr int NB = N / R;
+  constexpr int Q = (LINES * NB + kThreads - 1) / kThreads;
+  constexpr int TSTEP = N / (Ns * R);
+  const int nb = nlines * NB;
+  float2 v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int b = threadIdx.x + q * kThreads;
+    if (b < nb) {
+      const int line = b / NB, j = b - line * NB;
+      const float2* src = buf + line * N + j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = src[r * NB];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int b = threadIdx.x + q * kThreads;
+    if (b < nb) {
+      const int line = b / NB, j = b - line * NB;
+      const int k = j % Ns;
+      if (Ns > 1 && k != 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = __ldg(&tw[k * r * TSTEP]);
+          w.y *= -sign;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      dft<R>(v[q], sign);
+      float2* dst = buf + line * N + (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * Ns] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int LINES, int Ns, int R, int... Rest>
+__device__ __forceinline__ void passes_ct(float2* buf, int nlines, const float2* __restrict__ tw,
+                                          float sign, Rad<R, Rest...>) {
+  pass_ct<N, LINES, R, Ns>(buf, nlines, tw, sign);
+  if constexpr (sizeof...(Rest) > 0) passes_ct<N, LINES, Ns * R>(buf, nlines, tw, sign, Rad<Rest...>{});
+}
+
+template <int N>
+__host__ __device__ constexpr int ct_lines() { return kMaxElems / N; }
+template <int N>
+__host__ __device__ constexpr int ct_tile() { return (kMaxElems / N) < 16 ? (kMaxElems / N) : 16; }
+
+__device__ __forceinline__ float2 load_elem(const PassArgs& A, int64_t g) {
+  return A.in_real ? make_float2(__ldg(A.in_real + g), 0.f) : A.data[g];
+}
+
+__device__ __forceinline__ void store_elem(const PassArgs& A, int64_t g, float2 v) {
+  if (A.post_mul) {
+    const float f = __ldg(A.post_mul + g);
+    v.x *= f;
+    v.y *= f;
+  }
+  if (A.out_real) A.out_real[g] = v.x;
+  else A.data[g] = v;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) fft_contig_ct(PassArgs A) {
+  constexpr int L = ct_lines<N>();
+  extern __shared__ float2 sbuf[];
+  __shared__ int64_t lbase[L];
+  const int na = range_count(A.ls.a_lo[0], A.ls.a_hi[0]) + range_count(A.ls.a_lo[1], A.ls.a_hi[1]);
+  const int nbs = range_count(A.ls.b_lo[0], A.ls.b_hi[0]) + range_count(A.ls.b_lo[1], A.ls.b_hi[1]);
+  const int first = blockIdx.x * L;
+  const int nlines = min(L, na * nbs - first);
+  if (threadIdx.x < nlines) {
+    const int li = first + threadIdx.x;
+    const int a = pick(li / nbs, A.ls.a_lo, A.ls.a_hi);
+    const int b = pick(li % nbs, A.ls.b_lo, A.ls.b_hi);
+    lbase[threadIdx.x] = (int64_t)a * A.sa + (int64_t)b * A.sb;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
+    const int l = e / N, i = e - l * N;
+    sbuf[e] = load_elem(A, lbase[l] + i);
+  }
+  __syncthreads();
+  passes_ct<N, L, 1>(sbuf, nlines, A.tw, A.sign, typename RadixPlan<N>::type{});
+  for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
+    const int l = e / N, i = e - l * N;
+    store_elem(A, lbase[l] + i, sbuf[e]);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
+  constexpr int T = ct_tile<N>();
+  extern __shared__ float2 sbuf[];
+  __shared__ int64_t lbase[T];
+  const int nb_sel = range_count(A.ls.b_lo[0], A.ls.b_hi[0]) + range_count(A.ls.b_lo[1], A.ls.b_hi[1]);
+  const int tiles_b = (nb_sel + T - 1) / T;
+  const int tile = blockIdx.x % tiles_b;
+  const int a = pick(blockIdx.x / tiles_b, A.ls.a_lo, A.ls.a_hi);
+  const int first = tile * T;
+  const int nlines = min(T, nb_sel - first);
+  if (threadIdx.x < nlines)
+    lbase[threadIdx.x] = (int64_t)a * A.sa + (int64_t)pick(first + threadIdx.x, A.ls.b_lo, A.ls.b_hi) * A.sb;
+  __syncthreads();
+  for (int e = threadIdx.x; e < T * N; e += kThreads) {
+    const int l = e % T, i = e / T;
+    if (l < nlines) sbuf[l * N + i] = load_elem(A, lbase[l] + (int64_t)i * A.es);
+  }
+  __syncthreads();
+  passes_ct<N, T, 1>(sbuf, nlines, A.tw, A.sign, typename RadixPlan<N>::type{});
+  for (int e = threadIdx.x; e < T * N; e += kThreads) {
+    const int l = e % T, i = e / T;
+    if (l < nlines) store_elem(A, lbase[l] + (int64_t)i * A.es, sbuf[l * N + i]);
+  }
+}
+
+template <int N>
+int launch_ct(PassArgs& A, bool contiguous, int na, int nb, cudaStream_t s) {
+  if (contiguous) {
+    constexpr int L = ct_lines<N>();
+    const int grid = (int)ceil_div((int64_t)na * nb, L);
+    const size_t smem = (size_t)L * N * sizeof(float2);
+    return launch("fft_contig_kernel", s, [&] { fft_contig_ct<N><<<grid, kThreads, smem, s>>>(A); });
+  }
+  constexpr int T = ct_tile<N>();
+  const int64_t grid = ceil_div(nb, T) * (int64_t)na;
+  const size_t smem = (size_t)T * N * sizeof(float2);
+  return launch("fft_strided_kernel", s,
+                [&] { fft_strided_ct<N><<<(unsigned)grid, kThreads, smem, s>>>(A); });
+}
+
 int factorize(int n, int* radix) {
   int k = 0;
   while (n % 4 == 0) { radix[k++] = 4; n /= 4; }
@@ -271,6 +427,17 @@ int count(const int* lo, const int* hi) {
 int launch_pass(PassArgs A, bool contiguous, cudaStream_t s) {
   int na = count(A.ls.a_lo, A.ls.a_hi), nb = count(A.ls.b_lo, A.ls.b_hi);
   if (na == 0 || nb == 0) return SPF_OK;
+  switch (A.n) {
+    case 36: return launch_ct<36>(A, contiguous, na, nb, s);
+    case 72: return launch_ct<72>(A, contiguous, na, nb, s);
+    case 162: return launch_ct<162>(A, contiguous, na, nb, s);
+    case 216: return launch_ct<216>(A, contiguous, na, nb, s);
+    case 320: return launch_ct<320>(A, contiguous, na, nb, s);
+    case 324: return launch_ct<324>(A, contiguous, na, nb, s);
+    case 432: return launch_ct<432>(A, contiguous, na, nb, s);
+    case 640: return launch_ct<640>(A, contiguous, na, nb, s);
+    default: break;
+  }
   if (contiguous) {
     A.lines_per_cta = std::max(1, kMaxElems / A.n);
     int64_t total = (int64_t)na * nb;

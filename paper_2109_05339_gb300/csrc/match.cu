@@ -22,20 +22,34 @@ namespace spf {
 namespace {
 
 // ---------------------------------------------------------------- norms ---
-// out[r] = |scale * src_r|^2, one warp per row, FP64 accumulation.
+// out[r] = |scale * src_r|^2, one warp per row: four FP32 partial sums per
+// lane, combined across the warp in FP64.
 __global__ void row_norms_kernel(const float* __restrict__ src, int rows, int P2, float scale,
                                  float* __restrict__ out) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= rows) return;
   const float* row = src + (size_t)warp * P2;
-  double acc = 0.0;
-  for (int p = lane; p < P2; p += 32) {
-    float v = scale * row[p];
-    acc += (double)v * (double)v;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  const bool vec = (P2 % 4) == 0 && (((uintptr_t)row) & 15) == 0;
+  if (vec) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    for (int p = lane; p < P2 / 4; p += 32) {
+      float4 v = __ldg(r4 + p);
+      a0 = fmaf(v.x, v.x, a0);
+      a1 = fmaf(v.y, v.y, a1);
+      a2 = fmaf(v.z, v.z, a2);
+      a3 = fmaf(v.w, v.w, a3);
+    }
+  } else {
+    for (int p = lane; p < P2; p += 32) {
+      float v = __ldg(row + p);
+      a0 = fmaf(v, v, a0);
+    }
   }
+  double acc = ((double)a0 + (double)a1) + ((double)a2 + (double)a3);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) out[warp] = (float)acc;
+  if (lane == 0) out[warp] = (float)(acc * (double)scale * (double)scale);
 }
 
 __global__ void state_reset_kernel(float* __restrict__ d, int* __restrict__ idx, int n) {
@@ -97,21 +111,45 @@ __device__ __forceinline__ void list_insert_ordered(float* tv, int* ti, float s,
 }
 
 // ----------------------------------------------------- FP32 SIMT GEMM ----
-// CTA tile: 128 images x 128 orientations, 256 threads with 8x8 outputs,
-// k-tiles of 16 staged through shared memory (register prefetch of the next
-// tile). Grid: (image tiles, orientation splits); each CTA walks its range
-// of orientation tiles and keeps a running top-8 per image row in the
-// registers of threads 0..127.
-constexpr int BM = 128, BN = 128, BK = 16;
+// CTA tile: 128 images x 128 orientations, 256 threads, each computing an 8x8
+// block as four 4x4 quadrants (rows ty*4 and 64+ty*4, columns tx*4 and
+// 64+tx*4, conflict-free float4 shared reads). k-tiles of 8 are double-
+// buffered in shared memory with a register prefetch of the next tile.
+// Grid: (image tiles, orientation splits); a CTA walks its range of
+// orientation tiles and keeps a running top-8 per image row in shared memory.
+constexpr int BM = 128, BN = 128, BK = 8;
 
+template <bool VEC>
+__device__ __forceinline__ void simt_load(const float* __restrict__ X, int rows, int P2, int r0, int k0,
+                                          float scale, float (&v)[4]) {
+  const int t = threadIdx.x;
+  const int row = r0 + (t >> 1), k = k0 + (t & 1) * 4;
+  if (VEC) {
+    if (row < rows && k < P2) {
+      float4 q = __ldg(reinterpret_cast<const float4*>(X + (size_t)row * P2 + k));
+      v[0] = scale * q.x; v[1] = scale * q.y; v[2] = scale * q.z; v[3] = scale * q.w;
+    } else {
+      v[0] = v[1] = v[2] = v[3] = 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      v[e] = (row < rows && k + e < P2) ? scale * __ldg(X + (size_t)row * P2 + k + e) : 0.f;
+  }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(256, 2)
 simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const float* __restrict__ Y,
                   int n_orient, int orient_offset, int P2, const float* __restrict__ y2,
                   int tiles_per_split, float* __restrict__ cand_v, int* __restrict__ cand_i) {
-  extern __shared__ float smem[];
-  float* As = smem;                    // [BK][BM]
-  float* Bs = As + BK * BM;            // [BK][BN]
-  float* Sc = Bs + BK * BN;            // [BM][BN+1]
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  float* As = smem;                        // [2][BK][BM]
+  float* Bs = As + 2 * BK * BM;            // [2][BK][BN]
+  float* Sc = Bs + 2 * BK * BN;            // [BM][BN+1]
+  float* Lv = Sc + BM * (BN + 1);          // [BM][kCand] running list
+  int* Li = reinterpret_cast<int*>(Lv + BM * kCand);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.x * BM;
@@ -119,18 +157,12 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
   const int n_ot = (n_orient + BN - 1) / BN;
   const int ot_begin = split * tiles_per_split;
   const int ot_end = min(n_ot, ot_begin + tiles_per_split);
-
-  float tv[kCand];
-  int ti[kCand];
-#pragma unroll
-  for (int q = 0; q < kCand; ++q) {
-    tv[q] = FLT_MAX;
-    ti[q] = -1;
-  }
-
-  // global->register loader mapping: 2048 elements per operand tile
-  const int lrow = tid >> 2;           // 0..63 (+64)
-  const int lk = (tid & 3) * 4;        // 0,4,8,12
+  if (tid < BM)
+    for (int q = 0; q < kCand; ++q) {
+      Lv[tid * kCand + q] = FLT_MAX;
+      Li[tid * kCand + q] = -1;
+    }
+  const int srow = tid >> 1, sk = (tid & 1) * 4;
 
   for (int ot = ot_begin; ot < ot_end; ++ot) {
     const int j0 = ot * BN;
@@ -139,72 +171,86 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-
-    float ra[8], rb[8];
-    auto load_tile = [&](int k0) {
+    float ra[4], rb[4];
+    simt_load<VEC>(X, n_img, P2, i0, 0, xscale, ra);
+    simt_load<VEC>(Y, n_orient, P2, j0, 0, 1.f, rb);
+    __syncthreads();
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int row = lrow + 64 * h;
-        int gi = i0 + row, gj = j0 + row;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          int k = k0 + lk + e;
-          ra[h * 4 + e] = (gi < n_img && k < P2) ? xscale * X[(size_t)gi * P2 + k] : 0.f;
-          rb[h * 4 + e] = (gj < n_orient && k < P2) ? Y[(size_t)gj * P2 + k] : 0.f;
-        }
-      }
-    };
-    load_tile(0);
+    for (int e = 0; e < 4; ++e) {
+      As[(sk + e) * BM + srow] = ra[e];
+      Bs[(sk + e) * BN + srow] = rb[e];
+    }
+    __syncthreads();
+    int buf = 0;
     for (int k0 = 0; k0 < P2; k0 += BK) {
-      __syncthreads();
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          As[(lk + e) * BM + lrow + 64 * h] = ra[h * 4 + e];
-          Bs[(lk + e) * BN + lrow + 64 * h] = rb[h * 4 + e];
-        }
-      __syncthreads();
-      if (k0 + BK < P2) load_tile(k0 + BK);
+      const bool more = k0 + BK < P2;
+      if (more) {
+        simt_load<VEC>(X, n_img, P2, i0, k0 + BK, xscale, ra);
+        simt_load<VEC>(Y, n_orient, P2, j0, k0 + BK, 1.f, rb);
+      }
+      const float* A = As + buf * BK * BM;
+      const float* B = Bs + buf * BK * BN;
 #pragma unroll
       for (int k = 0; k < BK; ++k) {
-        float4 a0 = *reinterpret_cast<const float4*>(As + k * BM + ty * 4);
-        float4 a1 = *reinterpret_cast<const float4*>(As + k * BM + 64 + ty * 4);
-        float4 b0 = *reinterpret_cast<const float4*>(Bs + k * BN + tx * 4);
-        float4 b1 = *reinterpret_cast<const float4*>(Bs + k * BN + 64 + tx * 4);
-        float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        float4 a0 = *reinterpret_cast<const float4*>(A + k * BM + ty * 4);
+        float4 a1 = *reinterpret_cast<const float4*>(A + k * BM + 64 + ty * 4);
+        float4 b0 = *reinterpret_cast<const float4*>(B + k * BN + tx * 4);
+        float4 b1 = *reinterpret_cast<const float4*>(B + k * BN + 64 + tx * 4);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
           for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
       }
+      if (more) {
+        float* An = As + (buf ^ 1) * BK * BM;
+        float* Bn = Bs + (buf ^ 1) * BK * BN;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          An[(sk + e) * BM + srow] = ra[e];
+          Bn[(sk + e) * BN + srow] = rb[e];
+        }
+        __syncthreads();
+        buf ^= 1;
+      }
     }
-    __syncthreads();
-    // scores y2 - 2 x.y into the shared tile (rows: ty*4+a or 64+ty*4+a)
+    // scores |y|^2 - 2 x.y into the shared tile
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      int r = (a < 4) ? ty * 4 + a : 64 + ty * 4 + (a - 4);
+      const int r = (a < 4) ? ty * 4 + a : 64 + ty * 4 + (a - 4);
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
-        int c = (b < 4) ? tx * 4 + b : 64 + tx * 4 + (b - 4);
-        int gj = j0 + c;
-        float yy = gj < n_orient ? y2[gj] : 0.f;
-        Sc[r * (BN + 1) + c] = gj < n_orient ? fmaf(-2.f, acc[a][b], yy) : FLT_MAX;
+        const int c = (b < 4) ? tx * 4 + b : 64 + tx * 4 + (b - 4);
+        const int gj = j0 + c;
+        Sc[r * (BN + 1) + c] = gj < n_orient ? fmaf(-2.f, acc[a][b], __ldg(y2 + gj)) : FLT_MAX;
       }
     }
     __syncthreads();
     if (tid < BM) {
+      float tv[kCand];
+      int ti[kCand];
+#pragma unroll
+      for (int q = 0; q < kCand; ++q) {
+        tv[q] = Lv[tid * kCand + q];
+        ti[q] = Li[tid * kCand + q];
+      }
       for (int c = 0; c < BN && j0 + c < n_orient; ++c)
         list_insert<kCand>(tv, ti, Sc[tid * (BN + 1) + c], orient_offset + j0 + c);
+#pragma unroll
+      for (int q = 0; q < kCand; ++q) {
+        Lv[tid * kCand + q] = tv[q];
+        Li[tid * kCand + q] = ti[q];
+      }
     }
+    __syncthreads();
   }
   if (tid < BM && i0 + tid < n_img) {
     size_t o = ((size_t)(i0 + tid) * kMaxSplits + split) * kCand;
 #pragma unroll
     for (int q = 0; q < kCand; ++q) {
-      cand_v[o + q] = tv[q];
-      cand_i[o + q] = ti[q];
+      cand_v[o + q] = Lv[tid * kCand + q];
+      cand_i[o + q] = Li[tid * kCand + q];
     }
   }
 }
@@ -220,7 +266,6 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
   const int img = blockIdx.x;
   __shared__ float s_v[K];
   __shared__ int s_i[K];
-  __shared__ double s_red[8];
   if (threadIdx.x == 0) {
     float tv[K];
     int ti[K];
@@ -242,29 +287,50 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
     }
   }
   __syncthreads();
+  // exact FP32 distances of all candidates in one sweep over the pixels
   const float* x = X + (size_t)img * P2;
-  float exact[K];
-  for (int q = 0; q < K; ++q) {
-    int j = s_i[q];
-    exact[q] = FLT_MAX;
-    if (j < 0) continue;                       // uniform across the CTA
-    const float* y = Y + (size_t)(j - orient_offset) * P2;
-    float acc = 0.f;
+  const float* y[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) y[q] = s_i[q] >= 0 ? Y + (size_t)(s_i[q] - orient_offset) * P2 : x;
+  float acc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = 0.f;
+  bool vec = (P2 % 4) == 0 && (((uintptr_t)x) & 15) == 0 && (((uintptr_t)Y) & 15) == 0;
+  if (vec) {
+    for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
+      float4 xv = __ldg(reinterpret_cast<const float4*>(x) + p);
+      xv.x *= xscale; xv.y *= xscale; xv.z *= xscale; xv.w *= xscale;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        float4 yv = __ldg(reinterpret_cast<const float4*>(y[q]) + p);
+        float d0 = xv.x - yv.x, d1 = xv.y - yv.y, d2 = xv.z - yv.z, d3 = xv.w - yv.w;
+        acc[q] = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, acc[q]))));
+      }
+    }
+  } else {
     for (int p = threadIdx.x; p < P2; p += blockDim.x) {
-      float d = fmaf(xscale, x[p], -y[p]);
-      acc = fmaf(d, d, acc);
+      float xv = xscale * __ldg(x + p);
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        float d = xv - __ldg(y[q] + p);
+        acc[q] = fmaf(d, d, acc[q]);
+      }
     }
-    double v = (double)acc;
+  }
+  __shared__ double s_red[K][8];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double v = (double)acc[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
-      s_v[q] = (float)t;                      // reuse as exact distance
-    }
-    __syncthreads();
-    exact[q] = s_v[q];
+    if ((threadIdx.x & 31) == 0) s_red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  float exact[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[q][w];
+    exact[q] = (float)t;
   }
   if (threadIdx.x == 0) {
     float tv[K];
@@ -306,12 +372,24 @@ int simt_launch(spf_matcher* m, const float* slices, int n_orient, int orient_of
   int n_ot = (int)ceil_div(n_orient, BN);
   int tps = (int)ceil_div(n_ot, nsplit);
   dim3 grid((unsigned)ceil_div(m->n_img, BM), (unsigned)nsplit);
-  size_t smem = sizeof(float) * (BK * BM + BK * BN + BM * (BN + 1));
-  SPF_CUDA(cudaFuncSetAttribute(simt_match_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  size_t smem = sizeof(float) * (2 * BK * BM + 2 * BK * BN + BM * (BN + 1) + 2 * BM * kCand);
+  const bool vec = (m->P2 % 4) == 0 && ((uintptr_t)m->images % 16) == 0 && ((uintptr_t)slices % 16) == 0;
+  if (vec) {
+    SPF_CUDA(cudaFuncSetAttribute(simt_match_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    return launch("simt_match_kernel", s, [&] {
+      simt_match_kernel<true><<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient,
+                                                      orient_offset, m->P2, m->y2, tps, m->cand_v,
+                                                      m->cand_i);
+    });
+  }
+  SPF_CUDA(cudaFuncSetAttribute(simt_match_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
-  SPF_TRY(launch("simt_match_kernel", s, [&] { simt_match_kernel<<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient,
-                                            orient_offset, m->P2, m->y2, tps, m->cand_v, m->cand_i); }));
-  return SPF_OK;
+  return launch("simt_match_kernel", s, [&] {
+    simt_match_kernel<false><<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient,
+                                                     orient_offset, m->P2, m->y2, tps, m->cand_v,
+                                                     m->cand_i);
+  });
 }
 
 int row_norms(const float* src, int rows, int P2, float scale, float* out, cudaStream_t s) {

@@ -30,29 +30,69 @@ namespace spf {
 
 namespace {
 
-// BF16 copy of scale * src rows, zero-padded to Kpad columns.
-__global__ void quantize_bf16_kernel(const float* __restrict__ src, int rows, int P2, int Kpad,
-                                     float scale, __nv_bfloat16* __restrict__ dst) {
-  int64_t total = (int64_t)rows * Kpad;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(i / Kpad), k = (int)(i - (int64_t)r * Kpad);
-    float v = k < P2 ? scale * src[(size_t)r * P2 + k] : 0.f;
-    dst[i] = __float2bfloat16_rn(v);
+__device__ __forceinline__ float block_sum_f64(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return (float)t;
+}
+
+// BF16 copy of scale * src rows (padding columns stay zero from creation)
+// and the FP32 squared norms of the scaled rows, one CTA per row.
+__global__ void __launch_bounds__(256) quantize_bf16_kernel(const float* __restrict__ src, int P2,
+                                                            int Kpad, float scale,
+                                                            __nv_bfloat16* __restrict__ dst,
+                                                            float* __restrict__ norms) {
+  const int r = blockIdx.x;
+  const float* row = src + (size_t)r * P2;
+  __nv_bfloat16* out = dst + (size_t)r * Kpad;
+  float a0 = 0.f, a1 = 0.f;
+  if ((P2 % 4) == 0 && (((uintptr_t)row) & 15) == 0) {
+    for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
+      float4 v = __ldg(reinterpret_cast<const float4*>(row) + p);
+      v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+      a0 = fmaf(v.x, v.x, fmaf(v.y, v.y, a0));
+      a1 = fmaf(v.z, v.z, fmaf(v.w, v.w, a1));
+      __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t*>(&lo);
+      pk.y = *reinterpret_cast<uint32_t*>(&hi);
+      reinterpret_cast<uint2*>(out)[p] = pk;
+    }
+  } else {
+    for (int p = threadIdx.x; p < P2; p += blockDim.x) {
+      float v = scale * __ldg(row + p);
+      a0 = fmaf(v, v, a0);
+      out[p] = __float2bfloat16_rn(v);
+    }
   }
+  __shared__ double sh[8];
+  float n = block_sum_f64((double)a0 + (double)a1, sh);
+  if (threadIdx.x == 0) norms[r] = n;
 }
 
 // FP8 e4m3 copy with a per-row scale a_r = max_p |scale * src_rp| / 448
-// (1 for an all-zero row): dst = e4m3(scale * src / a_r), zero-padded.
-__global__ void quantize_fp8_kernel(const float* __restrict__ src, int rows, int P2, int Kpad,
-                                    float scale, __nv_fp8_e4m3* __restrict__ dst,
-                                    float* __restrict__ row_scale) {
-  int r = blockIdx.x;
-  if (r >= rows) return;
+// (1 for an all-zero row): dst = e4m3(scale * src / a_r); also the FP32
+// squared norms of the scaled rows. One CTA per row.
+__global__ void __launch_bounds__(256) quantize_fp8_kernel(const float* __restrict__ src, int P2,
+                                                           int Kpad, float scale,
+                                                           __nv_fp8_e4m3* __restrict__ dst,
+                                                           float* __restrict__ row_scale,
+                                                           float* __restrict__ norms) {
+  const int r = blockIdx.x;
   const float* row = src + (size_t)r * P2;
-  float mx = 0.f;
-  for (int k = threadIdx.x; k < P2; k += blockDim.x) mx = fmaxf(mx, fabsf(scale * row[k]));
+  float mx = 0.f, a0 = 0.f;
+  for (int k = threadIdx.x; k < P2; k += blockDim.x) {
+    float v = scale * __ldg(row + k);
+    mx = fmaxf(mx, fabsf(v));
+    a0 = fmaf(v, v, a0);
+  }
   __shared__ float sm[32];
+  __shared__ double sh[8];
+  float n = block_sum_f64((double)a0, sh);
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
   __syncthreads();
@@ -61,13 +101,12 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ src, int rows, int
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sm[w]);
     sm[0] = m > 0.f ? m / 448.f : 1.f;
     row_scale[r] = sm[0];
+    norms[r] = n;
   }
   __syncthreads();
-  float inv = 1.f / sm[0];
-  for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
-    float v = k < P2 ? scale * row[k] * inv : 0.f;
-    dst[(size_t)r * Kpad + k] = __nv_fp8_e4m3(v);
-  }
+  const float inv = 1.f / sm[0];
+  for (int k = threadIdx.x; k < P2; k += blockDim.x)
+    dst[(size_t)r * Kpad + k] = __nv_fp8_e4m3(scale * __ldg(row + k) * inv);
 }
 
 }  // namespace
@@ -78,19 +117,17 @@ int tc_kpad(int P2, int precision) {
 }
 
 int quantize_rows(spf_matcher* m, const float* src, int rows, float scale, void* dst, float* scales,
-                  cudaStream_t s) {
+                  float* norms, cudaStream_t s) {
   if (rows == 0) return SPF_OK;
   if (m->precision == SPF_BF16) {
-    int64_t total = (int64_t)rows * m->Kpad;
-    int grid = (int)std::min<int64_t>(ceil_div(total, 256), 152 * 64);
     return launch("quantize_bf16_kernel", s, [&] {
-      quantize_bf16_kernel<<<grid, 256, 0, s>>>(src, rows, m->P2, m->Kpad, scale,
-                                                static_cast<__nv_bfloat16*>(dst));
+      quantize_bf16_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale,
+                                                static_cast<__nv_bfloat16*>(dst), norms);
     });
   }
   return launch("quantize_fp8_kernel", s, [&] {
-    quantize_fp8_kernel<<<rows, 256, 0, s>>>(src, rows, m->P2, m->Kpad, scale,
-                                             static_cast<__nv_fp8_e4m3*>(dst), scales);
+    quantize_fp8_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale,
+                                             static_cast<__nv_fp8_e4m3*>(dst), scales, norms);
   });
 }
 

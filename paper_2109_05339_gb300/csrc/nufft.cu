@@ -5,16 +5,22 @@
 // exponential-of-semicircle NUFFT that the paper runs through cuFINUFFT
 // (Sec. III-A), with these GB300-side choices:
 //   * points are never stored: each kernel recomputes t = R(quat) q_lab on
-//     the fly from the orientation and pixel index (a1 fused into a4/a9);
+//     the fly from the orientation and pixel index (rotation fused into the
+//     interpolation and spreading kernels);
+//   * both directions first counting-sort the points by the fine-grid cell
+//     of their tap origin (bin-major, warp-aggregated atomics, multi-block
+//     scan). Every slice passes through q = 0, so cells are dense: points with
+//     equal keys share their whole w^3 window;
 //   * type 2 deconvolves into a zero-padded complex cube, runs the pruned
-//     hand-written FFT, keeps only the real part (the model is real, so the
-//     slice is the real part) and gathers w^3 taps per point from that real
-//     fine grid, which stays resident in L2;
-//   * type 1 bin-sorts the points into 8^3-cell boxes (counting sort with
-//     warp-aggregated atomics), spreads each box's points into a shared-
-//     memory subgrid with shared atomics, then adds the subgrid into the fine
-//     grid; dense boxes near q = 0 are split into fixed-size subproblems so
-//     one box never serialises the grid; then FFT, real part, deconvolve.
+//     hand-written FFT, keeps the real part (the model is real) and gathers
+//     w^3 taps per point from that L2-resident real grid in sorted order, so
+//     the lanes of a warp mostly read the same addresses (L1 broadcasts);
+//   * type 1 gives each warp a private shared-memory subgrid of one bin: a
+//     lane owns a fixed (dy, dx) tap column and accumulates its w x 2 cells in
+//     registers while consecutive points share a tap origin, writing them back
+//     (plain read-modify-write: no two lanes touch one cell) only when the
+//     origin changes; subgrids are added to the fine grid with red.add once
+//     per subproblem. No shared-memory atomics are used.
 #include <cmath>
 #include <vector>
 
@@ -138,31 +144,216 @@ __global__ void deconv_pad_kernel(const float* __restrict__ A, int N, const floa
   }
 }
 
-// c_j = sum over W^3 taps of G[l] phi phi phi (periodic wrap), one thread per point.
+// Fine cell of a point's tap origin: c = ceil(u - W/2) + floor(W/2), wrapped,
+// and its sort key (bin-major). Returned l0 is the unwrapped first tap.
+struct SortGeom {
+  int nf;
+  int nb0, nb1, nb2;
+};
+
+template <int W>
+__device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
+  constexpr int H = W / 2;
+  int cx = wrap_index((int)ceilf(u.x - 0.5f * W) + H, g.nf);
+  int cy = wrap_index((int)ceilf(u.y - 0.5f * W) + H, g.nf);
+  int cz = wrap_index((int)ceilf(u.z - 0.5f * W) + H, g.nf);
+  constexpr int B = kBinLog, M = kBin - 1;
+  int bin = ((cz >> B) * g.nb1 + (cy >> B)) * g.nb0 + (cx >> B);
+  return (bin << (3 * B)) | ((cz & M) << (2 * B)) | ((cy & M) << B) | (cx & M);
+}
+
 template <int W, class Pts>
-__global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G, int nf, Pts pts,
-                                                     int64_t npts, float beta, float* __restrict__ out) {
+__global__ void key_count_kernel(Pts pts, int64_t npts, SortGeom g, int* __restrict__ count) {
   int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= npts) return;
-  float3 u = pts((uint32_t)id);
-  float wx[W], wy[W], wz[W];
-  int lx = es_weights<W>(u.x, beta, wx);
-  int ly = es_weights<W>(u.y, beta, wy);
-  int lz = es_weights<W>(u.z, beta, wz);
-  int ix[W];
+  int key = -1;
+  if (id < npts) key = point_key<W>(pts((uint32_t)id), g);
+  unsigned grp = __match_any_sync(0xffffffffu, key);
+  int lane = threadIdx.x & 31;
+  if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(count + key, __popc(grp));
+}
+
+template <int W, class Pts>
+__global__ void key_scatter_kernel(Pts pts, int64_t npts, SortGeom g, const int* __restrict__ start,
+                                   int* __restrict__ fill, uint32_t* __restrict__ sorted, int* err) {
+  int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int key = -1;
+  if (id < npts) key = point_key<W>(pts((uint32_t)id), g);
+  unsigned grp = __match_any_sync(0xffffffffu, key);
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(grp) - 1;
+  int rank = __popc(grp & ((1u << lane) - 1u));
+  int base = 0;
+  if (key >= 0 && lane == leader) base = atomicAdd(fill + key, __popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  if (key >= 0) {
+    int pos = start[key] + base + rank;
+    if (pos < start[key + 1]) sorted[pos] = (uint32_t)id;
+    else atomicOr(err, 1);   // counting and scattering disagreed: skip, never overrun
+  }
+}
+
+// ---- exclusive scan of n ints in three passes (block sums, their scan, apply)
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int d = 0; d < W; ++d) ix[d] = wrap_index(lx + d, nf);
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan across a 256-thread block; *total receives the block sum.
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+  __shared__ int ws[8];
+  __shared__ int tot_s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int inc = warp_incl_scan(v);
+  if (lane == 31) ws[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int w = lane < 8 ? ws[lane] : 0;
+    const int wi = warp_incl_scan(w);
+    if (lane < 8) ws[lane] = wi - w;
+    if (lane == 7) tot_s = wi;
+  }
+  __syncthreads();
+  const int res = ws[wid] + inc - v;
+  *total = tot_s;
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(256) scan_sums_kernel(const int* __restrict__ in, int64_t n,
+                                                        int* __restrict__ bsum) {
+  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  int64_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  int acc = 0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += in[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ int ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of nb <= 1024 block sums in place; out_total = their sum
+__global__ void __launch_bounds__(1024) scan_block_sums_kernel(int* __restrict__ bsum, int nb,
+                                                               int* __restrict__ out_total) {
+  __shared__ int sh[1024];
+  int t = threadIdx.x;
+  int v = t < nb ? bsum[t] : 0;
+  sh[t] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int a = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += a;
+    __syncthreads();
+  }
+  if (t < nb) bsum[t] = sh[t] - v;
+  if (t == 1023) *out_total = sh[1023];
+}
+
+__global__ void __launch_bounds__(256) scan_apply_kernel(const int* __restrict__ in, int64_t n,
+                                                         const int* __restrict__ bsum,
+                                                         int* __restrict__ out) {
+  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  int64_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  int running = bsum[blockIdx.x];
+  constexpr int ITEMS = 8;
+  for (int64_t base = b0; base < b1; base += 256 * ITEMS) {
+    int64_t i0 = base + (int64_t)threadIdx.x * ITEMS;
+    int v[ITEMS];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      v[k] = (i0 + k < b1) ? in[i0 + k] : 0;
+      sum += v[k];
+    }
+    int tot;
+    int pre = block_excl_scan(sum, &tot) + running;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (i0 + k < b1) out[i0 + k] = pre;
+      pre += v[k];
+    }
+    running += tot;
+  }
+}
+
+// Cut each bin's sorted range into subproblems of at most kSubPts points.
+__global__ void build_subs_kernel(const int* __restrict__ start, int nbins, int4* __restrict__ subs,
+                                  int64_t max_subs, int* __restrict__ nsubs, int* err) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  int s0 = start[(int64_t)b * kBinCells], s1 = start[(int64_t)(b + 1) * kBinCells];
+  int c = s1 - s0;
+  if (c <= 0) return;
+  int k = (c + kSubPts - 1) / kSubPts;
+  int o = atomicAdd(nsubs, k);
+  if (o + k > max_subs) {
+    atomicOr(err, 1);
+    return;
+  }
+  for (int q = 0; q < k; ++q) subs[o + q] = make_int4(b, s0 + q * kSubPts, min(kSubPts, c - q * kSubPts), 0);
+}
+
+// ------------------------------------------------------------ type 2 ------
+// Halo copy: Gp[z][y][x] = G[(z - H) mod nf][(y - H) mod nf][(x - H) mod nf]
+// on (nf + W)^3, so every tap window of a wrapped point is contiguous.
+__global__ void halo_kernel(const float* __restrict__ G, int nf, int np, int H, float* __restrict__ Gp) {
+  const int64_t total = (int64_t)np * np * np;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % np), y = (int)((i / np) % np), z = (int)(i / ((int64_t)np * np));
+    const int gx = wrap_index(x - H, nf), gy = wrap_index(y - H, nf), gz = wrap_index(z - H, nf);
+    Gp[i] = G[((size_t)gz * nf + gy) * nf + gx];
+  }
+}
+
+__device__ __forceinline__ float wrap_cells(float u, float nf) {
+  u -= nf * floorf(u / nf);
+  return u >= nf ? u - nf : u;
+}
+
+// c_j = sum over W^3 taps of G[l] phi phi phi, one thread per point, points
+// visited in sorted order when `sorted` is given. The point is wrapped into
+// [0, nf) and its window read from the halo copy with constant offsets.
+template <int W, class Pts>
+__global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ Gp, int nf, Pts pts,
+                                                     int64_t npts, const uint32_t* __restrict__ sorted,
+                                                     float beta, float* __restrict__ out) {
+  constexpr int H = W / 2;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  const uint32_t id = sorted ? __ldg(sorted + i) : (uint32_t)i;
+  const float fn = (float)nf;
+  float3 u = pts(id);
+  u.x = wrap_cells(u.x, fn);
+  u.y = wrap_cells(u.y, fn);
+  u.z = wrap_cells(u.z, fn);
+  float wx[W], wy[W], wz[W];
+  const int lx = es_weights<W>(u.x, beta, wx) + H;     // in [0, nf], halo frame
+  const int ly = es_weights<W>(u.y, beta, wy) + H;
+  const int lz = es_weights<W>(u.z, beta, wz) + H;
+  const int np = nf + W;
+  const float* base = Gp + ((size_t)lz * np + ly) * np + lx;
   float acc = 0.f;
 #pragma unroll
   for (int dz = 0; dz < W; ++dz) {
-    const float* plane = G + (size_t)wrap_index(lz + dz, nf) * nf * nf;
+    const float* plane = base + (size_t)dz * np * np;
     float accy = 0.f;
 #pragma unroll
     for (int dy = 0; dy < W; ++dy) {
-      const float* row = plane + (size_t)wrap_index(ly + dy, nf) * nf;
+      const float* row = plane + dy * np;
       float accx = 0.f;
 #pragma unroll
-      for (int dx = 0; dx < W; ++dx) accx = fmaf(__ldg(row + ix[dx]), wx[dx], accx);
+      for (int dx = 0; dx < W; ++dx) accx = fmaf(__ldg(row + dx), wx[dx], accx);
       accy = fmaf(accx, wy[dy], accy);
     }
     acc = fmaf(accy, wz[dz], acc);
@@ -171,162 +362,142 @@ __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G
 }
 
 // ------------------------------------------------------------ type 1 ------
-struct BinGeom {
-  int nf;
-  int nb0, nb1, nb2;
+// Per-warp shared-memory subgrid of one 4^3-cell bin: S planes of ROWS rows of
+// 16 floats, S = 4 + W - 1 cells per axis. A lane (r = lane / 8, dx =
+// lane % 8) owns tap rows dy = r and r + 4 and column dx. Column c of row R
+// is stored at c ^ (8 * ((R >> 1) & 1)): among any 4 consecutive rows the two
+// of equal parity then sit on disjoint halves of their 16-bank group, so one
+// instruction's 32 accesses are conflict-free.
+template <int W>
+struct SpreadCfg {
+  static constexpr int H = W / 2;
+  static constexpr int S = kBin + W - 1;   // cells per axis touched by a bin's points
+  static constexpr int ROWS = kBin + 7;    // rows reached by the (r, r + 4) lane rows
+  static constexpr int RS = 16;
+  static constexpr int PLANE = ROWS * RS;
+  static constexpr int GRID = S * PLANE;
+  static constexpr int REC = 28;           // staged point: lx, ly, lz, v, wz[8], wx[8], wy[8]
+  static constexpr int STAGE = 32 * REC;
+  static constexpr int WARPS = 20;
+  static constexpr size_t SMEM = (size_t)WARPS * (GRID + STAGE) * sizeof(float);
 };
 
-__device__ __forceinline__ int point_bin(float3 u, const BinGeom& g) {
-  int cx = wrap_index((int)floorf(u.x), g.nf);
-  int cy = wrap_index((int)floorf(u.y), g.nf);
-  int cz = wrap_index((int)floorf(u.z), g.nf);
-  return ((cz / kBin) * g.nb1 + (cy / kBin)) * g.nb0 + (cx / kBin);
-}
+__device__ __forceinline__ int swz(int R, int c) { return R * 16 + (c ^ (((R >> 1) & 1) << 3)); }
 
-template <class Pts>
-__global__ void bin_count_kernel(Pts pts, int64_t npts, BinGeom g, int* __restrict__ count) {
-  int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int bin = -1;
-  if (id < npts) bin = point_bin(pts((uint32_t)id), g);
-  unsigned grp = __match_any_sync(0xffffffffu, bin);
-  int lane = threadIdx.x & 31;
-  if (bin >= 0 && lane == __ffs(grp) - 1) atomicAdd(count + bin, __popc(grp));
-}
-
-template <class Pts>
-__global__ void bin_scatter_kernel(Pts pts, int64_t npts, BinGeom g, const int* __restrict__ start,
-                                   int* __restrict__ fill, uint32_t* __restrict__ sorted,
-                                   int* err) {
-  int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int bin = -1;
-  if (id < npts) bin = point_bin(pts((uint32_t)id), g);
-  unsigned grp = __match_any_sync(0xffffffffu, bin);
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(grp) - 1;
-  int rank = __popc(grp & ((1u << lane) - 1u));
-  int base = 0;
-  if (bin >= 0 && lane == leader) base = atomicAdd(fill + bin, __popc(grp));
-  base = __shfl_sync(grp, base, leader);
-  if (bin >= 0) {
-    int pos = start[bin] + base + rank;
-    if (pos < start[bin + 1]) sorted[pos] = (uint32_t)id;
-    else atomicOr(err, 1);   // counting and scattering disagreed: skip, never overrun
+template <int W>
+__device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int lz, int r, int dx,
+                                              float (&acc)[W][2]) {
+  using C = SpreadCfg<W>;
+  const int a0 = swz(ly + r, lx + dx), a1 = swz(ly + r + 4, lx + dx);
+  float* p = grid + lz * C::PLANE;
+#pragma unroll
+  for (int dz = 0; dz < W; ++dz) {
+    p[dz * C::PLANE + a0] += acc[dz][0];
+    p[dz * C::PLANE + a1] += acc[dz][1];
+    acc[dz][0] = 0.f;
+    acc[dz][1] = 0.f;
   }
 }
 
-// Exclusive scans of the bin counts and of their subproblem counts, one CTA.
-__global__ void __launch_bounds__(1024) bin_scan_kernel(const int* __restrict__ count, int nbins,
-                                                        int* __restrict__ start,
-                                                        int* __restrict__ sub_start,
-                                                        int* __restrict__ nsubs) {
-  __shared__ long long s_pts[1024];
-  __shared__ int s_sub[1024];
-  int t = threadIdx.x;
-  int chunk = (nbins + 1023) / 1024;
-  int b0 = t * chunk, b1 = min(nbins, b0 + chunk);
-  long long sp = 0;
-  int ss = 0;
-  for (int b = b0; b < b1; ++b) {
-    int c = count[b];
-    sp += c;
-    ss += (c + kSubPts - 1) / kSubPts;
-  }
-  s_pts[t] = sp;
-  s_sub[t] = ss;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    long long vp = t >= off ? s_pts[t - off] : 0;
-    int vs = t >= off ? s_sub[t - off] : 0;
-    __syncthreads();
-    s_pts[t] += vp;
-    s_sub[t] += vs;
-    __syncthreads();
-  }
-  long long run_p = t ? s_pts[t - 1] : 0;
-  int run_s = t ? s_sub[t - 1] : 0;
-  for (int b = b0; b < b1; ++b) {
-    int c = count[b];
-    start[b] = (int)run_p;
-    sub_start[b] = run_s;
-    run_p += c;
-    run_s += (c + kSubPts - 1) / kSubPts;
-  }
-  if (t == 1023) {
-    start[nbins] = (int)s_pts[1023];
-    sub_start[nbins] = s_sub[1023];
-    *nsubs = s_sub[1023];
-  }
-}
-
-__global__ void build_subs_kernel(const int* __restrict__ count, const int* __restrict__ start,
-                                  const int* __restrict__ sub_start, int nbins,
-                                  int4* __restrict__ subs) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbins) return;
-  int c = count[b];
-  int s0 = sub_start[b];
-  for (int k = 0; k * kSubPts < c; ++k)
-    subs[s0 + k] = make_int4(b, start[b] + k * kSubPts, min(kSubPts, c - k * kSubPts), 0);
-}
-
-// One CTA per subproblem (grid-stride over the device-side count): spread its
-// points into a (kBin+W)^3 shared subgrid, then add the subgrid to the grid.
 template <int W, class Pts, class Str>
-__global__ void __launch_bounds__(256) spread_kernel(Pts pts, Str str, BinGeom g, float beta,
-                                                     const uint32_t* __restrict__ sorted,
-                                                     const int4* __restrict__ subs,
-                                                     const int* __restrict__ nsubs,
-                                                     float* __restrict__ grid, int* err) {
-  constexpr int S = kBin + W;
-  constexpr int H = W / 2;
-  __shared__ float sg[S * S * S];
+__global__ void __launch_bounds__(32 * SpreadCfg<W>::WARPS, 1)
+spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restrict__ sorted,
+              const int4* __restrict__ subs, int* __restrict__ nsubs, float* __restrict__ out, int* err) {
+  using C = SpreadCfg<W>;
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* grid = smem + warp * (C::GRID + C::STAGE);
+  float* stage = grid + C::GRID;
+  const int r = lane >> 3, dx = lane & 7;
   const int nf = g.nf;
-  const int nsub = *nsubs;
-  for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
-    int4 sub = subs[s];
-    int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
-    int ox = bx * kBin - H, oy = by * kBin - H, oz = bz * kBin - H;
-    for (int c = threadIdx.x; c < S * S * S; c += blockDim.x) sg[c] = 0.f;
-    __syncthreads();
-    for (int i = threadIdx.x; i < sub.z; i += blockDim.x) {
-      uint32_t id = sorted[sub.y + i];
-      float3 u = pts(id);
-      float v = str(id);
-      float wx[W], wy[W], wz[W];
-      int lx = es_weights<W>(u.x, beta, wx);
-      int ly = es_weights<W>(u.y, beta, wy);
-      int lz = es_weights<W>(u.z, beta, wz);
-      // shift the taps into the wrapped frame of the point's bin
-      int fx = (int)floorf(u.x), fy = (int)floorf(u.y), fz = (int)floorf(u.z);
-      lx += wrap_index(fx, nf) - fx - ox;
-      ly += wrap_index(fy, nf) - fy - oy;
-      lz += wrap_index(fz, nf) - fz - oz;
-      if (lx < 0 || ly < 0 || lz < 0 || lx > S - W || ly > S - W || lz > S - W) {
-        atomicOr(err, 1);  // cannot happen when binning and spreading agree
-        continue;
-      }
+  for (int c = lane; c < C::GRID; c += 32) grid[c] = 0.f;
+  __syncwarp();
+  const int nsub = nsubs[0];
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(nsubs + 1, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= nsub) break;
+    const int4 sub = subs[s];
+    const int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
+    int cur = -1, cx0 = 0, cy0 = 0, cz0 = 0;
+    float acc[W][2];
 #pragma unroll
-      for (int dz = 0; dz < W; ++dz) {
-        float vz = v * wz[dz];
+    for (int dz = 0; dz < W; ++dz) acc[dz][0] = acc[dz][1] = 0.f;
+    for (int base = 0; base < sub.z; base += 32) {
+      const int nb = min(32, sub.z - base);
+      // stage: lane k prepares point base + k
+      if (lane < nb) {
+        const uint32_t id = __ldg(sorted + sub.y + base + lane);
+        const float3 u = pts(id);
+        float v = str(id);
+        float wx[W], wy[W], wz[W];
+        const int lx = es_weights<W>(u.x, beta, wx);
+        const int ly = es_weights<W>(u.y, beta, wy);
+        const int lz = es_weights<W>(u.z, beta, wz);
+        // tap-origin cell, wrapped; its position inside the bin is the local origin
+        const int cx = wrap_index(lx + C::H, nf), cy = wrap_index(ly + C::H, nf),
+                  cz = wrap_index(lz + C::H, nf);
+        int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);
+        if ((cx >> kBinLog) != bx || (cy >> kBinLog) != by || (cz >> kBinLog) != bz) {
+          atomicOr(err, 1);   // cannot happen when sorting and spreading agree
+          v = 0.f;
+          ox = oy = oz = 0;
+        }
+        float* rec = stage + lane * C::REC;
+        rec[0] = __int_as_float(ox);
+        rec[1] = __int_as_float(oy);
+        rec[2] = __int_as_float(oz);
+        rec[3] = v;
 #pragma unroll
-        for (int dy = 0; dy < W; ++dy) {
-          float vzy = vz * wy[dy];
-          float* row = sg + ((lz + dz) * S + (ly + dy)) * S + lx;
-#pragma unroll
-          for (int dx = 0; dx < W; ++dx) atomicAdd(row + dx, vzy * wx[dx]);
+        for (int d = 0; d < 8; ++d) {
+          rec[4 + d] = d < W ? wz[d] : 0.f;
+          rec[12 + d] = d < W ? wx[d] : 0.f;
+          rec[20 + d] = d < W ? wy[d] : 0.f;
         }
       }
+      __syncwarp();
+      for (int k = 0; k < nb; ++k) {
+        const float* rec = stage + k * C::REC;
+        const int4 hdr = *reinterpret_cast<const int4*>(rec);
+        const int key = hdr.x | (hdr.y << 4) | (hdr.z << 8);
+        if (key != cur) {
+          if (cur >= 0) flush_columns<W>(grid, cx0, cy0, cz0, r, dx, acc);
+          cur = key;
+          cx0 = hdr.x;
+          cy0 = hdr.y;
+          cz0 = hdr.z;
+        }
+        const float a = __int_as_float(hdr.w) * rec[12 + dx];
+        const float c0 = a * rec[20 + r];
+        const float c1 = a * rec[24 + r];
+        const float4 z0 = *reinterpret_cast<const float4*>(rec + 4);
+        const float4 z1 = *reinterpret_cast<const float4*>(rec + 8);
+        const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+        for (int dz = 0; dz < W; ++dz) {
+          acc[dz][0] = fmaf(wz[dz], c0, acc[dz][0]);
+          acc[dz][1] = fmaf(wz[dz], c1, acc[dz][1]);
+        }
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < S * S * S; c += blockDim.x) {
-      float val = sg[c];
+    if (cur >= 0) flush_columns<W>(grid, cx0, cy0, cz0, r, dx, acc);
+    __syncwarp();
+    // add the subgrid to the fine grid and clear it
+    const int ox = bx * kBin - C::H, oy = by * kBin - C::H, oz = bz * kBin - C::H;
+    for (int c = lane; c < C::S * C::S * C::S; c += 32) {
+      const int x = c % C::S, y = (c / C::S) % C::S, z = c / (C::S * C::S);
+      float* p = grid + z * C::PLANE + swz(y, x);
+      const float val = *p;
       if (val != 0.f) {
-        int cx = c % S, cy = (c / S) % S, cz = c / (S * S);
-        int gx = wrap_index(ox + cx, nf), gy = wrap_index(oy + cy, nf), gz = wrap_index(oz + cz, nf);
-        atomicAdd(grid + ((size_t)gz * nf + gy) * nf + gx, val);
+        *p = 0.f;
+        const int gx = wrap_index(ox + x, nf), gy = wrap_index(oy + y, nf), gz = wrap_index(oz + z, nf);
+        atomicAdd(out + ((size_t)gz * nf + gy) * nf + gx, val);
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -373,43 +544,78 @@ int grid_for(int64_t n, int threads = 256) {
   return (int)std::min<int64_t>(b, 152 * 32);
 }
 
+// Counting sort of npts points by tap-origin cell into `sorted`.
 template <int W, class Pts>
-int interp_w(const Grid& g, Pts pts, int64_t npts, float beta, float* out, cudaStream_t s) {
+int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cudaStream_t s) {
+  BinSort& b = g.bins;
+  SortGeom geom{g.nf, b.nb[0], b.nb[1], b.nb[2]};
+  SPF_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int) * b.nkeys, s));
+  SPF_CUDA(cudaMemsetAsync(b.fill, 0, sizeof(int) * b.nkeys, s));
+  const unsigned nb = (unsigned)ceil_div(npts, 256);
+  SPF_TRY(launch("key_count_kernel", s,
+                 [&] { key_count_kernel<W, Pts><<<nb, 256, 0, s>>>(pts, npts, geom, b.count); }));
+  SPF_TRY(launch("scan_sums_kernel", s,
+                 [&] { scan_sums_kernel<<<kScanBlocks, 256, 0, s>>>(b.count, b.nkeys, b.block_sums); }));
+  SPF_TRY(launch("scan_block_sums_kernel", s, [&] {
+    scan_block_sums_kernel<<<1, 1024, 0, s>>>(b.block_sums, kScanBlocks, b.start + b.nkeys);
+  }));
+  SPF_TRY(launch("scan_apply_kernel", s, [&] {
+    scan_apply_kernel<<<kScanBlocks, 256, 0, s>>>(b.count, b.nkeys, b.block_sums, b.start);
+  }));
+  return launch("key_scatter_kernel", s, [&] {
+    key_scatter_kernel<W, Pts><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err);
+  });
+}
+
+template <int W, class Pts>
+int interp_w(spf_plan* P, Pts pts, int64_t npts, bool use_sort, float* out, cudaStream_t s) {
   if (npts == 0) return SPF_OK;
-  SPF_TRY(launch("interp_kernel", s, [&] { interp_kernel<W, Pts><<<(unsigned)ceil_div(npts, 256), 256, 0, s>>>(g.real, g.nf, pts, npts, beta, out); }));
-  return SPF_OK;
+  Grid& g = P->g;
+  const uint32_t* order = nullptr;
+  if (use_sort) {
+    SPF_TRY((sort_points<W, Pts>(g, P->sorted, pts, npts, P->err, s)));
+    order = P->sorted;
+  }
+  const float beta = (float)P->beta;
+  return launch("interp_kernel", s, [&] {
+    interp_kernel<W, Pts><<<(unsigned)ceil_div(npts, 256), 256, 0, s>>>(g.halo, g.nf, pts, npts, order,
+                                                                       beta, out);
+  });
 }
 
 template <int W, class Pts, class Str>
-int spread_w(Grid& g, uint32_t* sorted, Pts pts, Str str, int64_t npts, float beta, int* err,
-             cudaStream_t s) {
+int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cudaStream_t s) {
   BinSort& b = g.bins;
-  BinGeom geom{g.nf, b.nb[0], b.nb[1], b.nb[2]};
-  SPF_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int) * b.nbins, s));
-  SPF_CUDA(cudaMemsetAsync(b.fill, 0, sizeof(int) * b.nbins, s));
   SPF_CUDA(cudaMemsetAsync(g.real, 0, sizeof(float) * (size_t)g.nf * g.nf * g.nf, s));
-  if (npts > 0) {
-    unsigned nb = (unsigned)ceil_div(npts, 256);
-    SPF_TRY(launch("bin_count_kernel", s, [&] { bin_count_kernel<Pts><<<nb, 256, 0, s>>>(pts, npts, geom, b.count); }));
-    SPF_TRY(launch("bin_scan_kernel", s, [&] { bin_scan_kernel<<<1, 1024, 0, s>>>(b.count, b.nbins, b.start, b.sub_start, b.nsubs); }));
-    SPF_TRY(launch("bin_scatter_kernel", s, [&] { bin_scatter_kernel<Pts><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err); }));
-    SPF_TRY(launch("build_subs_kernel", s, [&] { build_subs_kernel<<<(unsigned)ceil_div(b.nbins, 256), 256, 0, s>>>(b.count, b.start, b.sub_start,
-                                                                      b.nbins, b.subs); }));
-    SPF_TRY(launch("spread_kernel", s, [&] { spread_kernel<W, Pts, Str><<<152 * 8, 256, 0, s>>>(pts, str, geom, beta, sorted, b.subs,
-                                                       b.nsubs, g.real, err); }));
-  }
-  return SPF_OK;
+  if (npts == 0) return SPF_OK;
+  SPF_TRY((sort_points<W, Pts>(g, P->sorted, pts, npts, err, s)));
+  SPF_CUDA(cudaMemsetAsync(b.nsubs, 0, 2 * sizeof(int), s));
+  SPF_TRY(launch("build_subs_kernel", s, [&] {
+    build_subs_kernel<<<(unsigned)ceil_div(b.nbins, 256), 256, 0, s>>>(b.start, b.nbins, b.subs,
+                                                                      b.max_subs, b.nsubs, err);
+  }));
+  using C = SpreadCfg<W>;
+  SPF_CUDA(cudaFuncSetAttribute(spread_kernel<W, Pts, Str>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::SMEM));
+  SortGeom geom{g.nf, b.nb[0], b.nb[1], b.nb[2]};
+  const float beta = (float)P->beta;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  return launch("spread_kernel", s, [&] {
+    spread_kernel<W, Pts, Str><<<sms, 32 * C::WARPS, C::SMEM, s>>>(pts, str, geom, beta, P->sorted,
+                                                                   b.subs, b.nsubs, g.real, err);
+  });
 }
 
 }  // namespace
 
 // ------------------------------------------------------------ drivers -----
-#define SPF_W_DISPATCH(w, call) \
-  switch (w) {                  \
-    case 5: { constexpr int W = 5; return call; } \
-    case 6: { constexpr int W = 6; return call; } \
-    case 7: { constexpr int W = 7; return call; } \
-    case 8: { constexpr int W = 8; return call; } \
+#define SPF_W_SWITCH(w, stmt)                                                     \
+  switch (w) {                                                                    \
+    case 5: { constexpr int W = 5; stmt; } break;                                 \
+    case 6: { constexpr int W = 6; stmt; } break;                                 \
+    case 7: { constexpr int W = 7; stmt; } break;                                 \
+    case 8: { constexpr int W = 8; stmt; } break;                                 \
     default: set_error("kernel width %d not built", w); return SPF_ERR_UNSUPPORTED; \
   }
 
@@ -417,40 +623,56 @@ int spread_w(Grid& g, uint32_t* sorted, Pts pts, Str str, int64_t npts, float be
 int type2_setup(spf_plan* P, const float* A, cudaStream_t s) {
   Grid& g = P->g;
   int64_t n3 = (int64_t)g.nf * g.nf * g.nf;
-  SPF_TRY(launch("deconv_pad_kernel", s, [&] { deconv_pad_kernel<<<grid_for(n3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); }));
-  return fft3_exec_ex(&g.fft, g.cube, nullptr, g.real, nullptr, -1, P->Mh + 1, 0, s);
+  SPF_TRY(launch("deconv_pad_kernel", s,
+                 [&] { deconv_pad_kernel<<<grid_for(n3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); }));
+  SPF_TRY(fft3_exec_ex(&g.fft, g.cube, nullptr, g.real, nullptr, -1, P->Mh + 1, 0, s));
+  const int np = g.nf + P->w;
+  const int64_t np3 = (int64_t)np * np * np;
+  return launch("halo_kernel", s, [&] {
+    halo_kernel<<<grid_for(np3), 256, 0, s>>>(g.real, g.nf, np, P->w / 2, g.halo);
+  });
 }
 
+// Slices of M orientations; sorted in chunks of whole orientations that fit
+// the plan's sort buffer, unsorted when not even one orientation fits.
 int type2_quat(spf_plan* P, const float* quats, int M, const float* qlab, int P2, float* out,
                cudaStream_t s) {
-  QuatPts pts{reinterpret_cast<const float4*>(quats), qlab, (uint32_t)P2, P->g.cells_per_q, nullptr, 0, P->err};
-  SPF_W_DISPATCH(P->w, (interp_w<W, QuatPts>(P->g, pts, (int64_t)M * P2, (float)P->beta, out, s)));
+  const int64_t per = P->max_points / P2;
+  if (per <= 0) {
+    QuatPts pts{reinterpret_cast<const float4*>(quats), qlab, (uint32_t)P2, P->g.cells_per_q, nullptr, 0, P->err};
+    SPF_W_SWITCH(P->w, SPF_TRY((interp_w<W, QuatPts>(P, pts, (int64_t)M * P2, false, out, s))));
+    return SPF_OK;
+  }
+  for (int64_t j0 = 0; j0 < M; j0 += per) {
+    const int m = (int)std::min<int64_t>(per, M - j0);
+    QuatPts pts{reinterpret_cast<const float4*>(quats) + j0, qlab, (uint32_t)P2, P->g.cells_per_q,
+                nullptr, 0, P->err};
+    float* o = out + j0 * P2;
+    SPF_W_SWITCH(P->w, SPF_TRY((interp_w<W, QuatPts>(P, pts, (int64_t)m * P2, true, o, s))));
+  }
+  return SPF_OK;
 }
 
 int type2_explicit(spf_plan* P, const float* t, int64_t npts, float* out, cudaStream_t s) {
+  const bool sort = npts <= P->max_points;
   ExplicitPts pts{t, (float)(P->g.nf / (2.0 * M_PI))};
-  SPF_W_DISPATCH(P->w, (interp_w<W, ExplicitPts>(P->g, pts, npts, (float)P->beta, out, s)));
+  SPF_W_SWITCH(P->w, SPF_TRY((interp_w<W, ExplicitPts>(P, pts, npts, sort, out, s))));
+  return SPF_OK;
 }
 
 // Type-1 of `str` at the points onto grid g, then FFT and crop/deconvolve
-// into out (n_modes^3), or into the Toeplitz embedding when emb != NULL.
+// into out (n_modes^3) when out is given.
 template <class Pts, class Str>
 static int type1_run(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, float* out,
                      int accumulate, int* err, cudaStream_t s) {
-  int rc;
-  switch (P->w) {
-    case 5: rc = spread_w<5, Pts, Str>(g, P->sorted, pts, str, npts, (float)P->beta, err, s); break;
-    case 6: rc = spread_w<6, Pts, Str>(g, P->sorted, pts, str, npts, (float)P->beta, err, s); break;
-    case 7: rc = spread_w<7, Pts, Str>(g, P->sorted, pts, str, npts, (float)P->beta, err, s); break;
-    case 8: rc = spread_w<8, Pts, Str>(g, P->sorted, pts, str, npts, (float)P->beta, err, s); break;
-    default: set_error("kernel width %d not built", P->w); return SPF_ERR_UNSUPPORTED;
-  }
-  if (rc != SPF_OK) return rc;
+  SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, Pts, Str>(P, g, pts, str, npts, err, s))));
   int h = (g.n_modes + 1) / 2;
   SPF_TRY(fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s));
   if (out) {
     int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
-    SPF_TRY(launch("crop_deconv_kernel", s, [&] { crop_deconv_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, out, accumulate); }));
+    SPF_TRY(launch("crop_deconv_kernel", s, [&] {
+      crop_deconv_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, out, accumulate);
+    }));
   }
   return SPF_OK;
 }
@@ -506,30 +728,34 @@ int grid_init(Grid* g, int n_modes, int nf, double cells_per_q, int w, double be
   SPF_CUDA(cudaMemcpy(g->deconv, pf.data(), sizeof(float) * n_modes, cudaMemcpyHostToDevice));
   size_t n3 = (size_t)nf * nf * nf;
   SPF_TRY(dev_alloc((void**)&g->real, sizeof(float) * n3, "fine grid"));
+  const size_t np = (size_t)nf + w;
+  SPF_TRY(dev_alloc((void**)&g->halo, sizeof(float) * np * np * np, "fine grid with halo"));
   SPF_TRY(dev_alloc((void**)&g->cube, sizeof(float2) * n3, "fine cube"));
   SPF_TRY(fft3_create(&g->fft, nf, nf, nf));
   BinSort& b = g->bins;
   for (int a = 0; a < 3; ++a) b.nb[a] = (int)ceil_div(nf, kBin);
   b.nbins = b.nb[0] * b.nb[1] * b.nb[2];
+  b.nkeys = (int64_t)b.nbins * kBinCells;
   b.max_subs = b.nbins + max_points / kSubPts + 1;
-  SPF_TRY(dev_alloc((void**)&b.count, sizeof(int) * b.nbins, "bin counts"));
-  SPF_TRY(dev_alloc((void**)&b.fill, sizeof(int) * b.nbins, "bin fill"));
-  SPF_TRY(dev_alloc((void**)&b.start, sizeof(int) * (b.nbins + 1), "bin starts"));
-  SPF_TRY(dev_alloc((void**)&b.sub_start, sizeof(int) * (b.nbins + 1), "subproblem starts"));
+  SPF_TRY(dev_alloc((void**)&b.count, sizeof(int) * b.nkeys, "sort counts"));
+  SPF_TRY(dev_alloc((void**)&b.fill, sizeof(int) * b.nkeys, "sort cursors"));
+  SPF_TRY(dev_alloc((void**)&b.start, sizeof(int) * (b.nkeys + 1), "sort starts"));
+  SPF_TRY(dev_alloc((void**)&b.block_sums, sizeof(int) * kScanBlocks, "scan partials"));
   SPF_TRY(dev_alloc((void**)&b.subs, sizeof(int4) * b.max_subs, "subproblems"));
-  SPF_TRY(dev_alloc((void**)&b.nsubs, sizeof(int), "subproblem count"));
+  SPF_TRY(dev_alloc((void**)&b.nsubs, 2 * sizeof(int), "subproblem count"));
   return SPF_OK;
 }
 
 void grid_free(Grid* g) {
   cudaFree(g->deconv);
   cudaFree(g->real);
+  cudaFree(g->halo);
   cudaFree(g->cube);
   fft3_destroy(&g->fft);
   cudaFree(g->bins.count);
   cudaFree(g->bins.fill);
   cudaFree(g->bins.start);
-  cudaFree(g->bins.sub_start);
+  cudaFree(g->bins.block_sums);
   cudaFree(g->bins.subs);
   cudaFree(g->bins.nsubs);
   *g = Grid();

@@ -5,21 +5,27 @@
 
 namespace spf {
 
-// Bin sort of nonuniform points into fine-grid boxes of kBin^3 cells, split
-// into subproblems of at most kSubPts points (one CTA each).
-constexpr int kBin = 8;
-constexpr int kSubPts = 2048;
+// Counting sort of nonuniform points by the fine-grid cell of their tap
+// origin, in bin-major order: key = bin * 64 + (cell within the 4^3 bin).
+// Points with equal keys share their whole w^3 tap window. Each bin's points
+// are then cut into subproblems of at most kSubPts points.
+constexpr int kBinLog = 2;
+constexpr int kBin = 1 << kBinLog;
+constexpr int kBinCells = kBin * kBin * kBin;
+constexpr int kSubPts = 4096;
+constexpr int kScanBlocks = 1024;
 
 struct BinSort {
   int nb[3] = {0, 0, 0};     // bins per axis
   int nbins = 0;
+  int64_t nkeys = 0;         // nbins * 512
   int64_t max_subs = 0;
-  int* count = nullptr;      // nbins
-  int* fill = nullptr;       // nbins
-  int* start = nullptr;      // nbins + 1
-  int* sub_start = nullptr;  // nbins + 1
+  int* count = nullptr;      // nkeys points per key
+  int* fill = nullptr;       // nkeys scatter cursors
+  int* start = nullptr;      // nkeys + 1 exclusive scan
+  int* block_sums = nullptr; // kScanBlocks scan partials
   int4* subs = nullptr;      // max_subs: (bin, first, npts, 0)
-  int* nsubs = nullptr;      // 1
+  int* nsubs = nullptr;      // [0] subproblem count, [1] work cursor
 };
 
 struct Grid {
@@ -27,7 +33,8 @@ struct Grid {
   int n_modes = 0;           // modes per axis (odd)
   float cells_per_q = 0.f;   // fine-grid cells per unit physical q
   float* deconv = nullptr;   // n_modes deconvolution factors p_k (device)
-  float* real = nullptr;     // nf^3 real grid (spread target / interp source)
+  float* real = nullptr;     // nf^3 real grid (spread target / type-2 FFT output)
+  float* halo = nullptr;     // (nf + w)^3 periodic copy of `real` with a w/2 halo (interp source)
   float2* cube = nullptr;    // nf^3 complex work cube
   FFT3 fft;
   BinSort bins;

@@ -100,3 +100,39 @@ def test_plain_nufft_oracle_agrees_at_c1_scale(torch):
     pb = problem("c1")
     t = rotation.nufft_points(pb.quats[:3], pb.q_lab, pb.cfg.N, 1.0).reshape(-1, 3)
     assert rel_l2(nufft.type2(pb.A, t).real, nudft.type2(pb.A, t).real) < 1e-9
+
+
+def test_dense_cluster_many_subproblems(torch):
+    """Points piled into a few fine cells (like q = 0, where every slice
+    passes): one bin holds several subproblems and many points share each tap
+    window. Both directions must still match the direct sums."""
+    from paper_2109_05339_gb300 import Plan
+    N, npts = 17, 20000
+    rng = np.random.default_rng(12)
+    plan = Plan(N, 1.0, 1e-6, max_points=npts)
+    h = 2 * np.pi / plan.nf
+    t = np.concatenate([rng.normal(0.0, 0.7 * h, (npts - 2000, 3)),
+                        rng.uniform(-np.pi, np.pi, (2000, 3))]).astype(np.float32)
+    v = rng.standard_normal(npts).astype(np.float32)
+    A = rng.standard_normal((N, N, N)).astype(np.float32)
+    f = plan.nufft_type1(to_dev(v), to_dev(t)).cpu().numpy()
+    assert rel_l2(f, nudft.type1(f32(v), f32(t), N).real) < TOL
+    c = plan.nufft_type2(to_dev(A), to_dev(t)).cpu().numpy()
+    assert rel_l2(c, nudft.type2(f32(A), f32(t)).real) < TOL
+    plan.status()
+
+
+def test_slice_chunks_when_sort_buffer_is_small(torch):
+    """max_points below M * P2: slicing runs in sorted chunks of whole
+    orientations; max_points below P2: unsorted. Same results either way."""
+    from paper_2109_05339_gb300 import Plan
+    pb = problem("c1")
+    N = pb.cfg.N
+    quats = pb.quats[:40].astype(np.float32)
+    qlab = pb.q_lab.astype(np.float32)
+    A = to_dev(pb.A.astype(np.float32))
+    ref = slicing.slice_model(f32(pb.A.astype(np.float32)), f32(quats), f32(qlab), 1.0)
+    for mp in (40 * 256, 7 * 256 + 3, 100):
+        plan = Plan(N, 1.0, 1e-6, max_points=mp)
+        s = plan.slice_model(A, to_dev(quats), to_dev(qlab)).cpu().numpy()
+        assert rel_l2(s, ref) < TOL, mp
