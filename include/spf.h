@@ -195,6 +195,32 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
                            float* best_d, float* second_d, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Matching without device allocation. The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc when they match -- code running
+ * while its stream is being captured into a CUDA graph, code inside a host
+ * framework that owns the device memory pool, or a real-time loop that must
+ * not touch the allocator. It computes what spf_match_orientations computes
+ * with precision SPF_FP32 and topk 8 (fused FP32 distance + top-8, exact FP32
+ * re-rank), but every intermediate buffer lives in one static device array of
+ * 4,526,080 bytes (about 4.5 MB) that each GPU loading this library holds
+ * until the process exits.
+ *   images: n_img x P2, slices: n_orient x P2, outputs: n_img each (device).
+ *   n_img <= SPF_STATIC_MATCH_MAX_IMAGES, n_orient <= SPF_STATIC_MATCH_MAX_ORIENT;
+ *   larger sizes return SPF_ERR_ARG with a message.
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. It allocates nothing, then or later. All calls on a device
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and give wrong results --
+ * serialise them. Runs on the calling thread's current device.
+ * ------------------------------------------------------------------------- */
+#define SPF_STATIC_MATCH_MAX_IMAGES 1024
+#define SPF_STATIC_MATCH_MAX_ORIENT 65536
+int spf_match_orientations_static(const float* images, int n_img, float img_scale,
+                                  const float* slices, int n_orient, int P2, int32_t* best_idx,
+                                  float* best_d, float* second_d, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Tracing (no counterpart in the paper; it backs the per-stage timings of
  * its Fig. 5 style breakdown). Host calls.
  * spf_profile_enable(1) clears the counters and starts recording a CUDA event

@@ -58,6 +58,7 @@ PROTOTYPES = {
     "spf_matcher_add_slices": (I, [P, P, I, I, P]),
     "spf_matcher_results": (I, [P, P, P, P, P, P, P]),
     "spf_match_orientations": (I, [P, P, I, F, P, I, P, P, P, P]),
+    "spf_match_orientations_static": (I, [P, I, F, P, I, I, P, P, P, P]),
     "spf_profile_enable": (I, [I]),
     "spf_profile_read": (I, [I, C.c_char_p, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
     "spf_launch_count": (C.c_longlong, []),
