@@ -122,6 +122,23 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def traffic_for(kernel, units_per_launch):
+    """DRAM bytes per launch from profiles/dram_traffic.json (ncu counters per
+    unit of work), or None when no record exists or the kernel's source file
+    changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+        return None
+    return rec["dram_bytes_per_unit"] * units_per_launch
+
+
 def roofline_for(kernel, launches, ms, ctx, peaks, src, clocks):
     """Algorithmic work per launch / average launch time, against its peak."""
     avg_s = ms / launches / 1e3
@@ -142,10 +159,16 @@ def roofline_for(kernel, launches, ms, ctx, peaks, src, clocks):
         pts = ctx["points_per_launch"][kernel.split("_")[0]]
         taps = pts * w ** 3
         mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        # one 4-byte shared/L1 access per tap; 32 such words per clock per SM
-        peak = 152 * 32 * mhz * 1e6 / 1e9
+        if kernel.startswith("interp"):
+            # one 4-byte L1 gather per tap; 32 words per clock per SM
+            peak = 152 * 32 * mhz * 1e6 / 1e9
+            src_ = "152 SMs x 32 L1 words/clock x median SM clock (one gather per tap)"
+        else:
+            # taps accumulate in registers: one FP32 FMA per tap, 128 per clock per SM
+            peak = 152 * 128 * mhz * 1e6 / 1e9
+            src_ = "152 SMs x 128 FP32 FMA/clock x median SM clock (one FMA per tap)"
         return {"kernel": kernel, "bound": "alu", "achieved": taps / avg_s / 1e9, "peak": peak,
-                "unit": "Gtap/s", "peak_source": "152 SMs x 32 shared-memory words/clock x median SM clock"}
+                "unit": "Gtap/s", "peak_source": src_}
     # HBM-bound kernels: FFT passes etc.
     bytes_ = ctx.get("bytes_per_launch", {}).get(kernel)
     if bytes_ is None:
@@ -244,7 +267,9 @@ def run_ours(args, rank, world):
         r = roofline_for(dominant, n, t, ctx, peaks, src, ck)
         if r:
             r["frac"] = r["achieved"] / r["peak"]
-            r["traffic"] = None
+            units = (ctx["points_per_launch"].get(dominant.split("_")[0]) if dominant.startswith(("interp", "spread"))
+                     else ctx["n_img"] * ctx["n_orient_per_launch"] if dominant.startswith(("tc_", "simt")) else None)
+            r["traffic"] = traffic_for(dominant, units) if units else None
             roof = r
     stage = {}
     for k, v in kern.items():

@@ -113,6 +113,37 @@ int spf_nufft_type1(spf_plan* plan, const float* v, const float* pts, int64_t np
                     float* out, int accumulate, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Point sets: the rotated detector points of a fixed orientation set, sorted
+ * once for both fine grids (the "set points" step of a NUFFT plan). The paper
+ * slices at "a predetermined set of orientations" (Sec. II-A) that does not
+ * change between M-TIP iterations, so slicing and merging reuse the sort.
+ *
+ * spf_points_create: copies quats (M x 4) and q_lab (P2 x 3) and sorts the
+ *   M*P2 points (M*P2 < 2^31). Allocates about 16 bytes per point (two sort
+ *   orders, class sums) -- a create call. Stream-ordered after the copies.
+ * spf_slice_points: as spf_slice_model for the set's orientations;
+ *   slices: M x P2.
+ * spf_merge_points: Sec. II-C merge by class sums. Images whose orientation
+ *   orient_idx[i] falls in [orient_offset, orient_offset + M) are summed per
+ *   orientation (weighted by D[p] b_scale) -- the class sums of the M-TIP
+ *   pipeline -- and the class sums and class counts are spread at the set's
+ *   points. By linearity the result equals spf_merge_images with
+ *   quats[orient_idx[i]] for those images:
+ *     rhs        (+)= Re sum_{j,p} (sum_{i in class j} D[p] b_scale img[i,p]) e^{+i n.t_jp}
+ *     kernel_hat (+)= FFT_{P_T}(embed Re sum_{j,p} count_j D[p] e^{+i d.t_jp}).
+ *   Images outside the range are ignored (chunked orientation sets add up
+ *   with accumulate = 1). Either output may be NULL.
+ * ------------------------------------------------------------------------- */
+typedef struct spf_points spf_points;
+int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int M, const float* q_lab,
+                      int P2, void* stream);
+int spf_points_destroy(spf_points* pts);
+int spf_slice_points(spf_plan* plan, spf_points* pts, const float* A, float* slices, void* stream);
+int spf_merge_points(spf_plan* plan, spf_points* pts, const float* images, const int32_t* orient_idx,
+                     int n_img, int orient_offset, const float* D, float b_scale, float* rhs,
+                     float* kernel_hat, int accumulate, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Merge, Sec. II-C (Eq. 2 with the Toeplitz method): from one chunk of
  * oriented images build
  *   rhs[n]        (+)= Re sum_{i,p} D[p] b_scale images[i*P2+p] exp(+i n.t_ip)
@@ -144,6 +175,20 @@ int spf_cg_begin(spf_plan* plan, const float* kernel_hat, double lambda, const f
                  const float* x0, float* x, double* res_norm, void* stream);
 int spf_cg_merge_step(spf_plan* plan, const float* kernel_hat, double lambda, float* x,
                       double* res_norm, void* stream);
+
+/* L-curve quantities of a merge solution x (Sec. II-C: the regularisation
+ * parameter is chosen on the L-curve). out (device, 2 doubles):
+ *   out[0] = |A x - b|_D^2 = x.T x - 2 x.rhs + b_norm2[0]
+ *   out[1] = |x - x0|^2
+ * with T x the Toeplitz product without lambda, rhs the merge right-hand side
+ * Re(A^H D b) and b_norm2 (device, 1 double, may be NULL for 0) = b.D b from
+ * spf_weighted_sumsq. FP64 reductions; uses the plan's CG scratch, so call it
+ * between CG solves, not inside one. */
+int spf_cg_objective(spf_plan* plan, const float* kernel_hat, const float* rhs, const float* x,
+                     const float* x0, const double* b_norm2, double* out, void* stream);
+/* out[0] (+)= sum_{i,p} D[p] (scale images[i*P2+p])^2 in FP64 (D NULL: ones). */
+int spf_weighted_sumsq(spf_plan* plan, const float* images, int n_img, int P2, const float* D,
+                       float scale, double* out, int accumulate, void* stream);
 
 /* H x without the CG state (Toeplitz form): out = crop(IFFT(kernel_hat *
  * FFT(pad x))) + lambda x. Used to check the operator. */
@@ -182,6 +227,11 @@ int spf_matcher_destroy(spf_matcher* m);
 int spf_matcher_status(spf_matcher* m);
 int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float img_scale,
                            void* stream);
+/* Pixel weights for the distance, d_ij = sum_p D[p] (x_ip - y_jp)^2 (D >= 0;
+ * D = 0 excludes a pixel, e.g. behind the beam stop of Sec. II-C). D: P2
+ * floats (device) or NULL for all ones. Takes effect for the next
+ * set_images / add_slices calls: set it before set_images. */
+int spf_matcher_set_mask(spf_matcher* m, const float* D, void* stream);
 int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient,
                            int orient_offset, void* stream);
 int spf_matcher_results(spf_matcher* m, int32_t* best_idx, float* best_d, float* second_d,

@@ -11,7 +11,7 @@ submodule compiles it and does not need it.
 import importlib
 
 _EXPORTS = {
-    "Plan": "api", "Matcher": "api", "SliceModel": "api", "slice_model": "api",
+    "Plan": "api", "PointSet": "api", "Matcher": "api", "SliceModel": "api", "slice_model": "api",
     "SpfError": "api", "PRECISIONS": "api", "MTIP": "mtip",
 }
 

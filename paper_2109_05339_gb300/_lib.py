@@ -48,13 +48,20 @@ PROTOTYPES = {
     "spf_nufft_type2": (I, [P, P, P, I64, P, P]),
     "spf_nufft_type1": (I, [P, P, P, I64, P, I, P]),
     "spf_merge_images": (I, [P, P, P, I, P, I, P, I, P, F, P, P, I, P]),
+    "spf_points_create": (I, [C.POINTER(P), P, P, I, P, I, P]),
+    "spf_points_destroy": (I, [P]),
+    "spf_slice_points": (I, [P, P, P, P, P]),
+    "spf_merge_points": (I, [P, P, P, P, I, I, P, F, P, P, I, P]),
     "spf_cg_begin": (I, [P, P, D, P, P, P, P, P]),
     "spf_cg_merge_step": (I, [P, P, D, P, P, P]),
     "spf_toeplitz_apply": (I, [P, P, D, P, P, P]),
+    "spf_cg_objective": (I, [P, P, P, P, P, P, P, P]),
+    "spf_weighted_sumsq": (I, [P, P, I, I, P, F, P, I, P]),
     "spf_matcher_create": (I, [C.POINTER(P), I, I, I, I, I, I]),
     "spf_matcher_destroy": (I, [P]),
     "spf_matcher_status": (I, [P]),
     "spf_matcher_set_images": (I, [P, P, I, F, P]),
+    "spf_matcher_set_mask": (I, [P, P, P]),
     "spf_matcher_add_slices": (I, [P, P, I, I, P]),
     "spf_matcher_results": (I, [P, P, P, P, P, P, P]),
     "spf_match_orientations": (I, [P, P, I, F, P, I, P, P, P, P]),

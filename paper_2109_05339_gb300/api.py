@@ -12,7 +12,7 @@ import torch
 
 from ._lib import SPF_BF16, SPF_FP8, SPF_FP32, SpfError, check, lib
 
-__all__ = ["Plan", "Matcher", "SliceModel", "slice_model", "SpfError", "PRECISIONS"]
+__all__ = ["Plan", "PointSet", "Matcher", "SliceModel", "slice_model", "SpfError", "PRECISIONS"]
 
 PRECISIONS = {"fp32": SPF_FP32, "bf16": SPF_BF16, "fp8": SPF_FP8}
 
@@ -216,6 +216,70 @@ class Plan:
         return x
 
 
+class PointSet:
+    """Rotated detector points of a fixed orientation set, sorted once (Sec. II-A:
+    the model images live on a predetermined orientation set)."""
+
+    def __init__(self, plan: Plan, quats, q_lab):
+        d = plan.device
+        _f32(quats, "quats", d)
+        _f32(q_lab, "q_lab", d)
+        self.plan = plan
+        self.M, self.P2 = quats.shape[0], q_lab.shape[0]
+        h = C.c_void_p()
+        check(lib.spf_points_create(C.byref(h), plan._h, _ptr(quats), self.M, _ptr(q_lab), self.P2,
+                                    _stream(d)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.spf_points_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def slice(self, A, out=None):
+        """Model images (M, P2) of model A at the set's orientations."""
+        p, d = self.plan, self.plan.device
+        p._grid(A, "A")
+        if out is None:
+            out = torch.empty((self.M, self.P2), dtype=torch.float32, device=A.device)
+        _f32(out, "out", d, (self.M, self.P2))
+        check(lib.spf_slice_points(p._h, self._h, _ptr(A), _ptr(out), _stream(d)))
+        return out
+
+    def merge(self, images, orient_idx, orient_offset=0, D=None, b_scale=1.0, rhs=None, kernel_hat=None,
+              accumulate=False, want_rhs=True, want_kernel=True):
+        """Sec. II-C right-hand side and Toeplitz kernel from class sums of the
+        images whose orient_idx lies in [orient_offset, orient_offset + M)."""
+        p, d = self.plan, self.plan.device
+        _f32(images, "images", d)
+        if orient_idx.dtype != torch.int32 or not orient_idx.is_contiguous():
+            raise TypeError("orient_idx must be a contiguous int32 tensor")
+        n_img = images.shape[0]
+        if images.dim() != 2 or images.shape[1] != self.P2 or orient_idx.shape[0] != n_img:
+            raise ValueError("images must be (n, P2) with one orient_idx per image")
+        if D is not None:
+            _f32(D, "D", d, (self.P2,))
+        if want_rhs and rhs is None:
+            if accumulate:
+                raise ValueError("accumulate needs an rhs tensor")
+            rhs = torch.empty((p.N,) * 3, dtype=torch.float32, device=images.device)
+        if want_kernel and kernel_hat is None:
+            if accumulate:
+                raise ValueError("accumulate needs a kernel_hat tensor")
+            kernel_hat = torch.empty((p.PT,) * 3, dtype=torch.float32, device=images.device)
+        check(lib.spf_merge_points(p._h, self._h, _ptr(images), _ptr(orient_idx), n_img, int(orient_offset),
+                                   _ptr(D), float(b_scale), _ptr(rhs) if want_rhs else None,
+                                   _ptr(kernel_hat) if want_kernel else None, int(bool(accumulate)),
+                                   _stream(d)))
+        return rhs, kernel_hat
+
+
 class Matcher:
     """Orientation matcher (Sec. II-B) with a streaming top-k across chunks."""
 
@@ -245,6 +309,13 @@ class Matcher:
 
     def status(self):
         check(lib.spf_matcher_status(self._h))
+
+    def set_mask(self, D=None):
+        """Pixel weights D (P2,) for the distance (0 excludes a pixel); None clears."""
+        if D is not None:
+            _f32(D, "D", self.device, (self.P2,))
+        self._mask = D
+        check(lib.spf_matcher_set_mask(self._h, _ptr(D), _stream(self.device)))
 
     def set_images(self, images, img_scale=1.0):
         _f32(images, "images", self.device)

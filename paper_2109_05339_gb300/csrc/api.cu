@@ -68,7 +68,12 @@ int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats,
               const int* oidx, int n_img, const float* qlab, int P2, const float* D, float b_scale,
               float* rhs, float* kernel_hat, int accumulate, int* err, cudaStream_t s);
 int grid_init(Grid* g, int n_modes, int nf, double cells_per_q, int w, double beta,
-              int64_t max_points);
+              int64_t max_points, bool interp_source);
+int points_build(spf_plan* P, spf_points* S, cudaStream_t s);
+int slice_points(spf_plan* P, spf_points* S, const float* A, float* out, cudaStream_t s);
+int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oidx, int n_img, int off,
+                 const float* D, float b_scale, float* rhs, float* kernel_hat, int accumulate,
+                 cudaStream_t s);
 void grid_free(Grid* g);
 // cg.cu
 int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x, float* out,
@@ -77,10 +82,17 @@ int cg_begin(spf_plan* P, const float* khat, double lambda, const float* rhs, co
              float* x, double* res, cudaStream_t s);
 int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res, cudaStream_t s);
 int cg_alloc(spf_plan* P);
+int cg_objective(spf_plan* P, const float* khat, const float* rhs, const float* x, const float* x0,
+                 const double* b2, double* out, cudaStream_t s);
+int weighted_sumsq(spf_plan* P, const float* img, int64_t n, int P2, const float* D, float scale,
+                   double* out, int accumulate, cudaStream_t s);
 // match.cu / match_tc.cu
 int simt_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
                 cudaStream_t s);
 int row_norms(const float* src, int rows, int P2, float scale, float* out, cudaStream_t s);
+int row_norms_w(const float* src, int rows, int P2, float scale, const float* w, float* out,
+                cudaStream_t s);
+int set_mask_weights(spf_matcher* m, const float* D, cudaStream_t s);
 int state_reset(spf_matcher* m, cudaStream_t s);
 int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
                   cudaStream_t s);
@@ -118,8 +130,8 @@ static int plan_init(spf_plan* P) {
   P->radians_per_q = 2.0 * M_PI * dr;
   int nf = fine_size(N, P->w);
   int nfT = fine_size(2 * N - 1, P->w);
-  SPF_TRY(grid_init(&P->g, N, nf, nf * dr, P->w, P->beta, P->max_points));
-  SPF_TRY(grid_init(&P->gT, 2 * N - 1, nfT, nfT * dr, P->w, P->beta, P->max_points));
+  SPF_TRY(grid_init(&P->g, N, nf, nf * dr, P->w, P->beta, P->max_points, true));
+  SPF_TRY(grid_init(&P->gT, 2 * N - 1, nfT, nfT * dr, P->w, P->beta, P->max_points, false));
   P->PT = smooth_even_at_least(2 * N - 1);
   size_t PT3 = (size_t)P->PT * P->PT * P->PT;
   SPF_TRY(dev_alloc((void**)&P->cubeP, sizeof(float2) * PT3, "Toeplitz cube"));
@@ -307,6 +319,27 @@ int spf_cg_merge_step(spf_plan* plan, const float* kernel_hat, double lambda, fl
   return cg_step(plan, kernel_hat, lambda, x, res_norm, as_stream(stream));
 }
 
+int spf_cg_objective(spf_plan* plan, const float* kernel_hat, const float* rhs, const float* x,
+                     const float* x0, const double* b_norm2, double* out, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_CHECK_ARG(kernel_hat && rhs && x && x0 && out, "NULL pointer");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return cg_objective(plan, kernel_hat, rhs, x, x0, b_norm2, out, as_stream(stream));
+}
+
+int spf_weighted_sumsq(spf_plan* plan, const float* images, int n_img, int P2, const float* D,
+                       float scale, double* out, int accumulate, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_CHECK_ARG(n_img >= 0 && P2 > 0 && out && (n_img == 0 || images), "bad arguments");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return weighted_sumsq(plan, images, (int64_t)n_img * P2, P2, D, scale, out, accumulate,
+                        as_stream(stream));
+}
+
 int spf_toeplitz_apply(spf_plan* plan, const float* kernel_hat, double lambda, const float* x,
                        float* out, void* stream) {
   clear_error();
@@ -331,6 +364,7 @@ static void matcher_free(spf_matcher* m) {
   cudaFree(m->st_d);
   cudaFree(m->st_i);
   cudaFree(m->err);
+  cudaFree(m->wbuf);
   delete m;
 }
 
@@ -364,6 +398,7 @@ int spf_matcher_create(spf_matcher** out, int max_images, int max_orient_chunk, 
   A((void**)&m->st_d, sizeof(float) * (size_t)max_images * topk, "running list");
   A((void**)&m->st_i, sizeof(int) * (size_t)max_images * topk, "running list");
   A((void**)&m->err, sizeof(int), "error word");
+  A((void**)&m->wbuf, sizeof(float) * P2, "pixel weights");
   if (rc == SPF_OK && precision != SPF_FP32) {
     if (!match_tc_supported(device)) {
       set_error("tensor-core matching needs an sm_103 device");
@@ -425,6 +460,14 @@ int spf_matcher_status(spf_matcher* m) {
   return SPF_OK;
 }
 
+int spf_matcher_set_mask(spf_matcher* m, const float* D, void* stream) {
+  clear_error();
+  SPF_CHECK_ARG(m != nullptr, "matcher is NULL");
+  DeviceScope dev(m->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return set_mask_weights(m, D, as_stream(stream));
+}
+
 int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float img_scale,
                            void* stream) {
   clear_error();
@@ -439,7 +482,7 @@ int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float
   m->n_img = n_img;
   m->img_scale = img_scale;
   if (m->precision == SPF_FP32)
-    SPF_TRY(row_norms(images, n_img, m->P2, img_scale, m->x2, s));
+    SPF_TRY(row_norms_w(images, n_img, m->P2, img_scale, m->wsq, m->x2, s));
   else
     SPF_TRY(quantize_rows(m, images, n_img, img_scale, m->xq, m->xs, m->x2, s));
   return state_reset(m, s);
@@ -467,7 +510,7 @@ int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient, in
   cudaStream_t s = as_stream(stream);
   int nsplit;
   if (m->precision == SPF_FP32) {
-    SPF_TRY(row_norms(slices, n_orient, m->P2, 1.f, m->y2, s));
+    SPF_TRY(row_norms_w(slices, n_orient, m->P2, 1.f, m->wsq, m->y2, s));
     nsplit = choose_splits(m, n_orient, 128, 128);
     SPF_TRY(simt_launch(m, slices, n_orient, orient_offset, nsplit, s));
   } else {
@@ -494,6 +537,110 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
   SPF_TRY(spf_matcher_set_images(m, images, n_img, img_scale, stream));
   SPF_TRY(spf_matcher_add_slices(m, slices, n_orient, 0, stream));
   return spf_matcher_results(m, best_idx, best_d, second_d, nullptr, nullptr, stream);
+}
+
+// ------------------------------------------------------------ point sets --
+static void points_free(spf_points* S) {
+  if (!S) return;
+  cudaFree(S->quats);
+  cudaFree(S->qlab);
+  cudaFree(S->setN.ids);
+  cudaFree(S->setN.subs);
+  cudaFree(S->setN.nsubs);
+  cudaFree(S->setT.ids);
+  cudaFree(S->setT.subs);
+  cudaFree(S->setT.nsubs);
+  cudaFree(S->cls);
+  cudaFree(S->cnt);
+  delete S;
+}
+
+int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int M, const float* q_lab,
+                      int P2, void* stream) {
+  clear_error();
+  SPF_CHECK_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  SPF_TRY(check_plan(plan));
+  SPF_CHECK_ARG(M >= 0 && P2 > 0, "M >= 0 and P2 > 0 required");
+  SPF_CHECK_ARG((int64_t)M * P2 <= 0x7fffffffLL, "M*P2 must be < 2^31");
+  SPF_CHECK_ARG(q_lab && (M == 0 || quats), "NULL pointer");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  spf_points* S = new spf_points();
+  S->plan = plan;
+  S->device = plan->device;
+  S->M = M;
+  S->P2 = P2;
+  const int64_t npts = (int64_t)M * P2;
+  int rc = SPF_OK;
+  auto A = [&](void** p, size_t b, const char* w) {
+    if (rc == SPF_OK) rc = dev_alloc(p, b, w);
+  };
+  A((void**)&S->quats, sizeof(float) * 4 * std::max(M, 1), "point-set orientations");
+  A((void**)&S->qlab, sizeof(float) * 3 * P2, "point-set q-points");
+  S->setN.max_subs = plan->g.bins.nbins + npts / kSubPts + 1;
+  S->setT.max_subs = plan->gT.bins.nbins + npts / kSubPts + 1;
+  A((void**)&S->setN.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
+  A((void**)&S->setN.subs, sizeof(int4) * S->setN.max_subs, "subproblems");
+  A((void**)&S->setN.nsubs, 2 * sizeof(int), "subproblem count");
+  A((void**)&S->setT.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
+  A((void**)&S->setT.subs, sizeof(int4) * S->setT.max_subs, "subproblems");
+  A((void**)&S->setT.nsubs, 2 * sizeof(int), "subproblem count");
+  A((void**)&S->cls, sizeof(float) * std::max<int64_t>(npts, 1), "class sums");
+  A((void**)&S->cnt, sizeof(float) * std::max(M, 1), "class counts");
+  if (rc != SPF_OK) {
+    points_free(S);
+    return rc;
+  }
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaSuccess;
+  if (M > 0) e = cudaMemcpyAsync(S->quats, quats, sizeof(float) * 4 * M, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->qlab, q_lab, sizeof(float) * 3 * P2, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) {
+    set_error("copy of the point set: %s", cudaGetErrorString(e));
+    points_free(S);
+    return SPF_ERR_CUDA;
+  }
+  rc = points_build(plan, S, s);
+  if (rc != SPF_OK) {
+    points_free(S);
+    return rc;
+  }
+  *out = S;
+  return SPF_OK;
+}
+
+int spf_points_destroy(spf_points* pts) {
+  clear_error();
+  if (!pts) return SPF_OK;
+  DeviceScope dev(pts->device);
+  cudaDeviceSynchronize();
+  points_free(pts);
+  return SPF_OK;
+}
+
+int spf_slice_points(spf_plan* plan, spf_points* pts, const float* A, float* slices, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_CHECK_ARG(pts && pts->plan == plan, "point set is NULL or belongs to another plan");
+  SPF_CHECK_ARG(A && (pts->M == 0 || slices), "NULL pointer");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return slice_points(plan, pts, A, slices, as_stream(stream));
+}
+
+int spf_merge_points(spf_plan* plan, spf_points* pts, const float* images, const int32_t* orient_idx,
+                     int n_img, int orient_offset, const float* D, float b_scale, float* rhs,
+                     float* kernel_hat, int accumulate, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_CHECK_ARG(pts && pts->plan == plan, "point set is NULL or belongs to another plan");
+  SPF_CHECK_ARG(n_img >= 0 && (n_img == 0 || (images && orient_idx)), "NULL pointer");
+  SPF_CHECK_ARG(rhs || kernel_hat, "rhs and kernel_hat are both NULL");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return merge_points(plan, pts, images, orient_idx, n_img, orient_offset, D, b_scale, rhs, kernel_hat,
+                      accumulate, as_stream(stream));
 }
 
 }  // extern "C"

@@ -142,6 +142,68 @@ __global__ void cg_dir_kernel(const float* __restrict__ r, float* __restrict__ p
     p[i] = fmaf(beta, p[i], r[i]);
 }
 
+// Per-block partials of x.Tx, x.rhs and |x - x0|^2 (FP64).
+__global__ void objective_kernel(const float* __restrict__ x, const float* __restrict__ Tx,
+                                 const float* __restrict__ rhs, const float* __restrict__ x0, int64_t n,
+                                 double* __restrict__ part) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double xv = x[i];
+    a += xv * (double)Tx[i];
+    b += xv * (double)rhs[i];
+    const double d = xv - (double)x0[i];
+    c += d * d;
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  c = block_sum(c);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+  }
+}
+
+// out[0] = xTx - 2 x.rhs + b2[0], out[1] = |x - x0|^2.
+__global__ void objective_finalize_kernel(const double* __restrict__ part, int nparts,
+                                          const double* __restrict__ b2, double* __restrict__ out) {
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    a += part[3 * i];
+    b += part[3 * i + 1];
+    c += part[3 * i + 2];
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  c = block_sum(c);
+  if (threadIdx.x == 0) {
+    out[0] = a - 2.0 * b + (b2 ? b2[0] : 0.0);
+    out[1] = c;
+  }
+}
+
+// out (+)= sum_{i,p} D[p] (scale img[i,p])^2, FP64, per-block partials then one block.
+__global__ void wsumsq_kernel(const float* __restrict__ img, int64_t n, int P2, const float* __restrict__ D,
+                              float scale, double* __restrict__ part) {
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)scale * (double)img[i];
+    a += (D ? (double)D[i % P2] : 1.0) * v * v;
+  }
+  a = block_sum(a);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+__global__ void wsumsq_finalize_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out,
+                                       int accumulate) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += part[i];
+  a = block_sum(a);
+  if (threadIdx.x == 0) out[0] = accumulate ? out[0] + a : a;
+}
+
 int grid_for(int64_t n) { return (int)std::min<int64_t>(ceil_div(n, 256), 152 * 32); }
 
 }  // namespace
@@ -191,4 +253,28 @@ int cg_alloc(spf_plan* P) {
   return SPF_OK;
 }
 
+}  // namespace spf
+
+namespace spf {
+int cg_objective(spf_plan* P, const float* khat, const float* rhs, const float* x, const float* x0,
+                 const double* b2, double* out, cudaStream_t s) {
+  const int64_t n3 = (int64_t)P->N * P->N * P->N;
+  SPF_TRY(toeplitz_apply(P, khat, 0.0, x, P->cg_Ap, nullptr, s));
+  SPF_TRY(launch("objective_kernel", s, [&] {
+    objective_kernel<<<kRedBlocks / 3, kRedThreads, 0, s>>>(x, P->cg_Ap, rhs, x0, n3, P->cg_part);
+  }));
+  return launch("objective_finalize_kernel", s, [&] {
+    objective_finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks / 3, b2, out);
+  });
+}
+
+int weighted_sumsq(spf_plan* P, const float* img, int64_t n, int P2, const float* D, float scale,
+                   double* out, int accumulate, cudaStream_t s) {
+  SPF_TRY(launch("wsumsq_kernel", s, [&] {
+    wsumsq_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(img, n, P2, D, scale, P->cg_part);
+  }));
+  return launch("wsumsq_finalize_kernel", s, [&] {
+    wsumsq_finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks, out, accumulate);
+  });
+}
 }  // namespace spf

@@ -25,13 +25,13 @@ namespace {
 // out[r] = |scale * src_r|^2, one warp per row: four FP32 partial sums per
 // lane, combined across the warp in FP64.
 __global__ void row_norms_kernel(const float* __restrict__ src, int rows, int P2, float scale,
-                                 float* __restrict__ out) {
+                                 const float* __restrict__ w, float* __restrict__ out) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= rows) return;
   const float* row = src + (size_t)warp * P2;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  const bool vec = (P2 % 4) == 0 && (((uintptr_t)row) & 15) == 0;
+  const bool vec = !w && (P2 % 4) == 0 && (((uintptr_t)row) & 15) == 0;
   if (vec) {
     const float4* r4 = reinterpret_cast<const float4*>(row);
     for (int p = lane; p < P2 / 4; p += 32) {
@@ -44,6 +44,7 @@ __global__ void row_norms_kernel(const float* __restrict__ src, int rows, int P2
   } else {
     for (int p = lane; p < P2; p += 32) {
       float v = __ldg(row + p);
+      if (w) v *= __ldg(w + p);
       a0 = fmaf(v, v, a0);
     }
   }
@@ -58,6 +59,11 @@ __global__ void state_reset_kernel(float* __restrict__ d, int* __restrict__ idx,
     d[i] = FLT_MAX;
     idx[i] = -1;
   }
+}
+
+__global__ void sqrt_weights_kernel(const float* __restrict__ D, int n, float* __restrict__ w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = sqrtf(fmaxf(D[i], 0.f));
 }
 
 // Insert (s, j) into an ascending list of K entries; equal scores keep the
@@ -121,7 +127,7 @@ constexpr int BM = 128, BN = 128, BK = 8;
 
 template <bool VEC>
 __device__ __forceinline__ void simt_load(const float* __restrict__ X, int rows, int P2, int r0, int k0,
-                                          float scale, float (&v)[4]) {
+                                          float scale, const float* __restrict__ w, float (&v)[4]) {
   const int t = threadIdx.x;
   const int row = r0 + (t >> 1), k = k0 + (t & 1) * 4;
   if (VEC) {
@@ -136,13 +142,18 @@ __device__ __forceinline__ void simt_load(const float* __restrict__ X, int rows,
     for (int e = 0; e < 4; ++e)
       v[e] = (row < rows && k + e < P2) ? scale * __ldg(X + (size_t)row * P2 + k + e) : 0.f;
   }
+  if (w) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] *= (k + e < P2) ? __ldg(w + k + e) : 0.f;
+  }
 }
 
 template <bool VEC>
 __global__ void __launch_bounds__(256, 2)
 simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const float* __restrict__ Y,
                   int n_orient, int orient_offset, int P2, const float* __restrict__ y2,
-                  int tiles_per_split, float* __restrict__ cand_v, int* __restrict__ cand_i) {
+                  int tiles_per_split, const float* __restrict__ wsq, float* __restrict__ cand_v,
+                  int* __restrict__ cand_i) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   float* As = smem;                        // [2][BK][BM]
@@ -172,8 +183,8 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
 #pragma unroll
       for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
     float ra[4], rb[4];
-    simt_load<VEC>(X, n_img, P2, i0, 0, xscale, ra);
-    simt_load<VEC>(Y, n_orient, P2, j0, 0, 1.f, rb);
+    simt_load<VEC>(X, n_img, P2, i0, 0, xscale, wsq, ra);
+    simt_load<VEC>(Y, n_orient, P2, j0, 0, 1.f, wsq, rb);
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -185,8 +196,8 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
     for (int k0 = 0; k0 < P2; k0 += BK) {
       const bool more = k0 + BK < P2;
       if (more) {
-        simt_load<VEC>(X, n_img, P2, i0, k0 + BK, xscale, ra);
-        simt_load<VEC>(Y, n_orient, P2, j0, k0 + BK, 1.f, rb);
+        simt_load<VEC>(X, n_img, P2, i0, k0 + BK, xscale, wsq, ra);
+        simt_load<VEC>(Y, n_orient, P2, j0, k0 + BK, 1.f, wsq, rb);
       }
       const float* A = As + buf * BK * BM;
       const float* B = Bs + buf * BK * BN;
@@ -262,7 +273,8 @@ template <int K>
 __global__ void __launch_bounds__(256)
 rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict__ Y, int P2,
               int orient_offset, int n_orient, int nsplit, const float* __restrict__ cand_v,
-              const int* __restrict__ cand_i, float* __restrict__ st_d, int* __restrict__ st_i) {
+              const int* __restrict__ cand_i, const float* __restrict__ wsq, float* __restrict__ st_d,
+              int* __restrict__ st_i) {
   const int img = blockIdx.x;
   __shared__ float s_v[K];
   __shared__ int s_i[K];
@@ -295,7 +307,7 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
   float acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.f;
-  bool vec = (P2 % 4) == 0 && (((uintptr_t)x) & 15) == 0 && (((uintptr_t)Y) & 15) == 0;
+  bool vec = !wsq && (P2 % 4) == 0 && (((uintptr_t)x) & 15) == 0 && (((uintptr_t)Y) & 15) == 0;
   if (vec) {
     for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
       float4 xv = __ldg(reinterpret_cast<const float4*>(x) + p);
@@ -310,9 +322,10 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
   } else {
     for (int p = threadIdx.x; p < P2; p += blockDim.x) {
       float xv = xscale * __ldg(x + p);
+      const float wp = wsq ? __ldg(wsq + p) : 1.f;
 #pragma unroll
       for (int q = 0; q < K; ++q) {
-        float d = xv - __ldg(y[q] + p);
+        float d = (xv - __ldg(y[q] + p)) * wp;
         acc[q] = fmaf(d, d, acc[q]);
       }
     }
@@ -379,22 +392,31 @@ int simt_launch(spf_matcher* m, const float* slices, int n_orient, int orient_of
                                   (int)smem));
     return launch("simt_match_kernel", s, [&] {
       simt_match_kernel<true><<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient,
-                                                      orient_offset, m->P2, m->y2, tps, m->cand_v,
-                                                      m->cand_i);
+                                                      orient_offset, m->P2, m->y2, tps, m->wsq,
+                                                      m->cand_v, m->cand_i);
     });
   }
   SPF_CUDA(cudaFuncSetAttribute(simt_match_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   return launch("simt_match_kernel", s, [&] {
     simt_match_kernel<false><<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient,
-                                                     orient_offset, m->P2, m->y2, tps, m->cand_v,
-                                                     m->cand_i);
+                                                     orient_offset, m->P2, m->y2, tps, m->wsq,
+                                                     m->cand_v, m->cand_i);
   });
+}
+
+int row_norms_w(const float* src, int rows, int P2, float scale, const float* w, float* out,
+                cudaStream_t s) {
+  if (rows == 0) return SPF_OK;
+  SPF_TRY(launch("row_norms_kernel", s, [&] {
+    row_norms_kernel<<<(unsigned)ceil_div(rows, 8), 256, 0, s>>>(src, rows, P2, scale, w, out);
+  }));
+  return SPF_OK;
 }
 
 int row_norms(const float* src, int rows, int P2, float scale, float* out, cudaStream_t s) {
   if (rows == 0) return SPF_OK;
-  SPF_TRY(launch("row_norms_kernel", s, [&] { row_norms_kernel<<<(unsigned)ceil_div(rows, 8), 256, 0, s>>>(src, rows, P2, scale, out); }));
+  SPF_TRY(row_norms_w(src, rows, P2, scale, nullptr, out, s));
   return SPF_OK;
 }
 
@@ -413,7 +435,7 @@ int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_
     return launch("rerank_kernel", s, [&] {                                                     \
       rerank_kernel<K><<<m->n_img, 256, 0, s>>>(m->images, m->img_scale, slices, m->P2,         \
                                                 orient_offset, n_orient, nsplit, m->cand_v,     \
-                                                m->cand_i, m->st_d, m->st_i);                   \
+                                                m->cand_i, m->wsq, m->st_d, m->st_i);           \
     });
   switch (m->topk) {
     SPF_RR(2) SPF_RR(3) SPF_RR(4) SPF_RR(5) SPF_RR(6) SPF_RR(7) SPF_RR(8)
@@ -430,4 +452,18 @@ int results_launch(spf_matcher* m, int32_t* best_idx, float* best_d, float* seco
   return SPF_OK;
 }
 
+}  // namespace spf
+
+namespace spf {
+int set_mask_weights(spf_matcher* m, const float* D, cudaStream_t s) {
+  if (!D) {
+    m->wsq = nullptr;
+    return SPF_OK;
+  }
+  SPF_TRY(launch("sqrt_weights_kernel", s, [&] {
+    sqrt_weights_kernel<<<(unsigned)ceil_div(m->P2, 256), 256, 0, s>>>(D, m->P2, m->wbuf);
+  }));
+  m->wsq = m->wbuf;
+  return SPF_OK;
+}
 }  // namespace spf

@@ -25,6 +25,8 @@ struct spf_matcher {
   float* st_d = nullptr;          // max_images x topk exact distances (running)
   int* st_i = nullptr;            // max_images x topk indices
   int* err = nullptr;             // device error word (bounded waits, bounds)
+  float* wbuf = nullptr;          // P2 square roots of the pixel weights (allocated at create)
+  const float* wsq = nullptr;     // == wbuf when a weight mask is set, else nullptr
   int n_sms = 152;
 };
 

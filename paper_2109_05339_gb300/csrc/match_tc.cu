@@ -44,13 +44,14 @@ __device__ __forceinline__ float block_sum_f64(double v, double* sh) {
 // and the FP32 squared norms of the scaled rows, one CTA per row.
 __global__ void __launch_bounds__(256) quantize_bf16_kernel(const float* __restrict__ src, int P2,
                                                             int Kpad, float scale,
+                                                            const float* __restrict__ w,
                                                             __nv_bfloat16* __restrict__ dst,
                                                             float* __restrict__ norms) {
   const int r = blockIdx.x;
   const float* row = src + (size_t)r * P2;
   __nv_bfloat16* out = dst + (size_t)r * Kpad;
   float a0 = 0.f, a1 = 0.f;
-  if ((P2 % 4) == 0 && (((uintptr_t)row) & 15) == 0) {
+  if (!w && (P2 % 4) == 0 && (((uintptr_t)row) & 15) == 0) {
     for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
       float4 v = __ldg(reinterpret_cast<const float4*>(row) + p);
       v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(256) quantize_bf16_kernel(const float* __restr
   } else {
     for (int p = threadIdx.x; p < P2; p += blockDim.x) {
       float v = scale * __ldg(row + p);
+      if (w) v *= __ldg(w + p);
       a0 = fmaf(v, v, a0);
       out[p] = __float2bfloat16_rn(v);
     }
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(256) quantize_bf16_kernel(const float* __restr
 // squared norms of the scaled rows. One CTA per row.
 __global__ void __launch_bounds__(256) quantize_fp8_kernel(const float* __restrict__ src, int P2,
                                                            int Kpad, float scale,
+                                                           const float* __restrict__ w,
                                                            __nv_fp8_e4m3* __restrict__ dst,
                                                            float* __restrict__ row_scale,
                                                            float* __restrict__ norms) {
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(256) quantize_fp8_kernel(const float* __restri
   float mx = 0.f, a0 = 0.f;
   for (int k = threadIdx.x; k < P2; k += blockDim.x) {
     float v = scale * __ldg(row + k);
+    if (w) v *= __ldg(w + k);
     mx = fmaxf(mx, fabsf(v));
     a0 = fmaf(v, v, a0);
   }
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(256) quantize_fp8_kernel(const float* __restri
   __syncthreads();
   const float inv = 1.f / sm[0];
   for (int k = threadIdx.x; k < P2; k += blockDim.x)
-    dst[(size_t)r * Kpad + k] = __nv_fp8_e4m3(scale * __ldg(row + k) * inv);
+    dst[(size_t)r * Kpad + k] = __nv_fp8_e4m3(scale * __ldg(row + k) * (w ? __ldg(w + k) : 1.f) * inv);
 }
 
 }  // namespace
@@ -121,12 +125,12 @@ int quantize_rows(spf_matcher* m, const float* src, int rows, float scale, void*
   if (rows == 0) return SPF_OK;
   if (m->precision == SPF_BF16) {
     return launch("quantize_bf16_kernel", s, [&] {
-      quantize_bf16_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale,
+      quantize_bf16_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
                                                 static_cast<__nv_bfloat16*>(dst), norms);
     });
   }
   return launch("quantize_fp8_kernel", s, [&] {
-    quantize_fp8_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale,
+    quantize_fp8_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
                                              static_cast<__nv_fp8_e4m3*>(dst), scales, norms);
   });
 }

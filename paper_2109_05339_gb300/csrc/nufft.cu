@@ -31,19 +31,40 @@ namespace spf {
 namespace {
 
 // ------------------------------------------------------------ points ------
-// Fine-grid coordinate u = t * n_f / (2 pi) of a point, unwrapped, |u| < n_f/2
-// for rotated detector points. Explicit rounding intrinsics keep the value
-// bit-identical in every kernel that recomputes it (binning, spreading).
+// Division of point ids (< 2^31) by the pixel count, by multiplication with
+// a precomputed reciprocal (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, q = (umulhi(n, m) + n) >> l; n + umulhi
+// stays below 2^32 because n < 2^31.
+struct FastDiv {
+  uint32_t d = 1, m = 1, l = 0;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t d_) : d(d_) {
+    l = 0;
+    while ((1ull << l) < d) ++l;
+    m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, m) + n) >> l; }
+};
+
+// Fine-grid coordinate u = t * n_f / (2 pi) of a point, folded into
+// [-n_f/2, n_f/2] (a no-op for unit quaternions, |t| < pi; it keeps every
+// index in range for any input). Explicit rounding intrinsics keep the value
+// bit-identical in every kernel that recomputes it (sorting, spreading).
 struct QuatPts {
   const float4* quats;   // (w, x, y, z) per orientation
   const float* qlab;     // P2 x 3
-  uint32_t P2;
+  FastDiv P2;
   float scale;           // fine-grid cells per unit q
   const int* oidx;       // optional orientation index per row (merge)
   int nq;                // rows of quats when oidx is given
   int* err;
+  float nf, inv_nf;
+  __device__ __forceinline__ float fold(float u) const {
+    return __fsub_rn(u, __fmul_rn(nf, rintf(__fmul_rn(u, inv_nf))));
+  }
   __device__ __forceinline__ float3 operator()(uint32_t id) const {
-    uint32_t j = id / P2, p = id - j * P2;
+    uint32_t j = P2.div(id), p = id - j * P2.d;
     if (oidx) {
       int o = __ldg(oidx + j);
       if (o < 0 || o >= nq) {
@@ -64,7 +85,7 @@ struct QuatPts {
     float ux = __fmaf_rn(r00, qx, __fmaf_rn(r01, qy, __fmul_rn(r02, qz)));
     float uy = __fmaf_rn(r10, qx, __fmaf_rn(r11, qy, __fmul_rn(r12, qz)));
     float uz = __fmaf_rn(r20, qx, __fmaf_rn(r21, qy, __fmul_rn(r22, qz)));
-    return make_float3(__fmul_rn(ux, scale), __fmul_rn(uy, scale), __fmul_rn(uz, scale));
+    return make_float3(fold(__fmul_rn(ux, scale)), fold(__fmul_rn(uy, scale)), fold(__fmul_rn(uz, scale)));
   }
 };
 
@@ -91,18 +112,29 @@ struct StrPtr {
 struct StrImage {      // D[p] * scale * image[id]
   const float* img;
   const float* D;
-  uint32_t P2;
+  FastDiv P2;
   float scale;
   __device__ __forceinline__ float operator()(uint32_t id) const {
     float v = scale * __ldg(img + id);
-    return D ? v * __ldg(D + (id % P2)) : v;
+    return D ? v * __ldg(D + (id - P2.div(id) * P2.d)) : v;
   }
 };
 struct StrWeights {    // D[p] (ones if D is NULL)
   const float* D;
-  uint32_t P2;
+  FastDiv P2;
   __device__ __forceinline__ float operator()(uint32_t id) const {
-    return D ? __ldg(D + (id % P2)) : 1.f;
+    return D ? __ldg(D + (id - P2.div(id) * P2.d)) : 1.f;
+  }
+};
+
+struct StrCount {     // D[p] * count[j] for point id = j * P2 + p
+  const float* cnt;
+  const float* D;
+  FastDiv P2;
+  __device__ __forceinline__ float operator()(uint32_t id) const {
+    const uint32_t j = P2.div(id);
+    const float c = __ldg(cnt + j);
+    return D ? c * __ldg(D + (id - j * P2.d)) : c;
   }
 };
 
@@ -110,6 +142,9 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
 }
+
+// Wrap for arguments known to lie in [-n, 2n): one correction, no division.
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // ES weights of the W cells l0 .. l0+W-1 nearest to u (l0 = ceil(u - W/2)).
 template <int W>
@@ -120,7 +155,7 @@ __device__ __forceinline__ int es_weights(float u, float beta, float* wt) {
   for (int d = 0; d < W; ++d) {
     float z = ((float)(l0 + d) - u) * s;
     float r = fmaxf(0.f, 1.f - z * z);
-    wt[d] = expf(beta * (sqrtf(r) - 1.f));
+    wt[d] = __expf(beta * (sqrtf(r) - 1.f));
   }
   return l0;
 }
@@ -154,9 +189,9 @@ struct SortGeom {
 template <int W>
 __device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
   constexpr int H = W / 2;
-  int cx = wrap_index((int)ceilf(u.x - 0.5f * W) + H, g.nf);
-  int cy = wrap_index((int)ceilf(u.y - 0.5f * W) + H, g.nf);
-  int cz = wrap_index((int)ceilf(u.z - 0.5f * W) + H, g.nf);
+  int cx = wrap1((int)ceilf(u.x - 0.5f * W) + H, g.nf);
+  int cy = wrap1((int)ceilf(u.y - 0.5f * W) + H, g.nf);
+  int cz = wrap1((int)ceilf(u.z - 0.5f * W) + H, g.nf);
   constexpr int B = kBinLog, M = kBin - 1;
   int bin = ((cz >> B) * g.nb1 + (cy >> B)) * g.nb0 + (cx >> B);
   return (bin << (3 * B)) | ((cz & M) << (2 * B)) | ((cy & M) << B) | (cx & M);
@@ -303,18 +338,47 @@ __global__ void build_subs_kernel(const int* __restrict__ start, int nbins, int4
   for (int q = 0; q < k; ++q) subs[o + q] = make_int4(b, s0 + q * kSubPts, min(kSubPts, c - q * kSubPts), 0);
 }
 
+// Class sums: cls[j][p] += b_scale D[p] img[i][p] and cnt[j] += 1 for every
+// image i whose orientation index oidx[i] - off = j is in [0, M). One block
+// per (image, 1024-pixel chunk).
+__global__ void class_sum_kernel(const float* __restrict__ img, const int* __restrict__ oidx, int n_img,
+                                 int off, int M, int P2, const float* __restrict__ D, float b_scale,
+                                 float* __restrict__ cls, float* __restrict__ cnt) {
+  const int chunks = (P2 + 1023) / 1024;
+  const int i = blockIdx.x / chunks, c = blockIdx.x - i * chunks;
+  if (i >= n_img) return;
+  const int j = __ldg(oidx + i) - off;
+  if (j < 0 || j >= M) return;
+  const float* row = img + (size_t)i * P2;
+  float* dst = cls + (size_t)j * P2;
+  for (int p = c * 1024 + threadIdx.x; p < min(P2, (c + 1) * 1024); p += blockDim.x) {
+    float v = b_scale * __ldg(row + p);
+    if (D) v *= __ldg(D + p);
+    if (v != 0.f) atomicAdd(dst + p, v);
+  }
+  if (c == 0 && threadIdx.x == 0) atomicAdd(cnt + j, 1.f);
+}
+
 // ------------------------------------------------------------ type 2 ------
-// Halo copy: Gp[z][y][x] = G[(z - H) mod nf][(y - H) mod nf][(x - H) mod nf]
-// on (nf + W)^3, so every tap window of a wrapped point is contiguous.
-__global__ void halo_kernel(const float* __restrict__ G, int nf, int np, int H, float* __restrict__ Gp) {
-  const int64_t total = (int64_t)np * np * np;
+// Halo copies: four x-shifted periodic copies of G on np x np x npx cells,
+// Gq[k][z][y][x] = G[(z - H) mod nf][(y - H) mod nf][(x + k - H) mod nf],
+// np = nf + W, npx = np + 8 rounded up to 4. A tap row starting at halo x
+// lx is Gq[lx & 3][z][y][(lx & ~3) .. + 7]: two aligned float4 loads.
+__global__ void halo_kernel(const float* __restrict__ G, int nf, int np, int npx, int H,
+                            float* __restrict__ Gq) {
+  const int64_t per = (int64_t)np * np * npx;
+  const int64_t total = 4 * per;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % np), y = (int)((i / np) % np), z = (int)(i / ((int64_t)np * np));
-    const int gx = wrap_index(x - H, nf), gy = wrap_index(y - H, nf), gz = wrap_index(z - H, nf);
-    Gp[i] = G[((size_t)gz * nf + gy) * nf + gx];
+    const int k = (int)(i / per);
+    const int64_t r = i - k * per;
+    const int x = (int)(r % npx), y = (int)((r / npx) % np), z = (int)(r / ((int64_t)npx * np));
+    const int gx = wrap1(x + k - H, nf), gy = wrap1(y - H, nf), gz = wrap1(z - H, nf);
+    Gq[i] = G[((size_t)gz * nf + gy) * nf + gx];
   }
 }
+
+__host__ __device__ inline int halo_npx(int nf, int W) { return ((nf + W + 8) + 3) & ~3; }
 
 __device__ __forceinline__ float wrap_cells(float u, float nf) {
   u -= nf * floorf(u / nf);
@@ -323,11 +387,13 @@ __device__ __forceinline__ float wrap_cells(float u, float nf) {
 
 // c_j = sum over W^3 taps of G[l] phi phi phi, one thread per point, points
 // visited in sorted order when `sorted` is given. The point is wrapped into
-// [0, nf) and its window read from the halo copy with constant offsets.
+// [0, nf) and each of its W^2 tap rows is read from the halo copies as two
+// aligned float4 loads.
 template <int W, class Pts>
-__global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ Gp, int nf, Pts pts,
+__global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ Gq, int nf, Pts pts,
                                                      int64_t npts, const uint32_t* __restrict__ sorted,
                                                      float beta, float* __restrict__ out) {
+  static_assert(W <= 8, "two float4 per tap row");
   constexpr int H = W / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= npts) return;
@@ -337,23 +403,32 @@ __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G
   u.x = wrap_cells(u.x, fn);
   u.y = wrap_cells(u.y, fn);
   u.z = wrap_cells(u.z, fn);
-  float wx[W], wy[W], wz[W];
+  float wx[8], wy[W], wz[W];
   const int lx = es_weights<W>(u.x, beta, wx) + H;     // in [0, nf], halo frame
   const int ly = es_weights<W>(u.y, beta, wy) + H;
   const int lz = es_weights<W>(u.z, beta, wz) + H;
-  const int np = nf + W;
-  const float* base = Gp + ((size_t)lz * np + ly) * np + lx;
+#pragma unroll
+  for (int d = W; d < 8; ++d) wx[d] = 0.f;
+  const int np = nf + W, npx = halo_npx(nf, W);
+  const int k = lx & 3;
+  const float* base = Gq + (size_t)k * np * np * npx + ((size_t)lz * np + ly) * npx + (lx - k);
   float acc = 0.f;
 #pragma unroll
   for (int dz = 0; dz < W; ++dz) {
-    const float* plane = base + (size_t)dz * np * np;
+    const float* plane = base + (size_t)dz * np * npx;
     float accy = 0.f;
 #pragma unroll
     for (int dy = 0; dy < W; ++dy) {
-      const float* row = plane + dy * np;
-      float accx = 0.f;
-#pragma unroll
-      for (int dx = 0; dx < W; ++dx) accx = fmaf(__ldg(row + dx), wx[dx], accx);
+      const float4* row = reinterpret_cast<const float4*>(plane + dy * npx);
+      const float4 a = __ldg(row), b = __ldg(row + 1);
+      float accx = a.x * wx[0];
+      accx = fmaf(a.y, wx[1], accx);
+      accx = fmaf(a.z, wx[2], accx);
+      accx = fmaf(a.w, wx[3], accx);
+      accx = fmaf(b.x, wx[4], accx);
+      accx = fmaf(b.y, wx[5], accx);
+      accx = fmaf(b.z, wx[6], accx);
+      accx = fmaf(b.w, wx[7], accx);
       accy = fmaf(accx, wy[dy], accy);
     }
     acc = fmaf(accy, wz[dz], acc);
@@ -430,22 +505,26 @@ spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restri
       // stage: lane k prepares point base + k
       if (lane < nb) {
         const uint32_t id = __ldg(sorted + sub.y + base + lane);
-        const float3 u = pts(id);
         float v = str(id);
+        float* rec = stage + lane * C::REC;
+        if (v == 0.f) {                       // contributes nothing: skip its weights
+          rec[3] = 0.f;
+          goto staged;
+        }
+        {
+        const float3 u = pts(id);
         float wx[W], wy[W], wz[W];
         const int lx = es_weights<W>(u.x, beta, wx);
         const int ly = es_weights<W>(u.y, beta, wy);
         const int lz = es_weights<W>(u.z, beta, wz);
         // tap-origin cell, wrapped; its position inside the bin is the local origin
-        const int cx = wrap_index(lx + C::H, nf), cy = wrap_index(ly + C::H, nf),
-                  cz = wrap_index(lz + C::H, nf);
+        const int cx = wrap1(lx + C::H, nf), cy = wrap1(ly + C::H, nf), cz = wrap1(lz + C::H, nf);
         int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);
         if ((cx >> kBinLog) != bx || (cy >> kBinLog) != by || (cz >> kBinLog) != bz) {
           atomicOr(err, 1);   // cannot happen when sorting and spreading agree
           v = 0.f;
           ox = oy = oz = 0;
         }
-        float* rec = stage + lane * C::REC;
         rec[0] = __int_as_float(ox);
         rec[1] = __int_as_float(oy);
         rec[2] = __int_as_float(oz);
@@ -456,11 +535,14 @@ spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restri
           rec[12 + d] = d < W ? wx[d] : 0.f;
           rec[20 + d] = d < W ? wy[d] : 0.f;
         }
+        }
+      staged:;
       }
       __syncwarp();
       for (int k = 0; k < nb; ++k) {
         const float* rec = stage + k * C::REC;
         const int4 hdr = *reinterpret_cast<const int4*>(rec);
+        if (__int_as_float(hdr.w) == 0.f) continue;   // uniform: every lane reads record k
         const int key = hdr.x | (hdr.y << 4) | (hdr.z << 8);
         if (key != cur) {
           if (cur >= 0) flush_columns<W>(grid, cx0, cy0, cz0, r, dx, acc);
@@ -493,7 +575,7 @@ spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restri
       const float val = *p;
       if (val != 0.f) {
         *p = 0.f;
-        const int gx = wrap_index(ox + x, nf), gy = wrap_index(oy + y, nf), gz = wrap_index(oz + z, nf);
+        const int gx = wrap1(ox + x, nf), gy = wrap1(oy + y, nf), gz = wrap1(oz + z, nf);
         atomicAdd(out + ((size_t)gz * nf + gy) * nf + gx, val);
       }
     }
@@ -583,17 +665,26 @@ int interp_w(spf_plan* P, Pts pts, int64_t npts, bool use_sort, float* out, cuda
   });
 }
 
+// Sort the points of grid g into `set` and cut its bins into subproblems.
+template <int W, class Pts>
+int sort_and_cut(spf_plan* P, Grid& g, Pts pts, int64_t npts, SortedSet& set, int* err, cudaStream_t s) {
+  BinSort& b = g.bins;
+  SPF_TRY((sort_points<W, Pts>(g, set.ids, pts, npts, err, s)));
+  SPF_CUDA(cudaMemsetAsync(set.nsubs, 0, 2 * sizeof(int), s));
+  return launch("build_subs_kernel", s, [&] {
+    build_subs_kernel<<<(unsigned)ceil_div(b.nbins, 256), 256, 0, s>>>(b.start, b.nbins, set.subs,
+                                                                      set.max_subs, set.nsubs, err);
+  });
+}
+
+// Spread onto g.real (cleared first) the points of an already sorted set.
 template <int W, class Pts, class Str>
-int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cudaStream_t s) {
+int spread_sorted(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, const SortedSet& set, int* err,
+                  cudaStream_t s) {
   BinSort& b = g.bins;
   SPF_CUDA(cudaMemsetAsync(g.real, 0, sizeof(float) * (size_t)g.nf * g.nf * g.nf, s));
   if (npts == 0) return SPF_OK;
-  SPF_TRY((sort_points<W, Pts>(g, P->sorted, pts, npts, err, s)));
-  SPF_CUDA(cudaMemsetAsync(b.nsubs, 0, 2 * sizeof(int), s));
-  SPF_TRY(launch("build_subs_kernel", s, [&] {
-    build_subs_kernel<<<(unsigned)ceil_div(b.nbins, 256), 256, 0, s>>>(b.start, b.nbins, b.subs,
-                                                                      b.max_subs, b.nsubs, err);
-  }));
+  SPF_CUDA(cudaMemsetAsync(set.nsubs + 1, 0, sizeof(int), s));   // work cursor
   using C = SpreadCfg<W>;
   SPF_CUDA(cudaFuncSetAttribute(spread_kernel<W, Pts, Str>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)C::SMEM));
@@ -602,9 +693,16 @@ int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cud
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   return launch("spread_kernel", s, [&] {
-    spread_kernel<W, Pts, Str><<<sms, 32 * C::WARPS, C::SMEM, s>>>(pts, str, geom, beta, P->sorted,
-                                                                   b.subs, b.nsubs, g.real, err);
+    spread_kernel<W, Pts, Str><<<sms, 32 * C::WARPS, C::SMEM, s>>>(pts, str, geom, beta, set.ids,
+                                                                   set.subs, set.nsubs, g.real, err);
   });
+}
+
+template <int W, class Pts, class Str>
+int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cudaStream_t s) {
+  SortedSet set{P->sorted, g.bins.subs, g.bins.nsubs, g.bins.max_subs};
+  if (npts > 0) SPF_TRY((sort_and_cut<W, Pts>(P, g, pts, npts, set, err, s)));
+  return spread_sorted<W, Pts, Str>(P, g, pts, str, npts, set, err, s);
 }
 
 }  // namespace
@@ -626,10 +724,10 @@ int type2_setup(spf_plan* P, const float* A, cudaStream_t s) {
   SPF_TRY(launch("deconv_pad_kernel", s,
                  [&] { deconv_pad_kernel<<<grid_for(n3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); }));
   SPF_TRY(fft3_exec_ex(&g.fft, g.cube, nullptr, g.real, nullptr, -1, P->Mh + 1, 0, s));
-  const int np = g.nf + P->w;
-  const int64_t np3 = (int64_t)np * np * np;
+  const int np = g.nf + P->w, npx = halo_npx(g.nf, P->w);
+  const int64_t tot = 4 * (int64_t)np * np * npx;
   return launch("halo_kernel", s, [&] {
-    halo_kernel<<<grid_for(np3), 256, 0, s>>>(g.real, g.nf, np, P->w / 2, g.halo);
+    halo_kernel<<<grid_for(tot), 256, 0, s>>>(g.real, g.nf, np, npx, P->w / 2, g.halo);
   });
 }
 
@@ -639,14 +737,13 @@ int type2_quat(spf_plan* P, const float* quats, int M, const float* qlab, int P2
                cudaStream_t s) {
   const int64_t per = P->max_points / P2;
   if (per <= 0) {
-    QuatPts pts{reinterpret_cast<const float4*>(quats), qlab, (uint32_t)P2, P->g.cells_per_q, nullptr, 0, P->err};
+    QuatPts pts{reinterpret_cast<const float4*>(quats), qlab, FastDiv((uint32_t)P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
     SPF_W_SWITCH(P->w, SPF_TRY((interp_w<W, QuatPts>(P, pts, (int64_t)M * P2, false, out, s))));
     return SPF_OK;
   }
   for (int64_t j0 = 0; j0 < M; j0 += per) {
     const int m = (int)std::min<int64_t>(per, M - j0);
-    QuatPts pts{reinterpret_cast<const float4*>(quats) + j0, qlab, (uint32_t)P2, P->g.cells_per_q,
-                nullptr, 0, P->err};
+    QuatPts pts{reinterpret_cast<const float4*>(quats) + j0, qlab, FastDiv((uint32_t)P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
     float* o = out + j0 * P2;
     SPF_W_SWITCH(P->w, SPF_TRY((interp_w<W, QuatPts>(P, pts, (int64_t)m * P2, true, o, s))));
   }
@@ -662,24 +759,18 @@ int type2_explicit(spf_plan* P, const float* t, int64_t npts, float* out, cudaSt
 
 // Type-1 of `str` at the points onto grid g, then FFT and crop/deconvolve
 // into out (n_modes^3) when out is given.
+static int type1_finish(spf_plan* P, Grid& g, float* out, int accumulate, cudaStream_t s);
+
 template <class Pts, class Str>
 static int type1_run(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, float* out,
                      int accumulate, int* err, cudaStream_t s) {
   SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, Pts, Str>(P, g, pts, str, npts, err, s))));
-  int h = (g.n_modes + 1) / 2;
-  SPF_TRY(fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s));
-  if (out) {
-    int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
-    SPF_TRY(launch("crop_deconv_kernel", s, [&] {
-      crop_deconv_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, out, accumulate);
-    }));
-  }
-  return SPF_OK;
+  return type1_finish(P, g, out, accumulate, s);
 }
 
 int type1_quat(spf_plan* P, const float* g_vals, const float* quats, int M, const float* qlab,
                int P2, float* out, int accumulate, int* err, cudaStream_t s) {
-  QuatPts pts{reinterpret_cast<const float4*>(quats), qlab, (uint32_t)P2, P->g.cells_per_q, nullptr, 0, P->err};
+  QuatPts pts{reinterpret_cast<const float4*>(quats), qlab, FastDiv((uint32_t)P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
   return type1_run(P, P->g, pts, StrPtr{g_vals}, (int64_t)M * P2, out, accumulate, err, s);
 }
 
@@ -689,35 +780,117 @@ int type1_explicit(spf_plan* P, const float* v, const float* t, int64_t npts, fl
   return type1_run(P, P->g, pts, StrPtr{v}, npts, out, accumulate, err, s);
 }
 
+// FFT of the spread grid g.real, then real part and deconvolution into out.
+static int type1_finish(spf_plan* P, Grid& g, float* out, int accumulate, cudaStream_t s) {
+  int h = (g.n_modes + 1) / 2;
+  SPF_TRY(fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s));
+  int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
+  return launch("crop_deconv_kernel", s, [&] {
+    crop_deconv_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, out, accumulate);
+  });
+}
+
+// Toeplitz kernel from the spread T-grid: FFT, K(d) = Re, circulant
+// embedding, FFT, real part (+)-> kernel_hat.
+static int kernel_finish(spf_plan* P, float* kernel_hat, int accumulate, cudaStream_t s) {
+  Grid& g = P->gT;
+  int h = (g.n_modes + 1) / 2;
+  SPF_TRY(fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s));
+  int64_t PT3 = (int64_t)P->PT * P->PT * P->PT;
+  SPF_CUDA(cudaMemsetAsync(P->cubeP, 0, sizeof(float2) * PT3, s));
+  int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
+  SPF_TRY(launch("crop_embed_kernel", s, [&] {
+    crop_embed_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, P->PT, P->cubeP);
+  }));
+  SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, P->realP, nullptr, -1, P->N, 0, s));
+  return launch("accumulate_kernel", s, [&] {
+    accumulate_kernel<<<grid_for(PT3), 256, 0, s>>>(P->realP, kernel_hat, PT3, accumulate);
+  });
+}
+
 // Merge: RHS onto the N-mode grid, Toeplitz kernel onto the (2N-1)-mode grid.
-int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats,
-              const int* oidx, int n_img, const float* qlab, int P2, const float* D, float b_scale,
-              float* rhs, float* kernel_hat, int accumulate, int* err, cudaStream_t s) {
+int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats, const int* oidx,
+              int n_img, const float* qlab, int P2, const float* D, float b_scale, float* rhs,
+              float* kernel_hat, int accumulate, int* err, cudaStream_t s) {
   const float4* q4 = reinterpret_cast<const float4*>(quats);
   int64_t npts = (int64_t)n_img * P2;
   if (rhs) {
-    QuatPts pts{q4, qlab, (uint32_t)P2, P->g.cells_per_q, oidx, n_quats, err};
-    SPF_TRY(type1_run(P, P->g, pts, StrImage{images, D, (uint32_t)P2, b_scale}, npts, rhs,
-                      accumulate, err, s));
+    QuatPts pts{q4, qlab, FastDiv((uint32_t)P2), P->g.cells_per_q, oidx, n_quats, err, (float)P->g.nf, 1.f / (float)P->g.nf};
+    StrImage str{images, D, FastDiv((uint32_t)P2), b_scale};
+    SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, QuatPts, StrImage>(P, P->g, pts, str, npts, err, s))));
+    SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
   }
   if (kernel_hat) {
-    QuatPts pts{q4, qlab, (uint32_t)P2, P->gT.cells_per_q, oidx, n_quats, err};
-    SPF_TRY(type1_run(P, P->gT, pts, StrWeights{D, (uint32_t)P2}, npts, nullptr, 0, err, s));
-    // K(d) -> circulant embedding -> FFT -> real part (+)-> kernel_hat
-    int64_t PT3 = (int64_t)P->PT * P->PT * P->PT;
-    SPF_CUDA(cudaMemsetAsync(P->cubeP, 0, sizeof(float2) * PT3, s));
-    int64_t m3 = (int64_t)P->gT.n_modes * P->gT.n_modes * P->gT.n_modes;
-    SPF_TRY(launch("crop_embed_kernel", s, [&] { crop_embed_kernel<<<grid_for(m3), 256, 0, s>>>(P->gT.cube, P->gT.nf, P->gT.n_modes,
-                                                   P->gT.deconv, P->PT, P->cubeP); }));
-    SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, P->realP, nullptr, -1, P->N, 0, s));
-    SPF_TRY(launch("accumulate_kernel", s, [&] { accumulate_kernel<<<grid_for(PT3), 256, 0, s>>>(P->realP, kernel_hat, PT3, accumulate); }));
+    QuatPts pts{q4, qlab, FastDiv((uint32_t)P2), P->gT.cells_per_q, oidx, n_quats, err, (float)P->gT.nf, 1.f / (float)P->gT.nf};
+    StrWeights str{D, FastDiv((uint32_t)P2)};
+    SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, QuatPts, StrWeights>(P, P->gT, pts, str, npts, err, s))));
+    SPF_TRY(kernel_finish(P, kernel_hat, accumulate, s));
+  }
+  return SPF_OK;
+}
+
+// ------------------------------------------------------- point sets -------
+int points_build(spf_plan* P, spf_points* S, cudaStream_t s) {
+  const int64_t npts = (int64_t)S->M * S->P2;
+  if (npts == 0) return SPF_OK;
+  const float4* q4 = reinterpret_cast<const float4*>(S->quats);
+  QuatPts pn{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
+  SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->g, pn, npts, S->setN, P->err, s))));
+  QuatPts pt{q4, S->qlab, FastDiv((uint32_t)S->P2), P->gT.cells_per_q, nullptr, 0, P->err, (float)P->gT.nf, 1.f / (float)P->gT.nf};
+  SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->gT, pt, npts, S->setT, P->err, s))));
+  return SPF_OK;
+}
+
+int slice_points(spf_plan* P, spf_points* S, const float* A, float* out, cudaStream_t s) {
+  const int64_t npts = (int64_t)S->M * S->P2;
+  if (npts == 0) return SPF_OK;
+  SPF_TRY(type2_setup(P, A, s));
+  QuatPts pts{reinterpret_cast<const float4*>(S->quats), S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
+  const uint32_t* order = S->setN.ids;
+  const float beta = (float)P->beta;
+  Grid& g = P->g;
+  SPF_W_SWITCH(P->w, SPF_TRY(launch("interp_kernel", s, [&] {
+    interp_kernel<W, QuatPts><<<(unsigned)ceil_div(npts, 256), 256, 0, s>>>(g.halo, g.nf, pts, npts, order,
+                                                                           beta, out);
+  })));
+  return SPF_OK;
+}
+
+int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oidx, int n_img, int off,
+                 const float* D, float b_scale, float* rhs, float* kernel_hat, int accumulate,
+                 cudaStream_t s) {
+  const int64_t npts = (int64_t)S->M * S->P2;
+  SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)npts, s));
+  SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
+  if (n_img > 0) {
+    const int chunks = (int)ceil_div(S->P2, 1024);
+    const int64_t blocks = (int64_t)n_img * chunks;
+    SPF_TRY(launch("class_sum_kernel", s, [&] {
+      class_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(images, oidx, n_img, off, S->M, S->P2, D, b_scale,
+                                                        S->cls, S->cnt);
+    }));
+  }
+  const float4* q4 = reinterpret_cast<const float4*>(S->quats);
+  if (rhs) {
+    QuatPts pts{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
+    StrPtr str{S->cls};
+    SPF_W_SWITCH(P->w, SPF_TRY((spread_sorted<W, QuatPts, StrPtr>(P, P->g, pts, str, npts, S->setN,
+                                                                 P->err, s))));
+    SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
+  }
+  if (kernel_hat) {
+    QuatPts pts{q4, S->qlab, FastDiv((uint32_t)S->P2), P->gT.cells_per_q, nullptr, 0, P->err, (float)P->gT.nf, 1.f / (float)P->gT.nf};
+    StrCount str{S->cnt, D, FastDiv((uint32_t)S->P2)};
+    SPF_W_SWITCH(P->w, SPF_TRY((spread_sorted<W, QuatPts, StrCount>(P, P->gT, pts, str, npts, S->setT,
+                                                                   P->err, s))));
+    SPF_TRY(kernel_finish(P, kernel_hat, accumulate, s));
   }
   return SPF_OK;
 }
 
 // Allocation of one grid's buffers and bin-sort scratch.
 int grid_init(Grid* g, int n_modes, int nf, double cells_per_q, int w, double beta,
-              int64_t max_points) {
+              int64_t max_points, bool interp_source) {
   g->n_modes = n_modes;
   g->nf = nf;
   g->cells_per_q = (float)cells_per_q;
@@ -728,8 +901,10 @@ int grid_init(Grid* g, int n_modes, int nf, double cells_per_q, int w, double be
   SPF_CUDA(cudaMemcpy(g->deconv, pf.data(), sizeof(float) * n_modes, cudaMemcpyHostToDevice));
   size_t n3 = (size_t)nf * nf * nf;
   SPF_TRY(dev_alloc((void**)&g->real, sizeof(float) * n3, "fine grid"));
-  const size_t np = (size_t)nf + w;
-  SPF_TRY(dev_alloc((void**)&g->halo, sizeof(float) * np * np * np, "fine grid with halo"));
+  if (interp_source) {
+    const size_t np = (size_t)nf + w, npx = (size_t)halo_npx(nf, w);
+    SPF_TRY(dev_alloc((void**)&g->halo, sizeof(float) * 4 * np * np * npx, "shifted halo copies"));
+  }
   SPF_TRY(dev_alloc((void**)&g->cube, sizeof(float2) * n3, "fine cube"));
   SPF_TRY(fft3_create(&g->fft, nf, nf, nf));
   BinSort& b = g->bins;

@@ -34,10 +34,19 @@ struct Grid {
   float cells_per_q = 0.f;   // fine-grid cells per unit physical q
   float* deconv = nullptr;   // n_modes deconvolution factors p_k (device)
   float* real = nullptr;     // nf^3 real grid (spread target / type-2 FFT output)
-  float* halo = nullptr;     // (nf + w)^3 periodic copy of `real` with a w/2 halo (interp source)
+  float* halo = nullptr;     // 4 x-shifted periodic copies of `real` with a w/2 halo (interp source)
   float2* cube = nullptr;    // nf^3 complex work cube
   FFT3 fft;
   BinSort bins;
+};
+
+// A sorted point set of one grid: ids in sorted order, its subproblems, and
+// [count, work cursor] of the subproblem list.
+struct SortedSet {
+  uint32_t* ids = nullptr;
+  int4* subs = nullptr;
+  int* nsubs = nullptr;
+  int64_t max_subs = 0;
 };
 
 }  // namespace spf
@@ -64,6 +73,19 @@ struct spf_plan {
   double* cg_sc = nullptr;    // [rr, pAp, alpha, beta, rr_new, res]
   double* cg_part = nullptr;  // per-block partial sums
   int* err = nullptr;         // device error word (bit 1: point outside its bin)
+};
+
+// Orientations x pixels of a fixed orientation set, sorted once for both grids.
+struct spf_points {
+  spf_plan* plan = nullptr;
+  int device = 0;
+  int M = 0, P2 = 0;
+  float* quats = nullptr;     // M x 4 copy
+  float* qlab = nullptr;      // P2 x 3 copy
+  spf::SortedSet setN;        // N-mode grid (slicing, right-hand side)
+  spf::SortedSet setT;        // (2N-1)-mode grid (Toeplitz kernel)
+  float* cls = nullptr;       // M x P2 class sums of weighted images
+  float* cnt = nullptr;       // M class counts
 };
 
 namespace spf {

@@ -1,13 +1,17 @@
 """One slice -> match -> merge -> CG iteration of M-TIP on one GPU (Fig. 3
 without phasing), as a sequence of C-ABI calls.
 
+The reference orientations are fixed across iterations (Sec. II-A), so their
+rotated detector points are sorted once per orientation chunk (PointSet) and
+reused by every iteration's slicing and merge.
+
 1. Slicing (Sec. II-A) and matching (Sec. II-B), streamed in orientation
    chunks: each chunk of model images is sliced into one reusable buffer and
    matched against every image; the running top-k survives across chunks, so
-   no more than one chunk of slices is ever resident.
-2. Merging (Sec. II-C): type-1 right-hand side and Toeplitz kernel from the
-   matched orientations, accumulated over image chunks (linearity, the
-   paper's per-node type-1 sums followed by a reduction).
+   no more than one chunk of slices is resident.
+2. Merging (Sec. II-C): images are summed per matched orientation (class
+   sums) and the sums and class counts are spread at the fixed points; chunks
+   accumulate (linearity, the paper's per-node type-1 sums and reduction).
 3. ``cg_iters`` conjugate-gradient steps on Eq. 2 from x0 = current model,
    lambda = lam_rel * sum of the weights D over all merged pixels.
 """
@@ -15,7 +19,7 @@ from __future__ import annotations
 
 import torch
 
-from .api import Matcher, Plan
+from .api import Matcher, Plan, PointSet
 
 
 class MTIP:
@@ -33,24 +37,39 @@ class MTIP:
         self.khat = torch.empty((self.plan.PT,) * 3, dtype=torch.float32, device=dev)
         self.x = torch.empty((N,) * 3, dtype=torch.float32, device=dev)
         self.N, self.P2, self.n_img, self.n_orient = N, P2, n_img, n_orient
+        self.sets = None
+        self._key = None
 
-    def match(self, A, quats, q_lab, images, img_scale):
-        m = self.matcher
-        m.set_images(images, img_scale)
+    def set_orientations(self, quats, q_lab):
+        """Sort the points of every orientation chunk once (reused by later calls)."""
+        key = (quats.data_ptr(), tuple(quats.shape), q_lab.data_ptr(), tuple(q_lab.shape))
+        if self._key == key:
+            return
+        if self.sets:
+            for _, s in self.sets:
+                s.close()
+        self.sets = []
         M = quats.shape[0]
         for c0 in range(0, M, self.orient_chunk):
             c1 = min(M, c0 + self.orient_chunk)
-            sl = self.slices[: c1 - c0]
-            self.plan.slice_model(A, quats[c0:c1], q_lab, out=sl)
+            self.sets.append((c0, PointSet(self.plan, quats[c0:c1].contiguous(), q_lab)))
+        self._key = key
+
+    def match(self, A, quats, q_lab, images, img_scale):
+        self.set_orientations(quats, q_lab)
+        m = self.matcher
+        m.set_images(images, img_scale)
+        for c0, ps in self.sets:
+            sl = self.slices[: ps.M]
+            ps.slice(A, out=sl)
             m.add_slices(sl, orient_offset=c0)
         return m.results()
 
     def merge(self, images, quats, best, q_lab, img_scale, D=None):
-        n = images.shape[0]
-        for c0 in range(0, n, self.img_chunk):
-            c1 = min(n, c0 + self.img_chunk)
-            self.plan.merge_images(images[c0:c1], quats, q_lab, D=D, b_scale=img_scale, rhs=self.rhs,
-                                   kernel_hat=self.khat, accumulate=c0 > 0, orient_idx=best[c0:c1])
+        self.set_orientations(quats, q_lab)
+        for k, (c0, ps) in enumerate(self.sets):
+            ps.merge(images, best, orient_offset=c0, D=D, b_scale=img_scale, rhs=self.rhs,
+                     kernel_hat=self.khat, accumulate=k > 0)
         return self.rhs, self.khat
 
     def iteration(self, A, quats, q_lab, images, img_scale, cg_iters, lam_rel=1e-3, D=None,
@@ -64,5 +83,8 @@ class MTIP:
         return res, x, lam
 
     def close(self):
+        if self.sets:
+            for _, s in self.sets:
+                s.close()
         self.matcher.close()
         self.plan.close()

@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "Config", "CONFIGS", "Problem", "make_problem", "gaussian_density",
     "intensity_closed_form", "model_grid", "random_quaternions",
-    "detector_qlab", "poisson_counts",
+    "detector_qlab", "poisson_counts", "smooth_rows", "beamstop_mask",
 ]
 
 
@@ -146,9 +146,33 @@ def detector_qlab(P: int, qmax: float, edge_frac: float = 0.9):
     return d / wavelength
 
 
+def beamstop_mask(P: int, radius: float):
+    """Pixel weights of a P x P detector with a beam stop: 0 for pixels whose
+    centre lies within `radius` pixels of the detector centre, 1 elsewhere
+    (float32, flattened b*P + a like detector_qlab)."""
+    c = np.arange(P) - (P - 1) / 2.0
+    b, a = np.meshgrid(c, c, indexing="ij")
+    return (np.hypot(a, b).ravel() > radius).astype(np.float32)
+
+
 def poisson_counts(rng: np.random.Generator, lam):
     """Poisson photon counts with the given expectations (float32 output)."""
     return rng.poisson(np.maximum(np.asarray(lam, dtype=np.float64), 0.0)).astype(np.float32)
+
+
+def smooth_rows(rng: np.random.Generator, n: int, P: int, n_blobs: int = 24, width=(4.0, 20.0)):
+    """n smooth non-negative P x P images (rows of length P*P, float32): each a
+    random positive combination of isotropic 2D Gaussian blobs on the pixel
+    grid. Used as model-image-like rows where a test needs many of them
+    without computing slices."""
+    yy, xx = np.meshgrid(np.arange(P), np.arange(P), indexing="ij")
+    cx = rng.uniform(0, P, n_blobs)
+    cy = rng.uniform(0, P, n_blobs)
+    sw = rng.uniform(width[0], width[1], n_blobs)
+    basis = np.exp(-((xx[None] - cx[:, None, None]) ** 2 + (yy[None] - cy[:, None, None]) ** 2)
+                   / (2 * sw[:, None, None] ** 2)).reshape(n_blobs, P * P)
+    coef = rng.gamma(1.0, 1.0, (n, n_blobs))
+    return (coef @ basis).astype(np.float32)
 
 
 @dataclass

@@ -132,3 +132,34 @@ def test_fp8_precision_study(c1_data):
     refc = matching.match(f32(clean), f32(slices))
     clear = refc["margin"] > 1e-3
     np.testing.assert_array_equal(r8c["best"][clear], pb.img_pick[clear])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_beamstop_mask_weighted_matching(precision):
+    """Pixels behind a beam stop (weight 0) are left out of the distance."""
+    import torch
+    from paper_2109_05339_gb300 import Matcher
+    rng = np.random.default_rng(71)
+    P = 32
+    D = synth.beamstop_mask(P, 6.0)
+    Y = synth.smooth_rows(rng, 400, P)
+    pick = rng.integers(0, 400, 120)
+    X = synth.poisson_counts(rng, 20.0 * Y[pick])
+    X[:, D == 0] += 1e3 * rng.random((120, int((D == 0).sum()))).astype(np.float32)  # junk under the stop
+    scale = np.float32(0.05)
+    m = Matcher(120, 400, P * P, precision, 8)
+    m.set_mask(to_dev(D))
+    m.set_images(to_dev(X), float(scale))
+    m.add_slices(to_dev(Y))
+    r = {k: v.cpu().numpy() for k, v in m.results().items()}
+    m.status()
+    Xd = f32(X) * np.float64(scale)
+    ref = matching.match(Xd, f32(Y), D=f32(D))
+    ok = ref["margin"] > (MARGIN if precision != "fp8" else 1e-2)
+    if precision != "fp8":
+        assert ok.sum() > 60
+    np.testing.assert_array_equal(r["best"][ok], ref["best"][ok])
+    w = f32(D)
+    d_true = np.sum(w * (Xd - f32(Y)[r["best"]]) ** 2, axis=1)
+    sc = np.sum(w * Xd * Xd, 1) + np.sum(w * f32(Y)[r["best"]] ** 2, 1)
+    assert np.all(np.abs(r["d1"] - d_true) <= 1e-5 * sc)

@@ -1,0 +1,75 @@
+"""Point sets (points sorted once for a fixed orientation set): slicing equals
+spf_slice_model exactly; the class-sum merge equals the per-image merge and
+the FP64 oracle; orientation chunks accumulate to the whole."""
+import numpy as np
+import pytest
+
+from oracle import merge, rotation
+from tests.gpu_util import f32, problem, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c1():
+    import torch
+    from paper_2109_05339_gb300 import Plan, PointSet
+    pb = problem("c1")
+    N, P2, M = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0]
+    quats = to_dev(pb.quats.astype(np.float32))
+    qlab = to_dev(pb.q_lab.astype(np.float32))
+    plan = Plan(N, 1.0, 1e-6, max_points=M * P2)
+    ps = PointSet(plan, quats, qlab)
+    rng = np.random.default_rng(31)
+    images = rng.poisson(8.0, (137, P2)).astype(np.float32)
+    images[rng.random(images.shape) < 0.7] = 0.0            # sparse counts, like the c2 images
+    best = rng.integers(0, M, 137).astype(np.int32)
+    D = (rng.uniform(size=P2) > 0.1).astype(np.float32)
+    return dict(pb=pb, plan=plan, ps=ps, quats=quats, qlab=qlab, images=images, best=best, D=D,
+                N=N, P2=P2, M=M, torch=torch)
+
+
+def test_slice_points_equals_slice_model(c1):
+    A = to_dev(c1["pb"].A.astype(np.float32))
+    a = c1["ps"].slice(A)
+    b = c1["plan"].slice_model(A, c1["quats"], c1["qlab"])
+    assert c1["torch"].equal(a, b)
+
+
+def test_class_sum_merge_equals_per_image_merge_and_oracle(c1):
+    torch = c1["torch"]
+    plan, ps = c1["plan"], c1["ps"]
+    img, best, D = to_dev(c1["images"]), to_dev(c1["best"], torch.int32), to_dev(c1["D"])
+    r1, k1 = ps.merge(img, best, D=D, b_scale=0.25)
+    r2, k2 = plan.merge_images(img, c1["quats"], c1["qlab"], D=D, b_scale=0.25, orient_idx=best)
+    plan.status()
+    assert rel_l2(r1.cpu().numpy(), r2.cpu().numpy()) < 1e-6
+    assert rel_l2(k1.cpu().numpy(), k2.cpu().numpy()) < 1e-6
+    N = c1["N"]
+    t = rotation.nufft_points(f32(c1["pb"].quats.astype(np.float32))[c1["best"]],
+                              f32(c1["pb"].q_lab.astype(np.float32)), N, 1.0).reshape(-1, 3)
+    Dall = np.tile(f32(c1["D"]), len(c1["best"]))
+    ref_rhs = merge.rhs(f32(c1["images"]).reshape(-1) * 0.25, t, Dall, N)
+    ref_khat = merge.kernel_hat(merge.toeplitz_kernel(t, Dall, N), N)
+    assert rel_l2(r1.cpu().numpy(), ref_rhs) < 1e-5
+    assert rel_l2(k1.cpu().numpy(), ref_khat) < 1e-5
+
+
+def test_orientation_chunks_accumulate(c1):
+    torch = c1["torch"]
+    from paper_2109_05339_gb300 import PointSet
+    plan = c1["plan"]
+    img, best = to_dev(c1["images"]), to_dev(c1["best"], torch.int32)
+    whole_r, whole_k = c1["ps"].merge(img, best, b_scale=0.5)
+    rhs = torch.zeros_like(whole_r)
+    kh = torch.zeros_like(whole_k)
+    for c0, c1_ in [(0, 123), (123, 124), (124, c1["M"])]:
+        ps = PointSet(plan, c1["quats"][c0:c1_].contiguous(), c1["qlab"])
+        ps.merge(img, best, orient_offset=c0, b_scale=0.5, rhs=rhs, kernel_hat=kh, accumulate=c0 > 0)
+        torch.cuda.synchronize()
+        ps.close()
+    assert rel_l2(rhs.cpu().numpy(), whole_r.cpu().numpy()) < 1e-6
+    assert rel_l2(kh.cpu().numpy(), whole_k.cpu().numpy()) < 1e-6
+    # images outside every chunk leave the outputs at zero
+    empty_r, empty_k = c1["ps"].merge(img, best + c1["M"], b_scale=0.5)
+    assert float(empty_r.abs().max()) == 0.0 and float(empty_k.abs().max()) == 0.0

@@ -39,3 +39,25 @@ def test_margin_definition():
     assert res["best"][0] == 0 and list(res["topk"][0]) == [0, 1]
     assert abs(res["margin"][0] - (1.0 - 0.25) / (1.0 + 1.25)) < 1e-15
     assert abs(res["margin_alt"][0] - 0.75) < 1e-15
+
+
+def test_weighted_distance_definition():
+    import synth
+    rng = np.random.default_rng(3)
+    D = synth.beamstop_mask(8, 2.0)
+    assert D.shape == (64,) and 0 < D.sum() < 64 and D[27] == 0.0      # centre pixel masked
+    X = rng.uniform(0, 3, (5, 64))
+    Y = rng.uniform(0, 3, (7, 64))
+    d = matching.distances(X, Y, D)
+    for i in range(2):
+        for j in range(3):
+            ref = sum(D[p] * (X[i, p] - Y[j, p]) ** 2 for p in range(64))
+            assert abs(d[i, j] - ref) < 1e-10
+    # equals the unweighted distance of sqrt(D)-scaled rows, and the expanded form
+    s = np.sqrt(D)
+    np.testing.assert_allclose(d, matching.distances(X * s, Y * s), rtol=1e-12)
+    np.testing.assert_allclose(matching.distances_expanded(X, Y, D), d, rtol=1e-10, atol=1e-10)
+    res = matching.match(X, Y, k=3, D=D)
+    x2 = np.sum(D * X * X, 1)
+    y2 = np.sum(D * Y * Y, 1)
+    assert abs(res["margin"][0] - (res["d2"][0] - res["d1"][0]) / (x2[0] + y2[res["best"][0]])) < 1e-15
