@@ -692,7 +692,7 @@ int spread_sorted(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, const So
   const float beta = (float)P->beta;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
-  return launch("spread_kernel", s, [&] {
+  return launch(&g == &P->gT ? "spread_toeplitz_kernel" : "spread_kernel", s, [&] {
     spread_kernel<W, Pts, Str><<<sms, 32 * C::WARPS, C::SMEM, s>>>(pts, str, geom, beta, set.ids,
                                                                    set.subs, set.nsubs, g.real, err);
   });
