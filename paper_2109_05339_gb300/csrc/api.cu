@@ -56,7 +56,7 @@ struct DeviceScope {
 };
 
 // nufft.cu
-int type2_setup(spf_plan* P, const float* A, cudaStream_t s);
+int type2_setup(spf_plan* P, const float* A, cudaStream_t s, bool halo = true);
 int type2_quat(spf_plan* P, const float* quats, int M, const float* qlab, int P2, float* out,
                cudaStream_t s);
 int type2_explicit(spf_plan* P, const float* t, int64_t npts, float* out, cudaStream_t s);
@@ -124,6 +124,7 @@ static void plan_free(spf_plan* P) {
 static int plan_init(spf_plan* P) {
   const int N = P->N;
   es_params(P->eps, &P->w, &P->beta);
+  es_poly(P->w, P->beta, &P->poly);
   P->Mh = (N - 1) / 2;
   double dq = P->qmax / P->Mh;
   double dr = 1.0 / (N * dq);

@@ -65,6 +65,50 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
   }
 }
 
+// Polynomial form of the kernel for the device. A point u has its first tap
+// at l0 = ceil(u - w/2); with x = l0 - (u - w/2) in [0, 1) tap d sits at
+// z_d = (2x + 2d - w) / w. Each phi(z_d(x)) is replaced by its Chebyshev
+// interpolant of degree w + 1 in t = 2x - 1 (nodes t_k = cos(pi (k + 1/2) /
+// (w + 2))), rewritten in powers of t for Horner's rule. This is the
+// piecewise-polynomial kernel evaluation of the FINUFFT library's published
+// method (Barnett, Magland and af Klinteberg, SIAM J. Sci. Comput. 41 (2019),
+// Sec. 3.1.1), with coefficients computed here in FP64. Its largest absolute
+// error is below exp(-beta) (the kernel's value at the support edge, where
+// the square root makes it non-smooth), e.g. 6e-8 for w = 7.
+void es_poly(int w, double beta, EsPoly* out) {
+  *out = EsPoly();
+  const int P = w + 1, n = P + 1;
+  if (w < 1 || w > 8) return;
+  for (int d = 0; d < w; ++d) {
+    std::vector<double> f(n), a(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+      const double t = std::cos(M_PI * (k + 0.5) / n), x = 0.5 * (t + 1.0);
+      const double z = (2.0 * x + 2.0 * d - w) / w;
+      const double s = 1.0 - z * z;
+      f[k] = std::fabs(z) <= 1.0 ? std::exp(beta * (std::sqrt(s > 0 ? s : 0) - 1.0)) : 0.0;
+    }
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc += f[k] * std::cos(j * M_PI * (k + 0.5) / n);
+      a[j] = (j == 0 ? 1.0 : 2.0) * acc / n;
+    }
+    // sum_j a_j T_j(t) in powers of t: T_0 = 1, T_1 = t, T_j+1 = 2t T_j - T_j-1
+    std::vector<double> m(n, 0.0), t0(n, 0.0), t1(n, 0.0), t2(n, 0.0);
+    t0[0] = 1.0;
+    if (n > 1) t1[1] = 1.0;
+    for (int i = 0; i < n; ++i) m[i] += a[0] * t0[i];
+    if (n > 1)
+      for (int i = 0; i < n; ++i) m[i] += a[1] * t1[i];
+    for (int j = 2; j < n; ++j) {
+      for (int i = 0; i < n; ++i) t2[i] = (i > 0 ? 2.0 * t1[i - 1] : 0.0) - t0[i];
+      for (int i = 0; i < n; ++i) m[i] += a[j] * t2[i];
+      t0 = t1;
+      t1 = t2;
+    }
+    for (int i = 0; i < n; ++i) out->c[d][i] = (float)m[i];
+  }
+}
+
 void deconv_factors(int n_modes, int nf, int w, double beta, double* out) {
   const int nq = 256;
   std::vector<double> z, wq;

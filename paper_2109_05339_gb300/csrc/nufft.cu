@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "plan.h"
+#include "tc.h"
 
 namespace spf {
 
@@ -146,16 +147,18 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 // Wrap for arguments known to lie in [-n, 2n): one correction, no division.
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// ES weights of the W cells l0 .. l0+W-1 nearest to u (l0 = ceil(u - W/2)).
+// ES weights of the W cells l0 .. l0+W-1 nearest to u (l0 = ceil(u - W/2)),
+// from the kernel's per-tap polynomials in t = 2 (l0 - u + W/2) - 1 (Horner).
 template <int W>
-__device__ __forceinline__ int es_weights(float u, float beta, float* wt) {
-  int l0 = (int)ceilf(u - 0.5f * W);
-  const float s = 2.f / W;
+__device__ __forceinline__ int es_weights(float u, const EsPoly& ep, float* wt) {
+  const int l0 = (int)ceilf(u - 0.5f * W);
+  const float t = 2.f * ((float)l0 - u + 0.5f * W) - 1.f;
 #pragma unroll
   for (int d = 0; d < W; ++d) {
-    float z = ((float)(l0 + d) - u) * s;
-    float r = fmaxf(0.f, 1.f - z * z);
-    wt[d] = __expf(beta * (sqrtf(r) - 1.f));
+    float v = ep.c[d][W + 1];
+#pragma unroll
+    for (int i = W; i >= 0; --i) v = fmaf(v, t, ep.c[d][i]);
+    wt[d] = v;
   }
   return l0;
 }
@@ -192,9 +195,14 @@ __device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
   int cx = wrap1((int)ceilf(u.x - 0.5f * W) + H, g.nf);
   int cy = wrap1((int)ceilf(u.y - 0.5f * W) + H, g.nf);
   int cz = wrap1((int)ceilf(u.z - 0.5f * W) + H, g.nf);
-  constexpr int B = kBinLog, M = kBin - 1;
+  constexpr int B = kBinLog;
   int bin = ((cz >> B) * g.nb1 + (cy >> B)) * g.nb0 + (cx >> B);
-  return (bin << (3 * B)) | ((cz & M) << (2 * B)) | ((cy & M) << B) | (cx & M);
+  // cell inside the 4^3 bin, ordered by its 2^3 cell pair block first: the
+  // points of one block are contiguous (the spreading accumulates a block's
+  // points in registers)
+  const int pair = (((cz >> 1) & 1) << 2) | (((cy >> 1) & 1) << 1) | ((cx >> 1) & 1);
+  const int sub = ((cz & 1) << 2) | ((cy & 1) << 1) | (cx & 1);
+  return (bin << (3 * B)) | (pair << 3) | sub;
 }
 
 template <int W, class Pts>
@@ -392,7 +400,7 @@ __device__ __forceinline__ float wrap_cells(float u, float nf) {
 template <int W, class Pts>
 __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ Gq, int nf, Pts pts,
                                                      int64_t npts, const uint32_t* __restrict__ sorted,
-                                                     float beta, float* __restrict__ out) {
+                                                     EsPoly ep, float* __restrict__ out) {
   static_assert(W <= 8, "two float4 per tap row");
   constexpr int H = W / 2;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -404,9 +412,9 @@ __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G
   u.y = wrap_cells(u.y, fn);
   u.z = wrap_cells(u.z, fn);
   float wx[8], wy[W], wz[W];
-  const int lx = es_weights<W>(u.x, beta, wx) + H;     // in [0, nf], halo frame
-  const int ly = es_weights<W>(u.y, beta, wy) + H;
-  const int lz = es_weights<W>(u.z, beta, wz) + H;
+  const int lx = es_weights<W>(u.x, ep, wx) + H;     // in [0, nf], halo frame
+  const int ly = es_weights<W>(u.y, ep, wy) + H;
+  const int lz = es_weights<W>(u.z, ep, wz) + H;
 #pragma unroll
   for (int d = W; d < 8; ++d) wx[d] = 0.f;
   const int np = nf + W, npx = halo_npx(nf, W);
@@ -436,22 +444,291 @@ __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G
   out[id] = acc;
 }
 
+// ---- type 2 on the tensor cores -------------------------------------------
+// For the points of one bin (4^3 cells) all W^3 taps lie in the S^3 window
+// of G (S = W + 3) whose corner is the bin's first cell minus H. With the
+// window as the matrix B[n][x] = G[z][y][x], n = z S + y, and each point's x
+// weights placed at their window columns, A[p][x] = phi_x,p(x) (zero outside
+// its W columns), the product T = A B^T holds T[p][n] = sum_x G[z][y][x]
+// phi_x,p(x), and c_p = sum_(z,y) T[p][z S + y] phi_z,p(z) phi_y,p(y). T is
+// formed by tcgen05.mma (kind::tf32; M = 128 points, N = S^2 rounded up to
+// 16, K = 16 window columns) into tensor memory; one thread per point reads
+// its row back and contracts it with its z and y weights.
+//
+// FP32 accuracy from TF32 inputs: every operand value v is split into
+// hi = tf32(v) and lo = tf32(v - hi), and T = A_hi B_hi + A_hi B_lo +
+// A_lo B_hi; the dropped A_lo B_lo term and the rounding of lo are
+// O(2^-22) relative. Both parts share a 128-byte swizzled row of the operand
+// tile: hi at K 0..15, lo at K 16..31.
+template <int W>
+struct InterpTcCfg {
+  static constexpr int H = W / 2;
+  static constexpr int S = kBin + W - 1;            // window cells per axis
+  static constexpr int NN = ((S * S + 15) / 16) * 16;   // MMA N
+  static constexpr int KSTEPS = S <= 8 ? 1 : 2;     // 8 window columns per MMA
+  static constexpr int PTS = 128;                   // points per MMA (M)
+  static constexpr uint32_t TILE = 128 * 128;       // one operand tile (bytes)
+  static constexpr int TCOLS = 128;                 // tensor-memory columns
+  // operand tiles, barriers, per-point y and z weights; 48 KB also keeps at
+  // most four CTAs on an SM, so their 4 x 128 TMEM columns always fit
+  static constexpr size_t SMEM = 48 * 1024;
+  static_assert(1024 + 2 * TILE + 64 + 2 * S * 128 * 4 <= SMEM, "shared memory layout");
+  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NN >> 3) << 17) |
+                                    ((128u >> 4) << 24);
+  static_assert(NN <= TCOLS && NN <= 128, "window rows exceed one tile");
+  static_assert(S <= 16, "window columns exceed K = 16");
+};
+
+// Nearest TF32 value (10 explicit mantissa bits; ties away from zero) by
+// integer rounding of the FP32 pattern.
+__device__ __forceinline__ float tf32_round(float v) {
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
+}
+
+// v = hi + lo with hi = tf32(v) and lo = tf32(v - hi) (v - hi is exact).
+__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
+  hi = tf32_round(v);
+  lo = tf32_round(v - hi);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// e[i] = w[i - o] for 0 <= i - o < W, else 0; o in [0, 3]; i in [0, L).
+template <int W, int L>
+__device__ __forceinline__ void shift_weights(const float* w, int o, float* e) {
+  float t[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const float a = i < W ? w[i] : 0.f;
+    const float b = i >= 1 && i - 1 < W ? w[i - 1] : 0.f;
+    t[i] = (o & 1) ? b : a;
+  }
+#pragma unroll
+  for (int i = 0; i < L; ++i) e[i] = (o & 2) ? (i >= 2 ? t[i - 2] : 0.f) : t[i];
+}
+
+template <int W, class Pts>
+__global__ void __launch_bounds__(128, 4)
+interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
+                 const uint32_t* __restrict__ sorted, const int4* __restrict__ subs, int* __restrict__ nsubs,
+                 float* __restrict__ out, int* err) {
+  using C = InterpTcCfg<W>;
+  constexpr int S = C::S;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* As = smem;
+  uint8_t* Bs = smem + C::TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * C::TILE);
+  uint64_t* done = bar + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  int* next = reinterpret_cast<int*>(tslot + 2);
+  float* Ey = reinterpret_cast<float*>(smem + 2 * C::TILE + 64);   // [S][128]
+  float* Ez = Ey + S * 128;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int nf = g.nf;
+
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tslot)), "r"(C::TCOLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // window rows n >= S^2 are read by the MMA: keep them zero
+  for (int i = t; i < (int)(C::TILE / 16); i += 128)
+    reinterpret_cast<float4*>(Bs)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
+  const int nsub = nsubs[0];
+  uint32_t phase = 0;
+  bool issued = false;
+
+  for (;;) {
+    if (t == 0) *next = atomicAdd(nsubs + 1, 1);
+    __syncthreads();
+    const int sidx = *next;
+    const bool stop = sidx >= nsub || *abort_flag;
+    __syncthreads();
+    if (stop) break;
+    const int4 sub = subs[sidx];
+    const int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
+    const int ox0 = bx * kBin - C::H, oy0 = by * kBin - C::H, oz0 = bz * kBin - C::H;
+    // window -> B (hi | lo), 4 columns per task
+    for (int task = t; task < S * S * 4; task += 128) {
+      const int n = task >> 2, c = task & 3;
+      const int z = n / S, y = n - z * S;
+      const float* row = G + ((size_t)wrap1(oz0 + z, nf) * nf + wrap1(oy0 + y, nf)) * nf;
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = 4 * c + e;
+        v[e] = x < S ? __ldg(row + wrap1(ox0 + x, nf)) : 0.f;
+      }
+      float4 hi, lo;
+      split_tf32(v[0], hi.x, lo.x);
+      split_tf32(v[1], hi.y, lo.y);
+      split_tf32(v[2], hi.z, lo.z);
+      split_tf32(v[3], hi.w, lo.w);
+      *reinterpret_cast<float4*>(Bs + swz128(n, c)) = hi;
+      *reinterpret_cast<float4*>(Bs + swz128(n, c + 4)) = lo;
+    }
+    bool aborted = false;
+    for (int base = 0; base < sub.z; base += C::PTS) {
+      const int i = base + t;
+      const bool valid = i < sub.z;
+      uint32_t id = 0;
+      bool ok = false;
+      int ox = 0, oy = 0, oz = 0;
+      float3 u = make_float3(0.f, 0.f, 0.f);
+      if (valid) {
+        id = __ldg(sorted + sub.y + i);
+        u = pts(id);
+        const int cx = wrap1((int)ceilf(u.x - 0.5f * W) + C::H, nf);
+        const int cy = wrap1((int)ceilf(u.y - 0.5f * W) + C::H, nf);
+        const int cz = wrap1((int)ceilf(u.z - 0.5f * W) + C::H, nf);
+        ok = (cx >> kBinLog) == bx && (cy >> kBinLog) == by && (cz >> kBinLog) == bz;
+        if (!ok) atomicOr(err, 1);   // cannot happen when sorting and interpolation agree
+        ox = cx & (kBin - 1);
+        oy = cy & (kBin - 1);
+        oz = cz & (kBin - 1);
+      }
+      {
+        // A row t: the x weights at their window columns, hi | lo
+        float w[W], ax[16];
+        es_weights<W>(u.x, ep, w);
+        shift_weights<W, 16>(w, ox, ax);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float4 hi, lo;
+          split_tf32(ok ? ax[4 * c] : 0.f, hi.x, lo.x);
+          split_tf32(ok ? ax[4 * c + 1] : 0.f, hi.y, lo.y);
+          split_tf32(ok ? ax[4 * c + 2] : 0.f, hi.z, lo.z);
+          split_tf32(ok ? ax[4 * c + 3] : 0.f, hi.w, lo.w);
+          *reinterpret_cast<float4*>(As + swz128(t, c)) = hi;
+          *reinterpret_cast<float4*>(As + swz128(t, c + 4)) = lo;
+        }
+      }
+      {
+        // y and z weights at their window rows, parked in shared memory
+        float w[W], e[S];
+        es_weights<W>(u.y, ep, w);
+        shift_weights<W, S>(w, oy, e);
+#pragma unroll
+        for (int k = 0; k < S; ++k) Ey[k * 128 + t] = ok ? e[k] : 0.f;
+        es_weights<W>(u.z, ep, w);
+        shift_weights<W, S>(w, oz, e);
+#pragma unroll
+        for (int k = 0; k < S; ++k) Ez[k * 128 + t] = ok ? e[k] : 0.f;
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (t == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < C::KSTEPS; ++kk) {
+          const uint64_t ahi = sdesc(a_addr + 32 * kk), alo = sdesc(a_addr + 64 + 32 * kk);
+          const uint64_t bhi = sdesc(b_addr + 32 * kk), blo = sdesc(b_addr + 64 + 32 * kk);
+          mma_tf32(tmem, alo, bhi, C::IDESC, kk > 0 ? 1u : 0u);
+          mma_tf32(tmem, ahi, blo, C::IDESC, 1u);
+          mma_tf32(tmem, ahi, bhi, C::IDESC, 1u);
+        }
+        mma_commit(bar);
+        issued = true;
+      }
+      mbar_wait(bar, phase, abort_flag, err);
+      phase ^= 1u;
+      tc_fence_after();
+      __syncthreads();
+      if (*abort_flag) {
+        aborted = true;
+        break;
+      }
+      // T row -> c_p
+      float az[S], ey[S];
+#pragma unroll
+      for (int z = 0; z < S; ++z) {
+        az[z] = 0.f;
+        ey[z] = Ey[z * 128 + t];
+      }
+#pragma unroll
+      for (int ch = 0; ch < C::NN / 16; ++ch) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 16), v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int n = ch * 16 + e;
+          if (n < S * S) az[n / S] = fmaf(v[e], ey[n % S], az[n / S]);
+        }
+      }
+      float acc = 0.f;
+#pragma unroll
+      for (int z = 0; z < S; ++z) acc = fmaf(az[z], Ez[z * 128 + t], acc);
+      if (ok) out[id] = acc;
+      tc_fence_before();
+      __syncthreads();
+    }
+    if (aborted) break;
+  }
+  // no MMA may still be running when the columns are freed
+  tc_fence_before();
+  __syncthreads();
+  if (t == 0) {
+    tc_fence_after();
+    if (issued) {
+      mma_commit(done);
+      mbar_wait(done, 0, abort_flag, err, false);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS)
+                 : "memory");
+  }
+}
+
 // ------------------------------------------------------------ type 1 ------
 // Per-warp shared-memory subgrid of one 4^3-cell bin: S planes of ROWS rows of
 // 16 floats, S = 4 + W - 1 cells per axis. A lane (r = lane / 8, dx =
-// lane % 8) owns tap rows dy = r and r + 4 and column dx. Column c of row R
+// lane % 8) owns window rows dy = r and r + 4 and column dx. Column c of row R
 // is stored at c ^ (8 * ((R >> 1) & 1)): among any 4 consecutive rows the two
 // of equal parity then sit on disjoint halves of their 16-bank group, so one
 // instruction's 32 accesses are conflict-free.
+//
+// For W < 8 the 8 lane columns and rows have room for a window one cell
+// wider than the kernel, so a warp accumulates the points of a whole 2^3
+// block of cells (PAIR): the window starts at the block's even corner and a
+// point whose cell is odd along an axis takes its weights shifted by one.
+// Register runs then cover 8 cells instead of one, at W + 1 instead of W
+// planes of FMAs.
 template <int W>
 struct SpreadCfg {
   static constexpr int H = W / 2;
+  static constexpr bool PAIR = W < 8;
+  static constexpr int WZ = PAIR ? W + 1 : W;   // accumulated planes
   static constexpr int S = kBin + W - 1;   // cells per axis touched by a bin's points
   static constexpr int ROWS = kBin + 7;    // rows reached by the (r, r + 4) lane rows
   static constexpr int RS = 16;
   static constexpr int PLANE = ROWS * RS;
   static constexpr int GRID = S * PLANE;
-  static constexpr int REC = 28;           // staged point: lx, ly, lz, v, wz[8], wx[8], wy[8]
+  static constexpr int REC = 28;           // staged point: ox, oy, oz, v, wz[8], wx[8], wy[8]
   static constexpr int STAGE = 32 * REC;
   static constexpr int WARPS = 20;
   static constexpr size_t SMEM = (size_t)WARPS * (GRID + STAGE) * sizeof(float);
@@ -461,12 +738,12 @@ __device__ __forceinline__ int swz(int R, int c) { return R * 16 + (c ^ (((R >> 
 
 template <int W>
 __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int lz, int r, int dx,
-                                              float (&acc)[W][2]) {
+                                              float (&acc)[SpreadCfg<W>::WZ][2]) {
   using C = SpreadCfg<W>;
   const int a0 = swz(ly + r, lx + dx), a1 = swz(ly + r + 4, lx + dx);
   float* p = grid + lz * C::PLANE;
 #pragma unroll
-  for (int dz = 0; dz < W; ++dz) {
+  for (int dz = 0; dz < C::WZ; ++dz) {
     p[dz * C::PLANE + a0] += acc[dz][0];
     p[dz * C::PLANE + a1] += acc[dz][1];
     acc[dz][0] = 0.f;
@@ -476,7 +753,7 @@ __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int l
 
 template <int W, class Pts, class Str>
 __global__ void __launch_bounds__(32 * SpreadCfg<W>::WARPS, 1)
-spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restrict__ sorted,
+spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restrict__ sorted,
               const int4* __restrict__ subs, int* __restrict__ nsubs, float* __restrict__ out, int* err) {
   using C = SpreadCfg<W>;
   extern __shared__ float4 smem4[];
@@ -497,15 +774,28 @@ spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restri
     const int4 sub = subs[s];
     const int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
     int cur = -1, cx0 = 0, cy0 = 0, cz0 = 0;
-    float acc[W][2];
+    float acc[C::WZ][2];
 #pragma unroll
-    for (int dz = 0; dz < W; ++dz) acc[dz][0] = acc[dz][1] = 0.f;
+    for (int dz = 0; dz < C::WZ; ++dz) acc[dz][0] = acc[dz][1] = 0.f;
+    // software pipeline of the global loads: ids two batches ahead, their
+    // strengths one batch ahead of the batch being staged
+    const uint32_t* ids = sorted + sub.y;
+    uint32_t idA = 0, idB = 0;
+    float vA = 0.f;
+    if (lane < sub.z) {
+      idA = __ldg(ids + lane);
+      vA = str(idA);
+    }
+    if (32 + lane < sub.z) idB = __ldg(ids + 32 + lane);
     for (int base = 0; base < sub.z; base += 32) {
       const int nb = min(32, sub.z - base);
+      const uint32_t id = idA;
+      float v = vA;
+      vA = base + 32 + lane < sub.z ? str(idB) : 0.f;
+      idA = idB;
+      if (base + 64 + lane < sub.z) idB = __ldg(ids + base + 64 + lane);
       // stage: lane k prepares point base + k
       if (lane < nb) {
-        const uint32_t id = __ldg(sorted + sub.y + base + lane);
-        float v = str(id);
         float* rec = stage + lane * C::REC;
         if (v == 0.f) {                       // contributes nothing: skip its weights
           rec[3] = 0.f;
@@ -514,9 +804,9 @@ spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restri
         {
         const float3 u = pts(id);
         float wx[W], wy[W], wz[W];
-        const int lx = es_weights<W>(u.x, beta, wx);
-        const int ly = es_weights<W>(u.y, beta, wy);
-        const int lz = es_weights<W>(u.z, beta, wz);
+        const int lx = es_weights<W>(u.x, ep, wx);
+        const int ly = es_weights<W>(u.y, ep, wy);
+        const int lz = es_weights<W>(u.z, ep, wz);
         // tap-origin cell, wrapped; its position inside the bin is the local origin
         const int cx = wrap1(lx + C::H, nf), cy = wrap1(ly + C::H, nf), cz = wrap1(lz + C::H, nf);
         int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);
@@ -525,15 +815,22 @@ spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restri
           v = 0.f;
           ox = oy = oz = 0;
         }
-        rec[0] = __int_as_float(ox);
-        rec[1] = __int_as_float(oy);
-        rec[2] = __int_as_float(oz);
+        // window corner (the pair block's even corner under PAIR) and the
+        // point's shift inside the window
+        const int sx = C::PAIR ? (ox & 1) : 0, sy = C::PAIR ? (oy & 1) : 0, sz = C::PAIR ? (oz & 1) : 0;
+        rec[0] = __int_as_float(ox - sx);
+        rec[1] = __int_as_float(oy - sy);
+        rec[2] = __int_as_float(oz - sz);
         rec[3] = v;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-          rec[4 + d] = d < W ? wz[d] : 0.f;
-          rec[12 + d] = d < W ? wx[d] : 0.f;
-          rec[20 + d] = d < W ? wy[d] : 0.f;
+          const float z0 = d < W ? wz[d] : 0.f, x0 = d < W ? wx[d] : 0.f, y0 = d < W ? wy[d] : 0.f;
+          const float z1 = d >= 1 && d - 1 < W ? wz[d - 1] : 0.f;
+          const float x1 = d >= 1 && d - 1 < W ? wx[d - 1] : 0.f;
+          const float y1 = d >= 1 && d - 1 < W ? wy[d - 1] : 0.f;
+          rec[4 + d] = sz ? z1 : z0;
+          rec[12 + d] = sx ? x1 : x0;
+          rec[20 + d] = sy ? y1 : y0;
         }
         }
       staged:;
@@ -558,7 +855,7 @@ spread_kernel(Pts pts, Str str, SortGeom g, float beta, const uint32_t* __restri
         const float4 z1 = *reinterpret_cast<const float4*>(rec + 8);
         const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
-        for (int dz = 0; dz < W; ++dz) {
+        for (int dz = 0; dz < C::WZ; ++dz) {
           acc[dz][0] = fmaf(wz[dz], c0, acc[dz][0]);
           acc[dz][1] = fmaf(wz[dz], c1, acc[dz][1]);
         }
@@ -649,6 +946,25 @@ int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cuda
   });
 }
 
+// Tensor-core interpolation of an already sorted set (its subproblems give
+// the bins) from g.real.
+template <int W, class Pts>
+int interp_tc(spf_plan* P, Pts pts, const SortedSet& set, float* out, cudaStream_t s) {
+  using C = InterpTcCfg<W>;
+  Grid& g = P->g;
+  SPF_CUDA(cudaMemsetAsync(set.nsubs + 1, 0, sizeof(int), s));   // work cursor
+  SPF_CUDA(cudaFuncSetAttribute(interp_tc_kernel<W, Pts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::SMEM));
+  SortGeom geom{g.nf, g.bins.nb[0], g.bins.nb[1], g.bins.nb[2]};
+  const EsPoly& ep = P->poly;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  return launch("interp_tc_kernel", s, [&] {
+    interp_tc_kernel<W, Pts><<<4 * sms, 128, C::SMEM, s>>>(g.real, pts, geom, ep, set.ids, set.subs,
+                                                           set.nsubs, out, P->err);
+  });
+}
+
 template <int W, class Pts>
 int interp_w(spf_plan* P, Pts pts, int64_t npts, bool use_sort, float* out, cudaStream_t s) {
   if (npts == 0) return SPF_OK;
@@ -658,10 +974,10 @@ int interp_w(spf_plan* P, Pts pts, int64_t npts, bool use_sort, float* out, cuda
     SPF_TRY((sort_points<W, Pts>(g, P->sorted, pts, npts, P->err, s)));
     order = P->sorted;
   }
-  const float beta = (float)P->beta;
+  const EsPoly& ep = P->poly;
   return launch("interp_kernel", s, [&] {
     interp_kernel<W, Pts><<<(unsigned)ceil_div(npts, 256), 256, 0, s>>>(g.halo, g.nf, pts, npts, order,
-                                                                       beta, out);
+                                                                       ep, out);
   });
 }
 
@@ -689,11 +1005,11 @@ int spread_sorted(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, const So
   SPF_CUDA(cudaFuncSetAttribute(spread_kernel<W, Pts, Str>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)C::SMEM));
   SortGeom geom{g.nf, b.nb[0], b.nb[1], b.nb[2]};
-  const float beta = (float)P->beta;
+  const EsPoly& ep = P->poly;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   return launch(&g == &P->gT ? "spread_toeplitz_kernel" : "spread_kernel", s, [&] {
-    spread_kernel<W, Pts, Str><<<sms, 32 * C::WARPS, C::SMEM, s>>>(pts, str, geom, beta, set.ids,
+    spread_kernel<W, Pts, Str><<<sms, 32 * C::WARPS, C::SMEM, s>>>(pts, str, geom, ep, set.ids,
                                                                    set.subs, set.nsubs, g.real, err);
   });
 }
@@ -718,12 +1034,13 @@ int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cud
   }
 
 // Fine-grid real part G of the deconvolved, padded model (type-2 set-up).
-int type2_setup(spf_plan* P, const float* A, cudaStream_t s) {
+int type2_setup(spf_plan* P, const float* A, cudaStream_t s, bool halo) {
   Grid& g = P->g;
   int64_t n3 = (int64_t)g.nf * g.nf * g.nf;
   SPF_TRY(launch("deconv_pad_kernel", s,
                  [&] { deconv_pad_kernel<<<grid_for(n3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); }));
   SPF_TRY(fft3_exec_ex(&g.fft, g.cube, nullptr, g.real, nullptr, -1, P->Mh + 1, 0, s));
+  if (!halo) return SPF_OK;
   const int np = g.nf + P->w, npx = halo_npx(g.nf, P->w);
   const int64_t tot = 4 * (int64_t)np * np * npx;
   return launch("halo_kernel", s, [&] {
@@ -844,15 +1161,9 @@ int points_build(spf_plan* P, spf_points* S, cudaStream_t s) {
 int slice_points(spf_plan* P, spf_points* S, const float* A, float* out, cudaStream_t s) {
   const int64_t npts = (int64_t)S->M * S->P2;
   if (npts == 0) return SPF_OK;
-  SPF_TRY(type2_setup(P, A, s));
+  SPF_TRY(type2_setup(P, A, s, false));
   QuatPts pts{reinterpret_cast<const float4*>(S->quats), S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
-  const uint32_t* order = S->setN.ids;
-  const float beta = (float)P->beta;
-  Grid& g = P->g;
-  SPF_W_SWITCH(P->w, SPF_TRY(launch("interp_kernel", s, [&] {
-    interp_kernel<W, QuatPts><<<(unsigned)ceil_div(npts, 256), 256, 0, s>>>(g.halo, g.nf, pts, npts, order,
-                                                                           beta, out);
-  })));
+  SPF_W_SWITCH(P->w, SPF_TRY((interp_tc<W, QuatPts>(P, pts, S->setN, out, s))));
   return SPF_OK;
 }
 

@@ -28,6 +28,13 @@ struct BinSort {
   int* nsubs = nullptr;      // [0] subproblem count, [1] work cursor
 };
 
+// ES kernel weights as polynomials: tap d (0 <= d < w) of a point at
+// fractional offset x in [0, 1) has weight sum_i c[d][i] t^i, t = 2x - 1,
+// degree w + 1 (see es_poly).
+struct EsPoly {
+  float c[8][10];
+};
+
 struct Grid {
   int nf = 0;                // fine grid side
   int n_modes = 0;           // modes per axis (odd)
@@ -57,6 +64,7 @@ struct spf_plan {
   double qmax = 0, eps = 0;
   int w = 0;
   double beta = 0;
+  spf::EsPoly poly;           // polynomial form of the kernel for the device
   double radians_per_q = 0;   // 2 pi dr
   int64_t max_points = 0;
   spf::Grid g;                // N modes (slicing, RHS)
@@ -91,6 +99,7 @@ struct spf_points {
 namespace spf {
 // Host side of the ES kernel set-up (es.cu).
 void es_params(double eps, int* w, double* beta);
+void es_poly(int w, double beta, EsPoly* out);
 int fine_size(int n_modes, int w);
 int smooth_even_at_least(int n);
 void deconv_factors(int n_modes, int nf, int w, double beta, double* out);

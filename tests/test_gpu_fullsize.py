@@ -47,6 +47,32 @@ def test_slicing_sampled_outputs(c2):
     assert err < 1e-5, err
 
 
+def test_point_set_slicing_sampled_outputs(c2):
+    """The slicing the M-TIP driver runs (orientation set sorted once, the
+    tensor-core interpolation) at the full size: sampled outputs against the
+    FP64 direct sum, and the whole slice stack against the per-call path."""
+    from paper_2109_05339_gb300 import PointSet
+    pb, plan = c2["pb"], c2["plan"]
+    ps = PointSet(plan, c2["quats"], c2["qlab"])
+    s = ps.slice(c2["A"])
+    plan.status()
+    rng = np.random.default_rng(23)
+    j = rng.integers(0, c2["M"], 256)
+    p = rng.integers(0, c2["P2"], 256)
+    got = s[j, p].cpu().numpy().astype(np.float64)
+    q32 = f32(pb.quats.astype(np.float32))
+    l32 = f32(pb.q_lab.astype(np.float32))
+    t = np.stack([nufft_points(q32[j[k]:j[k] + 1], l32[p[k]:p[k] + 1], c2["N"], 1.0)[0, 0]
+                  for k in range(256)])
+    ref = nudft.type2(f32(pb.A.astype(np.float32)), t).real
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 1e-5, err
+    whole = plan.slice_model(c2["A"], c2["quats"], c2["qlab"])
+    d = float((s.double() - whole.double()).norm() / whole.double().norm())
+    assert d < 2e-6, d
+    ps.close()
+
+
 def test_merge_sampled_modes_and_kernel(c2):
     import torch
     pb, plan, N, P2 = c2["pb"], c2["plan"], c2["N"], c2["P2"]
