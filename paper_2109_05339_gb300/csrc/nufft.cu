@@ -64,7 +64,13 @@ struct QuatPts {
   __device__ __forceinline__ float fold(float u) const {
     return __fsub_rn(u, __fmul_rn(nf, rintf(__fmul_rn(u, inv_nf))));
   }
-  __device__ __forceinline__ float3 operator()(uint32_t id) const {
+  // The loads of a point (orientation and pixel), apart from the arithmetic,
+  // so that kernels can issue them ahead of use.
+  struct Raw {
+    float4 q;
+    float qx, qy, qz;
+  };
+  __device__ __forceinline__ Raw load(uint32_t id) const {
     uint32_t j = P2.div(id), p = id - j * P2.d;
     if (oidx) {
       int o = __ldg(oidx + j);
@@ -74,9 +80,17 @@ struct QuatPts {
       }
       j = (uint32_t)o;
     }
-    float4 q = __ldg(quats + j);
-    float w = q.x, x = q.y, y = q.z, z = q.w;
-    float qx = __ldg(qlab + 3 * p), qy = __ldg(qlab + 3 * p + 1), qz = __ldg(qlab + 3 * p + 2);
+    Raw r;
+    r.q = __ldg(quats + j);
+    r.qx = __ldg(qlab + 3 * p);
+    r.qy = __ldg(qlab + 3 * p + 1);
+    r.qz = __ldg(qlab + 3 * p + 2);
+    return r;
+  }
+  __device__ __forceinline__ float3 operator()(uint32_t id) const { return rotate(load(id)); }
+  __device__ __forceinline__ float3 rotate(const Raw& rw) const {
+    const float w = rw.q.x, x = rw.q.y, y = rw.q.z, z = rw.q.w;
+    const float qx = rw.qx, qy = rw.qy, qz = rw.qz;
     float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
     float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
     float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
@@ -469,8 +483,11 @@ struct InterpTcCfg {
   static constexpr int PTS = 128;                   // points per MMA (M)
   static constexpr uint32_t TILE = 128 * 128;       // one operand tile (bytes)
   static constexpr int TCOLS = 128;                 // tensor-memory columns
-  // operand tiles, barriers, per-point y and z weights; 48 KB also keeps at
-  // most four CTAs on an SM, so their 4 x 128 TMEM columns always fit
+  // CTAs per SM: 3 x 128 threads leave 170 registers a thread (no spills)
+  // and 3 x 128 of the 512 TMEM columns; operand tiles, barriers and the
+  // per-point y and z weights take 48 KB, which also caps residency at four
+  // CTAs, so the TMEM columns of every resident CTA always fit
+  static constexpr int CTAS = 3;
   static constexpr size_t SMEM = 48 * 1024;
   static_assert(1024 + 2 * TILE + 64 + 2 * S * 128 * 4 <= SMEM, "shared memory layout");
   static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NN >> 3) << 17) |
@@ -514,7 +531,7 @@ __device__ __forceinline__ void shift_weights(const float* w, int o, float* e) {
 }
 
 template <int W, class Pts>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, InterpTcCfg<W>::CTAS)
 interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
                  const uint32_t* __restrict__ sorted, const int4* __restrict__ subs, int* __restrict__ nsubs,
                  float* __restrict__ out, int* err) {
@@ -589,16 +606,19 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
       *reinterpret_cast<float4*>(Bs + swz128(n, c + 4)) = lo;
     }
     bool aborted = false;
+    // loads run one block ahead: the next block's id is fetched while this
+    // block is staged, its orientation and pixel while this block's MMA runs
+    uint32_t id = t < sub.z ? __ldg(sorted + sub.y + t) : 0u;
+    typename Pts::Raw raw = pts.load(id);
     for (int base = 0; base < sub.z; base += C::PTS) {
       const int i = base + t;
       const bool valid = i < sub.z;
-      uint32_t id = 0;
+      const uint32_t id_next = i + C::PTS < sub.z ? __ldg(sorted + sub.y + i + C::PTS) : 0u;
       bool ok = false;
       int ox = 0, oy = 0, oz = 0;
       float3 u = make_float3(0.f, 0.f, 0.f);
       if (valid) {
-        id = __ldg(sorted + sub.y + i);
-        u = pts(id);
+        u = pts.rotate(raw);
         const int cx = wrap1((int)ceilf(u.x - 0.5f * W) + C::H, nf);
         const int cy = wrap1((int)ceilf(u.y - 0.5f * W) + C::H, nf);
         const int cz = wrap1((int)ceilf(u.z - 0.5f * W) + C::H, nf);
@@ -652,6 +672,7 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
         mma_commit(bar);
         issued = true;
       }
+      raw = pts.load(id_next);
       mbar_wait(bar, phase, abort_flag, err);
       phase ^= 1u;
       tc_fence_after();
@@ -681,6 +702,7 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
 #pragma unroll
       for (int z = 0; z < S; ++z) acc = fmaf(az[z], Ez[z * 128 + t], acc);
       if (ok) out[id] = acc;
+      id = id_next;
       tc_fence_before();
       __syncthreads();
     }
@@ -724,11 +746,14 @@ struct SpreadCfg {
   static constexpr bool PAIR = W < 8;
   static constexpr int WZ = PAIR ? W + 1 : W;   // accumulated planes
   static constexpr int S = kBin + W - 1;   // cells per axis touched by a bin's points
+  // x is stored from the 4-aligned cell (bin corner - 4), so that the
+  // subgrid's rows go back to the fine grid as aligned 2- or 4-float vectors
+  static constexpr int PADX = kBin - H;
   static constexpr int ROWS = kBin + 7;    // rows reached by the (r, r + 4) lane rows
   static constexpr int RS = 16;
   static constexpr int PLANE = ROWS * RS;
   static constexpr int GRID = S * PLANE;
-  static constexpr int REC = 28;           // staged point: ox, oy, oz, v, wz[8], wx[8], wy[8]
+  static constexpr int REC = 28;           // staged point: key, -, -, -, wz[8], v wx[8], wy[8]
   static constexpr int STAGE = 32 * REC;
   static constexpr int WARPS = 20;
   static constexpr size_t SMEM = (size_t)WARPS * (GRID + STAGE) * sizeof(float);
@@ -740,7 +765,7 @@ template <int W>
 __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int lz, int r, int dx,
                                               float (&acc)[SpreadCfg<W>::WZ][2]) {
   using C = SpreadCfg<W>;
-  const int a0 = swz(ly + r, lx + dx), a1 = swz(ly + r + 4, lx + dx);
+  const int a0 = swz(ly + r, C::PADX + lx + dx), a1 = swz(ly + r + 4, C::PADX + lx + dx);
   float* p = grid + lz * C::PLANE;
 #pragma unroll
   for (int dz = 0; dz < C::WZ; ++dz) {
@@ -773,7 +798,7 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
     if (s >= nsub) break;
     const int4 sub = subs[s];
     const int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
-    int cur = -1, cx0 = 0, cy0 = 0, cz0 = 0;
+    int cur = -1;   // window corner (x | y << 4 | z << 8) of the points in acc
     float acc[C::WZ][2];
 #pragma unroll
     for (int dz = 0; dz < C::WZ; ++dz) acc[dz][0] = acc[dz][1] = 0.f;
@@ -794,34 +819,35 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
       vA = base + 32 + lane < sub.z ? str(idB) : 0.f;
       idA = idB;
       if (base + 64 + lane < sub.z) idB = __ldg(ids + base + 64 + lane);
-      // stage: lane k prepares point base + k
-      if (lane < nb) {
-        float* rec = stage + lane * C::REC;
-        if (v == 0.f) {                       // contributes nothing: skip its weights
-          rec[3] = 0.f;
-          goto staged;
-        }
-        {
+      // stage: lane k prepares point base + k; points that contribute are
+      // packed to the front of the stage in order
+      bool keep = lane < nb && v != 0.f;
+      int key = 0, sx = 0, sy = 0, sz = 0;
+      float wx[W], wy[W], wz[W];
+      if (keep) {
         const float3 u = pts(id);
-        float wx[W], wy[W], wz[W];
         const int lx = es_weights<W>(u.x, ep, wx);
         const int ly = es_weights<W>(u.y, ep, wy);
         const int lz = es_weights<W>(u.z, ep, wz);
         // tap-origin cell, wrapped; its position inside the bin is the local origin
         const int cx = wrap1(lx + C::H, nf), cy = wrap1(ly + C::H, nf), cz = wrap1(lz + C::H, nf);
-        int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);
+        const int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);
         if ((cx >> kBinLog) != bx || (cy >> kBinLog) != by || (cz >> kBinLog) != bz) {
           atomicOr(err, 1);   // cannot happen when sorting and spreading agree
-          v = 0.f;
-          ox = oy = oz = 0;
+          keep = false;
         }
         // window corner (the pair block's even corner under PAIR) and the
         // point's shift inside the window
-        const int sx = C::PAIR ? (ox & 1) : 0, sy = C::PAIR ? (oy & 1) : 0, sz = C::PAIR ? (oz & 1) : 0;
-        rec[0] = __int_as_float(ox - sx);
-        rec[1] = __int_as_float(oy - sy);
-        rec[2] = __int_as_float(oz - sz);
-        rec[3] = v;
+        sx = C::PAIR ? (ox & 1) : 0;
+        sy = C::PAIR ? (oy & 1) : 0;
+        sz = C::PAIR ? (oz & 1) : 0;
+        key = (ox - sx) | ((oy - sy) << 4) | ((oz - sz) << 8);
+      }
+      const unsigned kept = __ballot_sync(0xffffffffu, keep);
+      const int nrec = __popc(kept);
+      if (keep) {
+        float* rec = stage + __popc(kept & ((1u << lane) - 1u)) * C::REC;
+        rec[0] = __int_as_float(key);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
           const float z0 = d < W ? wz[d] : 0.f, x0 = d < W ? wx[d] : 0.f, y0 = d < W ? wy[d] : 0.f;
@@ -829,51 +855,61 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
           const float x1 = d >= 1 && d - 1 < W ? wx[d - 1] : 0.f;
           const float y1 = d >= 1 && d - 1 < W ? wy[d - 1] : 0.f;
           rec[4 + d] = sz ? z1 : z0;
-          rec[12 + d] = sx ? x1 : x0;
+          rec[12 + d] = v * (sx ? x1 : x0);      // strength folded into the x weights
           rec[20 + d] = sy ? y1 : y0;
         }
-        }
-      staged:;
       }
       __syncwarp();
-      for (int k = 0; k < nb; ++k) {
+      for (int k = 0; k < nrec; ++k) {
         const float* rec = stage + k * C::REC;
-        const int4 hdr = *reinterpret_cast<const int4*>(rec);
-        if (__int_as_float(hdr.w) == 0.f) continue;   // uniform: every lane reads record k
-        const int key = hdr.x | (hdr.y << 4) | (hdr.z << 8);
-        if (key != cur) {
-          if (cur >= 0) flush_columns<W>(grid, cx0, cy0, cz0, r, dx, acc);
-          cur = key;
-          cx0 = hdr.x;
-          cy0 = hdr.y;
-          cz0 = hdr.z;
+        const int key_k = __float_as_int(rec[0]);   // uniform: every lane reads record k
+        if (key_k != cur) {
+          if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
+          cur = key_k;
         }
-        const float a = __int_as_float(hdr.w) * rec[12 + dx];
+        const float a = rec[12 + dx];
         const float c0 = a * rec[20 + r];
         const float c1 = a * rec[24 + r];
         const float4 z0 = *reinterpret_cast<const float4*>(rec + 4);
         const float4 z1 = *reinterpret_cast<const float4*>(rec + 8);
-        const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+        const float wzk[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
         for (int dz = 0; dz < C::WZ; ++dz) {
-          acc[dz][0] = fmaf(wz[dz], c0, acc[dz][0]);
-          acc[dz][1] = fmaf(wz[dz], c1, acc[dz][1]);
+          acc[dz][0] = fmaf(wzk[dz], c0, acc[dz][0]);
+          acc[dz][1] = fmaf(wzk[dz], c1, acc[dz][1]);
         }
       }
       __syncwarp();
     }
-    if (cur >= 0) flush_columns<W>(grid, cx0, cy0, cz0, r, dx, acc);
+    if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
     __syncwarp();
-    // add the subgrid to the fine grid and clear it
-    const int ox = bx * kBin - C::H, oy = by * kBin - C::H, oz = bz * kBin - C::H;
-    for (int c = lane; c < C::S * C::S * C::S; c += 32) {
-      const int x = c % C::S, y = (c / C::S) % C::S, z = c / (C::S * C::S);
-      float* p = grid + z * C::PLANE + swz(y, x);
-      const float val = *p;
-      if (val != 0.f) {
-        *p = 0.f;
-        const int gx = wrap1(ox + x, nf), gy = wrap1(oy + y, nf), gz = wrap1(oz + z, nf);
-        atomicAdd(out + ((size_t)gz * nf + gy) * nf + gx, val);
+    // add the subgrid to the fine grid and clear it: rows of 12 stored x
+    // cells from the 4-aligned cell bin corner - 4, as 3 float4 (n_f = 0 mod
+    // 4) or 6 float2 (n_f = 2 mod 4) vector reductions, skipping zero vectors
+    const int ox = bx * kBin - kBin, oy = by * kBin - C::H, oz = bz * kBin - C::H;
+    if ((nf & 3) == 0) {
+      for (int task = lane; task < C::S * C::S * 3; task += 32) {
+        const int row = task / 3, m = task - 3 * row;
+        const int y = row % C::S, z = row / C::S;
+        float4* p = reinterpret_cast<float4*>(grid + z * C::PLANE + swz(y, 4 * m));
+        const float4 val = *p;
+        if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f) {
+          *p = make_float4(0.f, 0.f, 0.f, 0.f);
+          const int gx = wrap1(ox + 4 * m, nf), gy = wrap1(oy + y, nf), gz = wrap1(oz + z, nf);
+          atomicAdd(reinterpret_cast<float4*>(out + ((size_t)gz * nf + gy) * nf + gx), val);
+        }
+      }
+    } else {
+      for (int task = lane; task < C::S * C::S * 6; task += 32) {
+        const int row = task / 6, m = task - 6 * row;
+        const int y = row % C::S, z = row / C::S;
+        float2* p = reinterpret_cast<float2*>(grid + z * C::PLANE + swz(y, 2 * m));
+        const float2 val = *p;
+        if (val.x != 0.f || val.y != 0.f) {
+          *p = make_float2(0.f, 0.f);
+          const int gx = wrap1(ox + 2 * m, nf), gy = wrap1(oy + y, nf), gz = wrap1(oz + z, nf);
+          atomicAdd(reinterpret_cast<float2*>(out + ((size_t)gz * nf + gy) * nf + gx), val);
+        }
       }
     }
     __syncwarp();
@@ -960,7 +996,7 @@ int interp_tc(spf_plan* P, Pts pts, const SortedSet& set, float* out, cudaStream
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   return launch("interp_tc_kernel", s, [&] {
-    interp_tc_kernel<W, Pts><<<4 * sms, 128, C::SMEM, s>>>(g.real, pts, geom, ep, set.ids, set.subs,
+    interp_tc_kernel<W, Pts><<<C::CTAS * sms, 128, C::SMEM, s>>>(g.real, pts, geom, ep, set.ids, set.subs,
                                                            set.nsubs, out, P->err);
   });
 }
