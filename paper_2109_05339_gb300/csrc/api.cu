@@ -551,6 +551,7 @@ static void points_free(spf_points* S) {
   cudaFree(S->setT.ids);
   cudaFree(S->setT.subs);
   cudaFree(S->setT.nsubs);
+  cudaFree(S->invN);
   cudaFree(S->cls);
   cudaFree(S->cnt);
   delete S;
@@ -587,6 +588,7 @@ int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int 
   A((void**)&S->setT.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
   A((void**)&S->setT.subs, sizeof(int4) * S->setT.max_subs, "subproblems");
   A((void**)&S->setT.nsubs, 2 * sizeof(int), "subproblem count");
+  A((void**)&S->invN, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "inverse order");
   A((void**)&S->cls, sizeof(float) * std::max<int64_t>(npts, 1), "class sums");
   A((void**)&S->cnt, sizeof(float) * std::max(M, 1), "class counts");
   if (rc != SPF_OK) {

@@ -120,16 +120,21 @@ struct ExplicitPts {
 };
 
 // ---------------------------------------------------------- strengths -----
-struct StrPtr {
+// Strength of the point with id `id` at position `pos` of the sorted order.
+struct StrPtr {        // v[id]
   const float* v;
-  __device__ __forceinline__ float operator()(uint32_t id) const { return __ldg(v + id); }
+  __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const { return __ldg(v + id); }
+};
+struct StrSorted {     // v[pos]: strengths stored in the sorted order (coalesced)
+  const float* v;
+  __device__ __forceinline__ float operator()(uint32_t, uint32_t pos) const { return __ldg(v + pos); }
 };
 struct StrImage {      // D[p] * scale * image[id]
   const float* img;
   const float* D;
   FastDiv P2;
   float scale;
-  __device__ __forceinline__ float operator()(uint32_t id) const {
+  __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const {
     float v = scale * __ldg(img + id);
     return D ? v * __ldg(D + (id - P2.div(id) * P2.d)) : v;
   }
@@ -137,7 +142,7 @@ struct StrImage {      // D[p] * scale * image[id]
 struct StrWeights {    // D[p] (ones if D is NULL)
   const float* D;
   FastDiv P2;
-  __device__ __forceinline__ float operator()(uint32_t id) const {
+  __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const {
     return D ? __ldg(D + (id - P2.div(id) * P2.d)) : 1.f;
   }
 };
@@ -146,7 +151,7 @@ struct StrCount {     // D[p] * count[j] for point id = j * P2 + p
   const float* cnt;
   const float* D;
   FastDiv P2;
-  __device__ __forceinline__ float operator()(uint32_t id) const {
+  __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const {
     const uint32_t j = P2.div(id);
     const float c = __ldg(cnt + j);
     return D ? c * __ldg(D + (id - j * P2.d)) : c;
@@ -360,25 +365,35 @@ __global__ void build_subs_kernel(const int* __restrict__ start, int nbins, int4
   for (int q = 0; q < k; ++q) subs[o + q] = make_int4(b, s0 + q * kSubPts, min(kSubPts, c - q * kSubPts), 0);
 }
 
-// Class sums: cls[j][p] += b_scale D[p] img[i][p] and cnt[j] += 1 for every
-// image i whose orientation index oidx[i] - off = j is in [0, M). One block
-// per (image, 1024-pixel chunk).
+// Class sums: cls[inv[j P2 + p]] += b_scale D[p] img[i][p] and cnt[j] += 1
+// for every image i whose orientation index oidx[i] - off = j is in [0, M),
+// i.e. the class sums in the sorted order of the points (inv maps a point id
+// to its sorted position), so that spreading reads them coalesced. Only
+// nonzero pixels are added (photon-count images are sparse). One block per
+// (image, 1024-pixel chunk).
 __global__ void class_sum_kernel(const float* __restrict__ img, const int* __restrict__ oidx, int n_img,
                                  int off, int M, int P2, const float* __restrict__ D, float b_scale,
-                                 float* __restrict__ cls, float* __restrict__ cnt) {
+                                 const uint32_t* __restrict__ inv, float* __restrict__ cls,
+                                 float* __restrict__ cnt) {
   const int chunks = (P2 + 1023) / 1024;
   const int i = blockIdx.x / chunks, c = blockIdx.x - i * chunks;
   if (i >= n_img) return;
   const int j = __ldg(oidx + i) - off;
   if (j < 0 || j >= M) return;
   const float* row = img + (size_t)i * P2;
-  float* dst = cls + (size_t)j * P2;
+  const uint32_t* pos = inv + (size_t)j * P2;
   for (int p = c * 1024 + threadIdx.x; p < min(P2, (c + 1) * 1024); p += blockDim.x) {
     float v = b_scale * __ldg(row + p);
     if (D) v *= __ldg(D + p);
-    if (v != 0.f) atomicAdd(dst + p, v);
+    if (v != 0.f) atomicAdd(cls + __ldg(pos + p), v);
   }
   if (c == 0 && threadIdx.x == 0) atomicAdd(cnt + j, 1.f);
+}
+
+// inv[ids[i]] = i: sorted position of every point id.
+__global__ void inverse_order_kernel(const uint32_t* __restrict__ ids, int64_t n, uint32_t* __restrict__ inv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    inv[__ldg(ids + i)] = (uint32_t)i;
 }
 
 // ------------------------------------------------------------ type 2 ------
@@ -755,8 +770,11 @@ struct SpreadCfg {
   static constexpr int GRID = S * PLANE;
   static constexpr int REC = 28;           // staged point: key, -, -, -, wz[8], v wx[8], wy[8]
   static constexpr int STAGE = 32 * REC;
-  static constexpr int WARPS = 20;
-  static constexpr size_t SMEM = (size_t)WARPS * (GRID + STAGE) * sizeof(float);
+  static constexpr int QUEUE = 2 * 64;     // up to 63 queued (id, strength) pairs
+  static constexpr int PER_WARP = GRID + STAGE + QUEUE;
+  static constexpr int WARPS = W < 8 ? 20 : 19;
+  static constexpr size_t SMEM = (size_t)WARPS * PER_WARP * sizeof(float);
+  static_assert(SMEM <= 227 * 1024, "shared memory per block");
 };
 
 __device__ __forceinline__ int swz(int R, int c) { return R * 16 + (c ^ (((R >> 1) & 1) << 3)); }
@@ -776,6 +794,79 @@ __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int l
   }
 }
 
+// Stage points q[0 .. n) of the queue (lane k: point k) and add them to the
+// register accumulators in order, writing the accumulators back to the
+// subgrid whenever the window corner changes.
+template <int W, class Pts>
+__device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, int nf, int bx, int by, int bz,
+                                             const uint2* queue, int n, float* stage, float* grid, int lane,
+                                             int r, int dx, int& cur, float (&acc)[SpreadCfg<W>::WZ][2],
+                                             int* err) {
+  using C = SpreadCfg<W>;
+  bool keep = lane < n;
+  int key = 0, sx = 0, sy = 0, sz = 0;
+  float v = 0.f;
+  float wx[W], wy[W], wz[W];
+  if (keep) {
+    const uint2 e = queue[lane];
+    v = __uint_as_float(e.y);
+    const float3 u = pts(e.x);
+    const int lx = es_weights<W>(u.x, ep, wx);
+    const int ly = es_weights<W>(u.y, ep, wy);
+    const int lz = es_weights<W>(u.z, ep, wz);
+    // tap-origin cell, wrapped; its position inside the bin is the local origin
+    const int cx = wrap1(lx + C::H, nf), cy = wrap1(ly + C::H, nf), cz = wrap1(lz + C::H, nf);
+    const int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);
+    if ((cx >> kBinLog) != bx || (cy >> kBinLog) != by || (cz >> kBinLog) != bz) {
+      atomicOr(err, 1);   // cannot happen when sorting and spreading agree
+      keep = false;
+    }
+    // window corner (the pair block's even corner under PAIR) and the
+    // point's shift inside the window
+    sx = C::PAIR ? (ox & 1) : 0;
+    sy = C::PAIR ? (oy & 1) : 0;
+    sz = C::PAIR ? (oz & 1) : 0;
+    key = (ox - sx) | ((oy - sy) << 4) | ((oz - sz) << 8);
+  }
+  const unsigned kept = __ballot_sync(0xffffffffu, keep);
+  const int nrec = __popc(kept);
+  if (keep) {
+    float* rec = stage + __popc(kept & ((1u << lane) - 1u)) * C::REC;
+    rec[0] = __int_as_float(key);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const float z0 = d < W ? wz[d] : 0.f, x0 = d < W ? wx[d] : 0.f, y0 = d < W ? wy[d] : 0.f;
+      const float z1 = d >= 1 && d - 1 < W ? wz[d - 1] : 0.f;
+      const float x1 = d >= 1 && d - 1 < W ? wx[d - 1] : 0.f;
+      const float y1 = d >= 1 && d - 1 < W ? wy[d - 1] : 0.f;
+      rec[4 + d] = sz ? z1 : z0;
+      rec[12 + d] = v * (sx ? x1 : x0);      // strength folded into the x weights
+      rec[20 + d] = sy ? y1 : y0;
+    }
+  }
+  __syncwarp();
+  for (int k = 0; k < nrec; ++k) {
+    const float* rec = stage + k * C::REC;
+    const int key_k = __float_as_int(rec[0]);   // uniform: every lane reads record k
+    if (key_k != cur) {
+      if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
+      cur = key_k;
+    }
+    const float a = rec[12 + dx];
+    const float c0 = a * rec[20 + r];
+    const float c1 = a * rec[24 + r];
+    const float4 z0 = *reinterpret_cast<const float4*>(rec + 4);
+    const float4 z1 = *reinterpret_cast<const float4*>(rec + 8);
+    const float wzk[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+    for (int dz = 0; dz < C::WZ; ++dz) {
+      acc[dz][0] = fmaf(wzk[dz], c0, acc[dz][0]);
+      acc[dz][1] = fmaf(wzk[dz], c1, acc[dz][1]);
+    }
+  }
+  __syncwarp();
+}
+
 template <int W, class Pts, class Str>
 __global__ void __launch_bounds__(32 * SpreadCfg<W>::WARPS, 1)
 spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restrict__ sorted,
@@ -784,8 +875,9 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* grid = smem + warp * (C::GRID + C::STAGE);
+  float* grid = smem + warp * C::PER_WARP;
   float* stage = grid + C::GRID;
+  uint2* queue = reinterpret_cast<uint2*>(stage + C::STAGE);
   const int r = lane >> 3, dx = lane & 7;
   const int nf = g.nf;
   for (int c = lane; c < C::GRID; c += 32) grid[c] = 0.f;
@@ -802,85 +894,41 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
     float acc[C::WZ][2];
 #pragma unroll
     for (int dz = 0; dz < C::WZ; ++dz) acc[dz][0] = acc[dz][1] = 0.f;
-    // software pipeline of the global loads: ids two batches ahead, their
-    // strengths one batch ahead of the batch being staged
+    // Points with nonzero strength are queued (in order) and staged 32 at a
+    // time, so the weights are computed for contributing points only. The
+    // global loads run ahead: ids two chunks, strengths one chunk.
     const uint32_t* ids = sorted + sub.y;
+    const uint32_t pos0 = (uint32_t)sub.y;
     uint32_t idA = 0, idB = 0;
     float vA = 0.f;
     if (lane < sub.z) {
       idA = __ldg(ids + lane);
-      vA = str(idA);
+      vA = str(idA, pos0 + lane);
     }
     if (32 + lane < sub.z) idB = __ldg(ids + 32 + lane);
+    int q = 0;   // queued points
     for (int base = 0; base < sub.z; base += 32) {
-      const int nb = min(32, sub.z - base);
       const uint32_t id = idA;
-      float v = vA;
-      vA = base + 32 + lane < sub.z ? str(idB) : 0.f;
+      const float v = vA;
+      vA = base + 32 + lane < sub.z ? str(idB, pos0 + base + 32 + lane) : 0.f;
       idA = idB;
       if (base + 64 + lane < sub.z) idB = __ldg(ids + base + 64 + lane);
-      // stage: lane k prepares point base + k; points that contribute are
-      // packed to the front of the stage in order
-      bool keep = lane < nb && v != 0.f;
-      int key = 0, sx = 0, sy = 0, sz = 0;
-      float wx[W], wy[W], wz[W];
-      if (keep) {
-        const float3 u = pts(id);
-        const int lx = es_weights<W>(u.x, ep, wx);
-        const int ly = es_weights<W>(u.y, ep, wy);
-        const int lz = es_weights<W>(u.z, ep, wz);
-        // tap-origin cell, wrapped; its position inside the bin is the local origin
-        const int cx = wrap1(lx + C::H, nf), cy = wrap1(ly + C::H, nf), cz = wrap1(lz + C::H, nf);
-        const int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);
-        if ((cx >> kBinLog) != bx || (cy >> kBinLog) != by || (cz >> kBinLog) != bz) {
-          atomicOr(err, 1);   // cannot happen when sorting and spreading agree
-          keep = false;
-        }
-        // window corner (the pair block's even corner under PAIR) and the
-        // point's shift inside the window
-        sx = C::PAIR ? (ox & 1) : 0;
-        sy = C::PAIR ? (oy & 1) : 0;
-        sz = C::PAIR ? (oz & 1) : 0;
-        key = (ox - sx) | ((oy - sy) << 4) | ((oz - sz) << 8);
-      }
-      const unsigned kept = __ballot_sync(0xffffffffu, keep);
-      const int nrec = __popc(kept);
-      if (keep) {
-        float* rec = stage + __popc(kept & ((1u << lane) - 1u)) * C::REC;
-        rec[0] = __int_as_float(key);
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-          const float z0 = d < W ? wz[d] : 0.f, x0 = d < W ? wx[d] : 0.f, y0 = d < W ? wy[d] : 0.f;
-          const float z1 = d >= 1 && d - 1 < W ? wz[d - 1] : 0.f;
-          const float x1 = d >= 1 && d - 1 < W ? wx[d - 1] : 0.f;
-          const float y1 = d >= 1 && d - 1 < W ? wy[d - 1] : 0.f;
-          rec[4 + d] = sz ? z1 : z0;
-          rec[12 + d] = v * (sx ? x1 : x0);      // strength folded into the x weights
-          rec[20 + d] = sy ? y1 : y0;
-        }
-      }
+      const bool nz = base + lane < sub.z && v != 0.f;
+      const unsigned m = __ballot_sync(0xffffffffu, nz);
+      if (nz) queue[q + __popc(m & ((1u << lane) - 1u))] = make_uint2(id, __float_as_uint(v));
+      q += __popc(m);
       __syncwarp();
-      for (int k = 0; k < nrec; ++k) {
-        const float* rec = stage + k * C::REC;
-        const int key_k = __float_as_int(rec[0]);   // uniform: every lane reads record k
-        if (key_k != cur) {
-          if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
-          cur = key_k;
-        }
-        const float a = rec[12 + dx];
-        const float c0 = a * rec[20 + r];
-        const float c1 = a * rec[24 + r];
-        const float4 z0 = *reinterpret_cast<const float4*>(rec + 4);
-        const float4 z1 = *reinterpret_cast<const float4*>(rec + 8);
-        const float wzk[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
-#pragma unroll
-        for (int dz = 0; dz < C::WZ; ++dz) {
-          acc[dz][0] = fmaf(wzk[dz], c0, acc[dz][0]);
-          acc[dz][1] = fmaf(wzk[dz], c1, acc[dz][1]);
-        }
+      if (q >= 32) {
+        spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, 32, stage, grid, lane, r, dx, cur, acc, err);
+        uint2 tail = make_uint2(0u, 0u);
+        if (lane < q - 32) tail = queue[32 + lane];
+        __syncwarp();
+        if (lane < q - 32) queue[lane] = tail;
+        q -= 32;
+        __syncwarp();
       }
-      __syncwarp();
     }
+    if (q > 0) spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, q, stage, grid, lane, r, dx, cur, acc, err);
     if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
     __syncwarp();
     // add the subgrid to the fine grid and clear it: rows of 12 stored x
@@ -1189,6 +1237,9 @@ int points_build(spf_plan* P, spf_points* S, cudaStream_t s) {
   const float4* q4 = reinterpret_cast<const float4*>(S->quats);
   QuatPts pn{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
   SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->g, pn, npts, S->setN, P->err, s))));
+  SPF_TRY(launch("inverse_order_kernel", s, [&] {
+    inverse_order_kernel<<<grid_for(npts), 256, 0, s>>>(S->setN.ids, npts, S->invN);
+  }));
   QuatPts pt{q4, S->qlab, FastDiv((uint32_t)S->P2), P->gT.cells_per_q, nullptr, 0, P->err, (float)P->gT.nf, 1.f / (float)P->gT.nf};
   SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->gT, pt, npts, S->setT, P->err, s))));
   return SPF_OK;
@@ -1214,15 +1265,15 @@ int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oid
     const int64_t blocks = (int64_t)n_img * chunks;
     SPF_TRY(launch("class_sum_kernel", s, [&] {
       class_sum_kernel<<<(unsigned)blocks, 256, 0, s>>>(images, oidx, n_img, off, S->M, S->P2, D, b_scale,
-                                                        S->cls, S->cnt);
+                                                        S->invN, S->cls, S->cnt);
     }));
   }
   const float4* q4 = reinterpret_cast<const float4*>(S->quats);
   if (rhs) {
     QuatPts pts{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
-    StrPtr str{S->cls};
-    SPF_W_SWITCH(P->w, SPF_TRY((spread_sorted<W, QuatPts, StrPtr>(P, P->g, pts, str, npts, S->setN,
-                                                                 P->err, s))));
+    StrSorted str{S->cls};
+    SPF_W_SWITCH(P->w, SPF_TRY((spread_sorted<W, QuatPts, StrSorted>(P, P->g, pts, str, npts, S->setN,
+                                                                    P->err, s))));
     SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
   }
   if (kernel_hat) {

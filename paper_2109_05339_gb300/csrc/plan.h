@@ -92,7 +92,8 @@ struct spf_points {
   float* qlab = nullptr;      // P2 x 3 copy
   spf::SortedSet setN;        // N-mode grid (slicing, right-hand side)
   spf::SortedSet setT;        // (2N-1)-mode grid (Toeplitz kernel)
-  float* cls = nullptr;       // M x P2 class sums of weighted images
+  uint32_t* invN = nullptr;   // position of point id in setN's sorted order
+  float* cls = nullptr;       // class sums of weighted images, in setN's sorted order
   float* cnt = nullptr;       // M class counts
 };
 
