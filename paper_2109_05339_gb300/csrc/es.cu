@@ -68,16 +68,16 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 // Polynomial form of the kernel for the device. A point u has its first tap
 // at l0 = ceil(u - w/2); with x = l0 - (u - w/2) in [0, 1) tap d sits at
 // z_d = (2x + 2d - w) / w. Each phi(z_d(x)) is replaced by its Chebyshev
-// interpolant of degree w + 1 in t = 2x - 1 (nodes t_k = cos(pi (k + 1/2) /
-// (w + 2))), rewritten in powers of t for Horner's rule. This is the
-// piecewise-polynomial kernel evaluation of the FINUFFT library's published
-// method (Barnett, Magland and af Klinteberg, SIAM J. Sci. Comput. 41 (2019),
-// Sec. 3.1.1), with coefficients computed here in FP64. Its largest absolute
-// error is below exp(-beta) (the kernel's value at the support edge, where
-// the square root makes it non-smooth), e.g. 6e-8 for w = 7.
+// interpolant of degree es_degree(w) in t = 2x - 1 (nodes t_k = cos(pi (k +
+// 1/2) / (degree + 1))), rewritten in powers of t for Horner's rule. This is
+// the piecewise-polynomial kernel evaluation of the FINUFFT library's
+// published method (Barnett, Magland and af Klinteberg, SIAM J. Sci. Comput.
+// 41 (2019), Sec. 3.1.1), with coefficients computed here in FP64. The
+// largest absolute error (kernel peak 1) is 5e-6, 6e-7, 1.5e-7, 7e-9 for
+// w = 5, 6, 7, 8, i.e. below eps / 6 for eps = 10^(1 - w).
 void es_poly(int w, double beta, EsPoly* out) {
   *out = EsPoly();
-  const int P = w + 1, n = P + 1;
+  const int P = es_degree(w), n = P + 1;
   if (w < 1 || w > 8) return;
   for (int d = 0; d < w; ++d) {
     std::vector<double> f(n), a(n, 0.0);

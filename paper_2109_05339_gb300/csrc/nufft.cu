@@ -172,11 +172,12 @@ template <int W>
 __device__ __forceinline__ int es_weights(float u, const EsPoly& ep, float* wt) {
   const int l0 = (int)ceilf(u - 0.5f * W);
   const float t = 2.f * ((float)l0 - u + 0.5f * W) - 1.f;
+  constexpr int P = es_degree(W);
 #pragma unroll
   for (int d = 0; d < W; ++d) {
-    float v = ep.c[d][W + 1];
+    float v = ep.c[d][P];
 #pragma unroll
-    for (int i = W; i >= 0; --i) v = fmaf(v, t, ep.c[d][i]);
+    for (int i = P - 1; i >= 0; --i) v = fmaf(v, t, ep.c[d][i]);
     wt[d] = v;
   }
   return l0;
@@ -696,26 +697,47 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
         aborted = true;
         break;
       }
-      // T row -> c_p
-      float az[S], ey[S];
-#pragma unroll
-      for (int z = 0; z < S; ++z) {
-        az[z] = 0.f;
-        ey[z] = Ey[z * 128 + t];
-      }
-#pragma unroll
-      for (int ch = 0; ch < C::NN / 16; ++ch) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 16), v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int n = ch * 16 + e;
-          if (n < S * S) az[n / S] = fmaf(v[e], ey[n % S], az[n / S]);
-        }
-      }
+      // T row -> c_p: az[z] = sum_y T[z S + y] ey[y], c_p = sum_z az[z] ez[z];
+      // for even S the y sums take adjacent columns in packed FP32 pairs
       float acc = 0.f;
+      if constexpr (S % 2 == 0) {
+        float2 az[S], ey[S / 2];
 #pragma unroll
-      for (int z = 0; z < S; ++z) acc = fmaf(az[z], Ez[z * 128 + t], acc);
+        for (int k = 0; k < S / 2; ++k) ey[k] = make_float2(Ey[(2 * k) * 128 + t], Ey[(2 * k + 1) * 128 + t]);
+#pragma unroll
+        for (int z = 0; z < S; ++z) az[z] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int ch = 0; ch < C::NN / 16; ++ch) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 16), v);
+#pragma unroll
+          for (int e = 0; e < 16; e += 2) {
+            const int n = ch * 16 + e;
+            if (n < S * S) az[n / S] = __ffma2_rn(make_float2(v[e], v[e + 1]), ey[(n % S) / 2], az[n / S]);
+          }
+        }
+#pragma unroll
+        for (int z = 0; z < S; ++z) acc = fmaf(az[z].x + az[z].y, Ez[z * 128 + t], acc);
+      } else {
+        float az[S], ey[S];
+#pragma unroll
+        for (int z = 0; z < S; ++z) {
+          az[z] = 0.f;
+          ey[z] = Ey[z * 128 + t];
+        }
+#pragma unroll
+        for (int ch = 0; ch < C::NN / 16; ++ch) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 16), v);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int n = ch * 16 + e;
+            if (n < S * S) az[n / S] = fmaf(v[e], ey[n % S], az[n / S]);
+          }
+        }
+#pragma unroll
+        for (int z = 0; z < S; ++z) acc = fmaf(az[z], Ez[z * 128 + t], acc);
+      }
       if (ok) out[id] = acc;
       id = id_next;
       tc_fence_before();
@@ -760,6 +782,7 @@ struct SpreadCfg {
   static constexpr int H = W / 2;
   static constexpr bool PAIR = W < 8;
   static constexpr int WZ = PAIR ? W + 1 : W;   // accumulated planes
+  static constexpr int WZ2 = (WZ + 1) / 2;      // plane pairs (packed FP32 FMAs)
   static constexpr int S = kBin + W - 1;   // cells per axis touched by a bin's points
   // x is stored from the 4-aligned cell (bin corner - 4), so that the
   // subgrid's rows go back to the fine grid as aligned 2- or 4-float vectors
@@ -768,7 +791,9 @@ struct SpreadCfg {
   static constexpr int RS = 16;
   static constexpr int PLANE = ROWS * RS;
   static constexpr int GRID = S * PLANE;
-  static constexpr int REC = 28;           // staged point: key, -, -, -, wz[8], v wx[8], wy[8]
+  // staged point: key, -, -, -, wz[8], v wx[8], wy in lane-row order
+  // (wy[0], wy[4], wy[1], wy[5], ...: a lane's rows r and r + 4 side by side)
+  static constexpr int REC = 28;
   static constexpr int STAGE = 32 * REC;
   static constexpr int QUEUE = 2 * 64;     // up to 63 queued (id, strength) pairs
   static constexpr int PER_WARP = GRID + STAGE + QUEUE;
@@ -781,17 +806,18 @@ __device__ __forceinline__ int swz(int R, int c) { return R * 16 + (c ^ (((R >> 
 
 template <int W>
 __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int lz, int r, int dx,
-                                              float (&acc)[SpreadCfg<W>::WZ][2]) {
+                                              float2 (&acc)[SpreadCfg<W>::WZ2][2]) {
   using C = SpreadCfg<W>;
   const int a0 = swz(ly + r, C::PADX + lx + dx), a1 = swz(ly + r + 4, C::PADX + lx + dx);
   float* p = grid + lz * C::PLANE;
 #pragma unroll
   for (int dz = 0; dz < C::WZ; ++dz) {
-    p[dz * C::PLANE + a0] += acc[dz][0];
-    p[dz * C::PLANE + a1] += acc[dz][1];
-    acc[dz][0] = 0.f;
-    acc[dz][1] = 0.f;
+    const int q = dz >> 1;
+    p[dz * C::PLANE + a0] += (dz & 1) ? acc[q][0].y : acc[q][0].x;
+    p[dz * C::PLANE + a1] += (dz & 1) ? acc[q][1].y : acc[q][1].x;
   }
+#pragma unroll
+  for (int q = 0; q < C::WZ2; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
 }
 
 // Stage points q[0 .. n) of the queue (lane k: point k) and add them to the
@@ -800,7 +826,7 @@ __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int l
 template <int W, class Pts>
 __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, int nf, int bx, int by, int bz,
                                              const uint2* queue, int n, float* stage, float* grid, int lane,
-                                             int r, int dx, int& cur, float (&acc)[SpreadCfg<W>::WZ][2],
+                                             int r, int dx, int& cur, float2 (&acc)[SpreadCfg<W>::WZ2][2],
                                              int* err) {
   using C = SpreadCfg<W>;
   bool keep = lane < n;
@@ -841,7 +867,7 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
       const float y1 = d >= 1 && d - 1 < W ? wy[d - 1] : 0.f;
       rec[4 + d] = sz ? z1 : z0;
       rec[12 + d] = v * (sx ? x1 : x0);      // strength folded into the x weights
-      rec[20 + d] = sy ? y1 : y0;
+      rec[20 + 2 * (d & 3) + (d >> 2)] = sy ? y1 : y0;
     }
   }
   __syncwarp();
@@ -853,15 +879,17 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
       cur = key_k;
     }
     const float a = rec[12 + dx];
-    const float c0 = a * rec[20 + r];
-    const float c1 = a * rec[24 + r];
+    const float2 wy = *reinterpret_cast<const float2*>(rec + 20 + 2 * r);
+    const float c0 = a * wy.x, c1 = a * wy.y;
+    const float2 c00 = make_float2(c0, c0), c11 = make_float2(c1, c1);
     const float4 z0 = *reinterpret_cast<const float4*>(rec + 4);
     const float4 z1 = *reinterpret_cast<const float4*>(rec + 8);
-    const float wzk[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+    const float2 zp[4] = {make_float2(z0.x, z0.y), make_float2(z0.z, z0.w), make_float2(z1.x, z1.y),
+                          make_float2(z1.z, z1.w)};
 #pragma unroll
-    for (int dz = 0; dz < C::WZ; ++dz) {
-      acc[dz][0] = fmaf(wzk[dz], c0, acc[dz][0]);
-      acc[dz][1] = fmaf(wzk[dz], c1, acc[dz][1]);
+    for (int q = 0; q < C::WZ2; ++q) {
+      acc[q][0] = __ffma2_rn(zp[q], c00, acc[q][0]);
+      acc[q][1] = __ffma2_rn(zp[q], c11, acc[q][1]);
     }
   }
   __syncwarp();
@@ -891,9 +919,9 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
     const int4 sub = subs[s];
     const int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
     int cur = -1;   // window corner (x | y << 4 | z << 8) of the points in acc
-    float acc[C::WZ][2];
+    float2 acc[C::WZ2][2];   // [plane pair][row r, r + 4]
 #pragma unroll
-    for (int dz = 0; dz < C::WZ; ++dz) acc[dz][0] = acc[dz][1] = 0.f;
+    for (int q = 0; q < C::WZ2; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
     // Points with nonzero strength are queued (in order) and staged 32 at a
     // time, so the weights are computed for contributing points only. The
     // global loads run ahead: ids two chunks, strengths one chunk.

@@ -30,10 +30,11 @@ struct BinSort {
 
 // ES kernel weights as polynomials: tap d (0 <= d < w) of a point at
 // fractional offset x in [0, 1) has weight sum_i c[d][i] t^i, t = 2x - 1,
-// degree w + 1 (see es_poly).
+// of degree es_degree(w) (see es_poly).
 struct EsPoly {
   float c[8][10];
 };
+__host__ __device__ constexpr int es_degree(int w) { return w < 7 ? w + 1 : w; }
 
 struct Grid {
   int nf = 0;                // fine grid side
