@@ -37,7 +37,7 @@ CONFIG = "c2"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16", "fp8", "fp32"], default="bf16")
@@ -62,7 +62,7 @@ def workload_name(cfg, M, Ni):
 
 # ------------------------------------------------------------------ clocks --
 class Clocks:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 50 ms while the timed region runs."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -78,7 +78,7 @@ class Clocks:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -155,20 +155,18 @@ def roofline_for(kernel, launches, ms, ctx, peaks, src, clocks):
         return {"kernel": kernel, "bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock"}
     if kernel.startswith("interp") or kernel.startswith("spread"):
+        # w^3 taps per point, one FP32 multiply-add each, against the SMs'
+        # FP32 FMA rate (128 per clock per SM). The spreading accumulates taps
+        # in registers; the tensor-core interpolation contracts the window on
+        # the tensor cores and is bound by the per-point FP32 work around it.
         w = ctx["w"]
         pts = ctx["points_per_launch"][kernel.split("_")[0]]
         taps = pts * w ** 3
         mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        if kernel.startswith("interp"):
-            # one 4-byte L1 gather per tap; 32 words per clock per SM
-            peak = 152 * 32 * mhz * 1e6 / 1e9
-            src_ = "152 SMs x 32 L1 words/clock x median SM clock (one gather per tap)"
-        else:
-            # taps accumulate in registers: one FP32 FMA per tap, 128 per clock per SM
-            peak = 152 * 128 * mhz * 1e6 / 1e9
-            src_ = "152 SMs x 128 FP32 FMA/clock x median SM clock (one FMA per tap)"
+        peak = 152 * 128 * mhz * 1e6 / 1e9
         return {"kernel": kernel, "bound": "alu", "achieved": taps / avg_s / 1e9, "peak": peak,
-                "unit": "Gtap/s", "peak_source": src_}
+                "unit": "Gtap/s",
+                "peak_source": "152 SMs x 128 FP32 FMA/clock x median SM clock (one FMA per tap)"}
     # HBM-bound kernels: FFT passes etc.
     bytes_ = ctx.get("bytes_per_launch", {}).get(kernel)
     if bytes_ is None:

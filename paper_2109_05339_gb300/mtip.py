@@ -3,7 +3,12 @@ without phasing), as a sequence of C-ABI calls.
 
 The reference orientations are fixed across iterations (Sec. II-A), so their
 rotated detector points are sorted once per orientation chunk (PointSet) and
-reused by every iteration's slicing and merge.
+reused by every iteration's slicing and merge. A point set costs 16 bytes per
+(orientation, pixel); when the whole set would not fit the memory budget
+(e.g. the paper's 1.2 million orientations of 128 x 128 pixels, 315 GB) the
+driver streams instead: each chunk's points are sorted, sliced and matched,
+then released, and the merge spreads the images at their matched
+orientations (image chunks accumulate).
 
 1. Slicing (Sec. II-A) and matching (Sec. II-B), streamed in orientation
    chunks: each chunk of model images is sliced into one reusable buffer and
@@ -22,9 +27,16 @@ import torch
 from .api import Matcher, Plan, PointSet
 
 
+POINT_SET_BYTES = 16   # per (orientation, pixel): two sort orders, inverse order, class sum
+
+
 class MTIP:
     def __init__(self, N, qmax, P2, n_img, n_orient, orient_chunk=None, img_chunk=None,
-                 eps=1e-6, precision="bf16", topk=8, device=None):
+                 eps=1e-6, precision="bf16", topk=8, device=None, cache_points=None,
+                 point_budget_bytes=None):
+        """cache_points: keep every chunk's sorted points across iterations
+        (True), stream them (False), or decide from point_budget_bytes (None;
+        default budget: half of the device's free memory at construction)."""
         self.orient_chunk = min(n_orient, orient_chunk or n_orient)
         self.img_chunk = min(n_img, img_chunk or n_img)
         max_pts = max(self.orient_chunk, self.img_chunk) * P2
@@ -39,6 +51,12 @@ class MTIP:
         self.N, self.P2, self.n_img, self.n_orient = N, P2, n_img, n_orient
         self.sets = None
         self._key = None
+        if cache_points is None:
+            if point_budget_bytes is None:
+                free, _ = torch.cuda.mem_get_info(dev)
+                point_budget_bytes = free // 2
+            cache_points = POINT_SET_BYTES * n_orient * P2 <= point_budget_bytes
+        self.cache_points = bool(cache_points)
 
     def set_orientations(self, quats, q_lab):
         """Sort the points of every orientation chunk once (reused by later calls)."""
@@ -56,20 +74,38 @@ class MTIP:
         self._key = key
 
     def match(self, A, quats, q_lab, images, img_scale):
-        self.set_orientations(quats, q_lab)
         m = self.matcher
         m.set_images(images, img_scale)
-        for c0, ps in self.sets:
-            sl = self.slices[: ps.M]
+        if self.cache_points:
+            self.set_orientations(quats, q_lab)
+            for c0, ps in self.sets:
+                sl = self.slices[: ps.M]
+                ps.slice(A, out=sl)
+                m.add_slices(sl, orient_offset=c0)
+            return m.results()
+        M = quats.shape[0]
+        for c0 in range(0, M, self.orient_chunk):
+            c1 = min(M, c0 + self.orient_chunk)
+            ps = PointSet(self.plan, quats[c0:c1].contiguous(), q_lab)
+            sl = self.slices[: c1 - c0]
             ps.slice(A, out=sl)
             m.add_slices(sl, orient_offset=c0)
+            ps.close()
         return m.results()
 
     def merge(self, images, quats, best, q_lab, img_scale, D=None):
-        self.set_orientations(quats, q_lab)
-        for k, (c0, ps) in enumerate(self.sets):
-            ps.merge(images, best, orient_offset=c0, D=D, b_scale=img_scale, rhs=self.rhs,
-                     kernel_hat=self.khat, accumulate=k > 0)
+        if self.cache_points:
+            self.set_orientations(quats, q_lab)
+            for k, (c0, ps) in enumerate(self.sets):
+                ps.merge(images, best, orient_offset=c0, D=D, b_scale=img_scale, rhs=self.rhs,
+                         kernel_hat=self.khat, accumulate=k > 0)
+            return self.rhs, self.khat
+        n = images.shape[0]
+        for i0 in range(0, n, self.img_chunk):
+            i1 = min(n, i0 + self.img_chunk)
+            self.plan.merge_images(images[i0:i1], quats, q_lab, D=D, b_scale=img_scale, rhs=self.rhs,
+                                   kernel_hat=self.khat, accumulate=i0 > 0,
+                                   orient_idx=best[i0:i1].contiguous())
         return self.rhs, self.khat
 
     def iteration(self, A, quats, q_lab, images, img_scale, cg_iters, lam_rel=1e-3, D=None,
