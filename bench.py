@@ -254,8 +254,11 @@ def run_ours(args, rank, world):
     value = Ni * M * world / (ms / 1e3)
     # per-kernel table and the dominant kernel's roofline
     ctx = {"n_img": Ni, "n_orient_per_launch": drv.orient_chunk, "P2": P2, "precision": args.precision,
-           "w": drv.plan.w, "points_per_launch": {"interp": drv.orient_chunk * P2,
-                                                   "spread": drv.img_chunk * P2}}
+           "w": drv.plan.w, "points_per_launch": {
+               "interp": drv.orient_chunk * P2,
+               # class sums spread per cached orientation chunk; streaming
+               # spreads the images of one image chunk
+               "spread": (drv.orient_chunk if drv.cache_points else drv.img_chunk) * P2}}
     peaks, src = measured_peaks()
     kern = {k: {"launches": n / args.steps, "ms_per_step": t / args.steps} for k, (n, t) in prof.items()}
     dominant = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
@@ -291,7 +294,10 @@ def run_ours(args, rank, world):
         "config": {"workload": workload_name(cfg, M, Ni), "n_orient": M, "n_img": Ni, "N": cfg.N,
                    "detector": f"{cfg.P}x{cfg.P}", "cg_iters": cfg.cg_iters, "precision": args.precision,
                    "topk_rerank": 8, "nufft_eps": cfg.eps, "parallelism": f"dp{world} (image shards)",
-                   "l2": "inputs larger than L2 (images and slices 655 MB each)"},
+                   "l2": (f"inputs larger than L2 (images {Ni * P2 * 4 / 1e6:.0f} MB, slices "
+                          f"{drv.orient_chunk * P2 * 4 / 1e6:.0f} MB per chunk)"),
+                   "orient_chunk": drv.orient_chunk,
+                   "point_sets": "cached" if drv.cache_points else "streamed"},
         "nufft_mpts_per_s": {
             "slice_type2": (M * P2) / (stage.get("slice", 0) + 1e-12) / 1e3,
             "merge_type1_rhs_plus_kernel": (Ni * P2) / (stage.get("merge", 0) + 1e-12) / 1e3},

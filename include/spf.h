@@ -119,8 +119,11 @@ int spf_nufft_type1(spf_plan* plan, const float* v, const float* pts, int64_t np
  * change between M-TIP iterations, so slicing and merging reuse the sort.
  *
  * spf_points_create: copies quats (M x 4) and q_lab (P2 x 3) and sorts the
- *   M*P2 points (M*P2 < 2^31). Allocates about 16 bytes per point (two sort
- *   orders, class sums) -- a create call. Stream-ordered after the copies.
+ *   M*P2 points (M*P2 < 2^31). Allocates about 16 bytes per point (a sort
+ *   order for each grid, the inverse of the model-grid order, class sums) --
+ *   a create call. Stream-ordered after the copies. flags: 0, or
+ *   SPF_POINTS_SLICE_ONLY to sort for slicing alone (4 bytes per point; such a
+ *   set cannot merge: spf_merge_points returns SPF_ERR_ARG).
  * spf_slice_points: as spf_slice_model for the set's orientations;
  *   slices: M x P2.
  * spf_merge_points: Sec. II-C merge by class sums. Images whose orientation
@@ -135,8 +138,9 @@ int spf_nufft_type1(spf_plan* plan, const float* v, const float* pts, int64_t np
  *   with accumulate = 1). Either output may be NULL.
  * ------------------------------------------------------------------------- */
 typedef struct spf_points spf_points;
+#define SPF_POINTS_SLICE_ONLY 1
 int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int M, const float* q_lab,
-                      int P2, void* stream);
+                      int P2, int flags, void* stream);
 int spf_points_destroy(spf_points* pts);
 int spf_slice_points(spf_plan* plan, spf_points* pts, const float* A, float* slices, void* stream);
 int spf_merge_points(spf_plan* plan, spf_points* pts, const float* images, const int32_t* orient_idx,

@@ -48,7 +48,7 @@ PROTOTYPES = {
     "spf_nufft_type2": (I, [P, P, P, I64, P, P]),
     "spf_nufft_type1": (I, [P, P, P, I64, P, I, P]),
     "spf_merge_images": (I, [P, P, P, I, P, I, P, I, P, F, P, P, I, P]),
-    "spf_points_create": (I, [C.POINTER(P), P, P, I, P, I, P]),
+    "spf_points_create": (I, [C.POINTER(P), P, P, I, P, I, I, P]),
     "spf_points_destroy": (I, [P]),
     "spf_slice_points": (I, [P, P, P, P, P]),
     "spf_merge_points": (I, [P, P, P, P, I, I, P, F, P, P, I, P]),

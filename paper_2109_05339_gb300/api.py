@@ -220,7 +220,10 @@ class PointSet:
     """Rotated detector points of a fixed orientation set, sorted once (Sec. II-A:
     the model images live on a predetermined orientation set)."""
 
-    def __init__(self, plan: Plan, quats, q_lab):
+    SLICE_ONLY = 1   # SPF_POINTS_SLICE_ONLY
+
+    def __init__(self, plan: Plan, quats, q_lab, slice_only=False):
+        """slice_only: sort for slicing alone (4 bytes per point; no merge)."""
         d = plan.device
         _f32(quats, "quats", d)
         _f32(q_lab, "q_lab", d)
@@ -228,7 +231,7 @@ class PointSet:
         self.M, self.P2 = quats.shape[0], q_lab.shape[0]
         h = C.c_void_p()
         check(lib.spf_points_create(C.byref(h), plan._h, _ptr(quats), self.M, _ptr(q_lab), self.P2,
-                                    _stream(d)))
+                                    self.SLICE_ONLY if slice_only else 0, _stream(d)))
         self._h = h
 
     def close(self):

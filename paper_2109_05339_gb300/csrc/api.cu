@@ -558,7 +558,7 @@ static void points_free(spf_points* S) {
 }
 
 int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int M, const float* q_lab,
-                      int P2, void* stream) {
+                      int P2, int flags, void* stream) {
   clear_error();
   SPF_CHECK_ARG(out != nullptr, "out is NULL");
   *out = nullptr;
@@ -566,6 +566,7 @@ int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int 
   SPF_CHECK_ARG(M >= 0 && P2 > 0, "M >= 0 and P2 > 0 required");
   SPF_CHECK_ARG((int64_t)M * P2 <= 0x7fffffffLL, "M*P2 must be < 2^31");
   SPF_CHECK_ARG(q_lab && (M == 0 || quats), "NULL pointer");
+  SPF_CHECK_ARG(flags == 0 || flags == SPF_POINTS_SLICE_ONLY, "unknown flags %d", flags);
   DeviceScope dev(plan->device);
   if (dev.rc != SPF_OK) return dev.rc;
   spf_points* S = new spf_points();
@@ -573,6 +574,8 @@ int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int 
   S->device = plan->device;
   S->M = M;
   S->P2 = P2;
+  S->flags = flags;
+  const bool full = flags == 0;
   const int64_t npts = (int64_t)M * P2;
   int rc = SPF_OK;
   auto A = [&](void** p, size_t b, const char* w) {
@@ -585,12 +588,14 @@ int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int 
   A((void**)&S->setN.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
   A((void**)&S->setN.subs, sizeof(int4) * S->setN.max_subs, "subproblems");
   A((void**)&S->setN.nsubs, 2 * sizeof(int), "subproblem count");
-  A((void**)&S->setT.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
-  A((void**)&S->setT.subs, sizeof(int4) * S->setT.max_subs, "subproblems");
-  A((void**)&S->setT.nsubs, 2 * sizeof(int), "subproblem count");
-  A((void**)&S->invN, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "inverse order");
-  A((void**)&S->cls, sizeof(float) * std::max<int64_t>(npts, 1), "class sums");
-  A((void**)&S->cnt, sizeof(float) * std::max(M, 1), "class counts");
+  if (full) {
+    A((void**)&S->setT.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
+    A((void**)&S->setT.subs, sizeof(int4) * S->setT.max_subs, "subproblems");
+    A((void**)&S->setT.nsubs, 2 * sizeof(int), "subproblem count");
+    A((void**)&S->invN, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "inverse order");
+    A((void**)&S->cls, sizeof(float) * std::max<int64_t>(npts, 1), "class sums");
+    A((void**)&S->cnt, sizeof(float) * std::max(M, 1), "class counts");
+  }
   if (rc != SPF_OK) {
     points_free(S);
     return rc;
@@ -638,6 +643,7 @@ int spf_merge_points(spf_plan* plan, spf_points* pts, const float* images, const
   clear_error();
   SPF_TRY(check_plan(plan));
   SPF_CHECK_ARG(pts && pts->plan == plan, "point set is NULL or belongs to another plan");
+  SPF_CHECK_ARG(pts->flags == 0, "the point set was created for slicing only");
   SPF_CHECK_ARG(n_img >= 0 && (n_img == 0 || (images && orient_idx)), "NULL pointer");
   SPF_CHECK_ARG(rhs || kernel_hat, "rhs and kernel_hat are both NULL");
   DeviceScope dev(plan->device);

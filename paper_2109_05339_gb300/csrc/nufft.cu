@@ -1265,6 +1265,7 @@ int points_build(spf_plan* P, spf_points* S, cudaStream_t s) {
   const float4* q4 = reinterpret_cast<const float4*>(S->quats);
   QuatPts pn{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
   SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->g, pn, npts, S->setN, P->err, s))));
+  if (S->flags & SPF_POINTS_SLICE_ONLY) return SPF_OK;
   SPF_TRY(launch("inverse_order_kernel", s, [&] {
     inverse_order_kernel<<<grid_for(npts), 256, 0, s>>>(S->setN.ids, npts, S->invN);
   }));

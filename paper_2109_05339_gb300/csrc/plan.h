@@ -89,6 +89,7 @@ struct spf_points {
   spf_plan* plan = nullptr;
   int device = 0;
   int M = 0, P2 = 0;
+  int flags = 0;              // SPF_POINTS_SLICE_ONLY: setN only
   float* quats = nullptr;     // M x 4 copy
   float* qlab = nullptr;      // P2 x 3 copy
   spf::SortedSet setN;        // N-mode grid (slicing, right-hand side)

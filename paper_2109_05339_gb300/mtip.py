@@ -6,9 +6,9 @@ rotated detector points are sorted once per orientation chunk (PointSet) and
 reused by every iteration's slicing and merge. A point set costs 16 bytes per
 (orientation, pixel); when the whole set would not fit the memory budget
 (e.g. the paper's 1.2 million orientations of 128 x 128 pixels, 315 GB) the
-driver streams instead: each chunk's points are sorted, sliced and matched,
-then released, and the merge spreads the images at their matched
-orientations (image chunks accumulate).
+driver streams instead: each chunk's points are sorted (for slicing only,
+4 bytes per point), sliced and matched, then released, and the merge spreads
+the images at their matched orientations (image chunks accumulate).
 
 1. Slicing (Sec. II-A) and matching (Sec. II-B), streamed in orientation
    chunks: each chunk of model images is sliced into one reusable buffer and
@@ -38,8 +38,22 @@ class MTIP:
         (True), stream them (False), or decide from point_budget_bytes (None;
         default budget: half of the device's free memory at construction)."""
         self.orient_chunk = min(n_orient, orient_chunk or n_orient)
-        self.img_chunk = min(n_img, img_chunk or n_img)
-        max_pts = max(self.orient_chunk, self.img_chunk) * P2
+        if device is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        else:
+            dev = device if isinstance(device, torch.device) else torch.device("cuda", int(device))
+        if cache_points is None:
+            if point_budget_bytes is None:
+                free, _ = torch.cuda.mem_get_info(dev)
+                point_budget_bytes = free // 2
+            cache_points = POINT_SET_BYTES * n_orient * P2 <= point_budget_bytes
+        self.cache_points = bool(cache_points)
+        # the plan's own sort buffers serve per-call slicing of one orientation
+        # chunk and, when streaming, the merge of one image chunk (< 2^31 points)
+        self.img_chunk = min(n_img, img_chunk or n_img, (2 ** 31 - 1) // P2)
+        max_pts = self.orient_chunk * P2
+        if not self.cache_points:
+            max_pts = max(max_pts, self.img_chunk * P2)
         self.plan = Plan(N, qmax, eps, max_points=max_pts, device=device)
         self.device = self.plan.device
         self.matcher = Matcher(n_img, self.orient_chunk, P2, precision, topk, device=self.device)
@@ -51,12 +65,6 @@ class MTIP:
         self.N, self.P2, self.n_img, self.n_orient = N, P2, n_img, n_orient
         self.sets = None
         self._key = None
-        if cache_points is None:
-            if point_budget_bytes is None:
-                free, _ = torch.cuda.mem_get_info(dev)
-                point_budget_bytes = free // 2
-            cache_points = POINT_SET_BYTES * n_orient * P2 <= point_budget_bytes
-        self.cache_points = bool(cache_points)
 
     def set_orientations(self, quats, q_lab):
         """Sort the points of every orientation chunk once (reused by later calls)."""
@@ -86,7 +94,7 @@ class MTIP:
         M = quats.shape[0]
         for c0 in range(0, M, self.orient_chunk):
             c1 = min(M, c0 + self.orient_chunk)
-            ps = PointSet(self.plan, quats[c0:c1].contiguous(), q_lab)
+            ps = PointSet(self.plan, quats[c0:c1].contiguous(), q_lab, slice_only=True)
             sl = self.slices[: c1 - c0]
             ps.slice(A, out=sl)
             m.add_slices(sl, orient_offset=c0)

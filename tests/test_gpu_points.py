@@ -81,3 +81,14 @@ def test_orientation_chunks_accumulate(c1):
     # images outside every chunk leave the outputs at zero
     empty_r, empty_k = c1["ps"].merge(img, best + c1["M"], b_scale=0.5)
     assert float(empty_r.abs().max()) == 0.0 and float(empty_k.abs().max()) == 0.0
+
+
+def test_slice_only_set_slices_identically_and_refuses_merge(c1):
+    torch = c1["torch"]
+    from paper_2109_05339_gb300 import PointSet, SpfError
+    A = to_dev(c1["pb"].A.astype(np.float32))
+    ps = PointSet(c1["plan"], c1["quats"], c1["qlab"], slice_only=True)
+    assert torch.equal(ps.slice(A), c1["ps"].slice(A))
+    with pytest.raises(SpfError):
+        ps.merge(to_dev(c1["images"]), to_dev(c1["best"], torch.int32))
+    ps.close()
