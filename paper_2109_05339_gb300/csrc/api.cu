@@ -366,6 +366,9 @@ static void matcher_free(spf_matcher* m) {
   cudaFree(m->st_i);
   cudaFree(m->err);
   cudaFree(m->wbuf);
+  cudaFree(m->rr_key);
+  cudaFree(m->rr_start);
+  cudaFree(m->rr_order);
   delete m;
 }
 
@@ -400,6 +403,9 @@ int spf_matcher_create(spf_matcher** out, int max_images, int max_orient_chunk, 
   A((void**)&m->st_i, sizeof(int) * (size_t)max_images * topk, "running list");
   A((void**)&m->err, sizeof(int), "error word");
   A((void**)&m->wbuf, sizeof(float) * P2, "pixel weights");
+  A((void**)&m->rr_key, sizeof(int) * std::max(max_images, 1), "re-rank keys");
+  A((void**)&m->rr_start, sizeof(int) * ((size_t)max_orient_chunk + 1), "re-rank buckets");
+  A((void**)&m->rr_order, sizeof(int) * std::max(max_images, 1), "re-rank order");
   if (rc == SPF_OK && precision != SPF_FP32) {
     if (!match_tc_supported(device)) {
       set_error("tensor-core matching needs an sm_103 device");

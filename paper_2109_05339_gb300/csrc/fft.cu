@@ -6,7 +6,7 @@
 // 1D lines along one axis: the lines are staged through shared memory with
 // coalesced global accesses (whole rows for the contiguous axis; tiles of 8
 // or 16 neighbouring lines for the strided axes), transformed there by
-// self-sorting (Stockham) radix-2/3/4/5 passes with twiddles from an FP64-
+// self-sorting (Stockham) radix-2/3/4/5/9 passes with twiddles from an FP64-
 // built table, and written back in natural order. Three launches make a 3D
 // transform. Lines known to be all zero (zero-padded input) or whose output
 // is not needed (cropped output) are skipped.
@@ -88,6 +88,32 @@ __device__ __forceinline__ void dft<5>(float2* v, float sign) {
   v[4] = csub(r1, i1);
   v[2] = cadd(r2, i2);
   v[3] = csub(r2, i2);
+}
+
+// 9-point DFT as 3 x 3: with n = 3 n1 + n2 and k = k1 + 3 k2,
+// X[k1 + 3 k2] = sum_n2 w3^(n2 k2) [w9^(n2 k1) sum_n1 x[3 n1 + n2] w3^(n1 k1)],
+// w_m = exp(sign 2 pi i / m).
+template <>
+__device__ __forceinline__ void dft<9>(float2* v, float sign) {
+  const float c1 = 0.76604444311897803520f, s1 = 0.64278760968653932632f;   // 2 pi / 9
+  const float c2 = 0.17364817766693034885f, s2 = 0.98480775301220805936f;   // 4 pi / 9
+  const float c4 = -0.93969262078590838405f, s4 = 0.34202014332566873304f;  // 8 pi / 9
+  float2 a[3] = {v[0], v[3], v[6]}, b[3] = {v[1], v[4], v[7]}, c[3] = {v[2], v[5], v[8]};
+  dft<3>(a, sign);
+  dft<3>(b, sign);
+  dft<3>(c, sign);
+  b[1] = cmul(b[1], make_float2(c1, sign * s1));
+  b[2] = cmul(b[2], make_float2(c2, sign * s2));
+  c[1] = cmul(c[1], make_float2(c2, sign * s2));
+  c[2] = cmul(c[2], make_float2(c4, sign * s4));
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    float2 t[3] = {a[k1], b[k1], c[k1]};
+    dft<3>(t, sign);
+    v[k1] = t[0];
+    v[k1 + 3] = t[1];
+    v[k1 + 6] = t[2];
+  }
 }
 
 // One self-sorting pass of radix R over `lines` lines of length n in `buf`.
@@ -255,13 +281,13 @@ struct Rad {};
 
 template <int N>
 struct RadixPlan;
-template <> struct RadixPlan<36> { using type = Rad<4, 3, 3>; };
-template <> struct RadixPlan<72> { using type = Rad<4, 2, 3, 3>; };
-template <> struct RadixPlan<162> { using type = Rad<2, 3, 3, 3, 3>; };
-template <> struct RadixPlan<216> { using type = Rad<4, 2, 3, 3, 3>; };
+template <> struct RadixPlan<36> { using type = Rad<4, 9>; };
+template <> struct RadixPlan<72> { using type = Rad<4, 2, 9>; };
+template <> struct RadixPlan<162> { using type = Rad<2, 9, 9>; };
+template <> struct RadixPlan<216> { using type = Rad<4, 2, 3, 9>; };
 template <> struct RadixPlan<320> { using type = Rad<4, 4, 4, 5>; };
-template <> struct RadixPlan<324> { using type = Rad<4, 3, 3, 3, 3>; };
-template <> struct RadixPlan<432> { using type = Rad<4, 4, 3, 3, 3>; };
+template <> struct RadixPlan<324> { using type = Rad<4, 9, 9>; };
+template <> struct RadixPlan<432> { using type = Rad<4, 4, 3, 9>; };
 template <> struct RadixPlan<640> { using type = Rad<4, 4, 4, 2, 5>; };
 
 template <int N, int LINES, int R, int Ns>

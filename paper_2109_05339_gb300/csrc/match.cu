@@ -267,6 +267,73 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
 }
 
 // ------------------------------------------------------------ rerank -----
+// Re-rank order: images bucketed by the orientation of their best
+// approximate candidate (counting sort; bucket n_orient: no candidate).
+__global__ void rr_key_kernel(const float* __restrict__ cand_v, const int* __restrict__ cand_i, int n_img,
+                              int nsplit, int orient_offset, int n_orient, int* __restrict__ key,
+                              int* __restrict__ count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_img) return;
+  const size_t base = (size_t)i * kMaxSplits * kCand;
+  float bv = FLT_MAX;
+  int bj = -1;
+  for (int q = 0; q < nsplit * kCand; ++q) {
+    const int j = __ldg(cand_i + base + q);
+    const float v = __ldg(cand_v + base + q);
+    if (j >= 0 && (v < bv || (v == bv && j < bj))) {
+      bv = v;
+      bj = j;
+    }
+  }
+  int k = bj >= 0 ? bj - orient_offset : n_orient;
+  if (k < 0 || k > n_orient) k = n_orient;
+  key[i] = k;
+  atomicAdd(count + k, 1);
+}
+
+// Exclusive scan of n counts in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) rr_scan_kernel(int* __restrict__ c, int n) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < n ? c[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int y = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += t;
+      }
+      warp_sums[lane] = y;
+    }
+    __syncthreads();
+    const int excl = carry + (w > 0 ? warp_sums[w - 1] : 0) + x - v;
+    if (i < n) c[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+}
+
+__global__ void rr_scatter_kernel(const int* __restrict__ key, int n_img, int* __restrict__ start,
+                                  int* __restrict__ order) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_img) return;
+  order[atomicAdd(start + key[i], 1)] = i;
+}
+
 // One CTA per image: merge nsplit candidate lists, take the best topk by
 // approximate score, recompute them exactly, merge into the running list.
 template <int K>
@@ -274,8 +341,8 @@ __global__ void __launch_bounds__(256)
 rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict__ Y, int P2,
               int orient_offset, int n_orient, int nsplit, const float* __restrict__ cand_v,
               const int* __restrict__ cand_i, const float* __restrict__ wsq, float* __restrict__ st_d,
-              int* __restrict__ st_i) {
-  const int img = blockIdx.x;
+              int* __restrict__ st_i, const int* __restrict__ order) {
+  const int img = order ? __ldg(order + blockIdx.x) : blockIdx.x;
   __shared__ float s_v[K];
   __shared__ int s_i[K];
   if (threadIdx.x == 0) {
@@ -430,12 +497,26 @@ int state_reset(spf_matcher* m, cudaStream_t s) {
 int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
                   cudaStream_t s) {
   if (m->n_img == 0) return SPF_OK;
+  const int* order = nullptr;
+  if (m->rr_order && n_orient <= m->max_orient) {
+    const unsigned g = (unsigned)ceil_div(m->n_img, 256);
+    SPF_CUDA(cudaMemsetAsync(m->rr_start, 0, sizeof(int) * ((size_t)n_orient + 1), s));
+    SPF_TRY(launch("rr_key_kernel", s, [&] {
+      rr_key_kernel<<<g, 256, 0, s>>>(m->cand_v, m->cand_i, m->n_img, nsplit, orient_offset, n_orient,
+                                      m->rr_key, m->rr_start);
+    }));
+    SPF_TRY(launch("rr_scan_kernel", s, [&] { rr_scan_kernel<<<1, 1024, 0, s>>>(m->rr_start, n_orient + 1); }));
+    SPF_TRY(launch("rr_scatter_kernel", s, [&] {
+      rr_scatter_kernel<<<g, 256, 0, s>>>(m->rr_key, m->n_img, m->rr_start, m->rr_order);
+    }));
+    order = m->rr_order;
+  }
 #define SPF_RR(K)                                                                               \
   case K:                                                                                       \
     return launch("rerank_kernel", s, [&] {                                                     \
       rerank_kernel<K><<<m->n_img, 256, 0, s>>>(m->images, m->img_scale, slices, m->P2,         \
                                                 orient_offset, n_orient, nsplit, m->cand_v,     \
-                                                m->cand_i, m->wsq, m->st_d, m->st_i);           \
+                                                m->cand_i, m->wsq, m->st_d, m->st_i, order);    \
     });
   switch (m->topk) {
     SPF_RR(2) SPF_RR(3) SPF_RR(4) SPF_RR(5) SPF_RR(6) SPF_RR(7) SPF_RR(8)

@@ -27,6 +27,12 @@ struct spf_matcher {
   int* err = nullptr;             // device error word (bounded waits, bounds)
   float* wbuf = nullptr;          // P2 square roots of the pixel weights (allocated at create)
   const float* wsq = nullptr;     // == wbuf when a weight mask is set, else nullptr
+  // re-rank order (images grouped by their best candidate, so that images
+  // sharing candidate model images are re-ranked together and those rows are
+  // read from L2); nullptr: natural order
+  int* rr_key = nullptr;          // max_images
+  int* rr_start = nullptr;        // max_orient + 1 bucket starts / cursors
+  int* rr_order = nullptr;        // max_images
   int n_sms = 152;
 };
 
