@@ -105,7 +105,10 @@ void es_poly(int w, double beta, EsPoly* out) {
       t0 = t1;
       t1 = t2;
     }
-    for (int i = 0; i < n; ++i) out->c[d][i] = (float)m[i];
+    for (int i = 0; i < n; ++i) {
+      out->c[d][i] = (float)m[i];
+      out->c2[d][i] = make_float2((float)m[i], (float)m[i]);
+    }
   }
 }
 

@@ -183,6 +183,30 @@ __device__ __forceinline__ int es_weights(float u, const EsPoly& ep, float* wt) 
   return l0;
 }
 
+// The same for the three coordinates of a point: x and y share packed FP32
+// FMAs (one Horner chain on (t_x, t_y)), z runs alongside.
+template <int W>
+__device__ __forceinline__ int3 es_weights3(float3 u, const EsPoly& ep, float* wx, float* wy, float* wz) {
+  const int lx = (int)ceilf(u.x - 0.5f * W), ly = (int)ceilf(u.y - 0.5f * W), lz = (int)ceilf(u.z - 0.5f * W);
+  const float2 txy = make_float2(2.f * ((float)lx - u.x + 0.5f * W) - 1.f, 2.f * ((float)ly - u.y + 0.5f * W) - 1.f);
+  const float tz = 2.f * ((float)lz - u.z + 0.5f * W) - 1.f;
+  constexpr int P = es_degree(W);
+#pragma unroll
+  for (int d = 0; d < W; ++d) {
+    float2 v = ep.c2[d][P];
+    float vz = ep.c[d][P];
+#pragma unroll
+    for (int i = P - 1; i >= 0; --i) {
+      v = __ffma2_rn(v, txy, ep.c2[d][i]);
+      vz = fmaf(vz, tz, ep.c[d][i]);
+    }
+    wx[d] = v.x;
+    wy[d] = v.y;
+    wz[d] = vz;
+  }
+  return make_int3(lx, ly, lz);
+}
+
 // ------------------------------------------------------------ type 2 ------
 // cube[k mod nf] = A[k] p_kx p_ky p_kz for |k| <= Mh, zero elsewhere.
 __global__ void deconv_pad_kernel(const float* __restrict__ A, int N, const float* __restrict__ p,
@@ -644,11 +668,12 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
         oy = cy & (kBin - 1);
         oz = cz & (kBin - 1);
       }
+      float wx[W], wy[W], wz[W];
+      es_weights3<W>(u, ep, wx, wy, wz);
       {
         // A row t: the x weights at their window columns, hi | lo
-        float w[W], ax[16];
-        es_weights<W>(u.x, ep, w);
-        shift_weights<W, 16>(w, ox, ax);
+        float ax[16];
+        shift_weights<W, 16>(wx, ox, ax);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float4 hi, lo;
@@ -662,13 +687,11 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
       }
       {
         // y and z weights at their window rows, parked in shared memory
-        float w[W], e[S];
-        es_weights<W>(u.y, ep, w);
-        shift_weights<W, S>(w, oy, e);
+        float e[S];
+        shift_weights<W, S>(wy, oy, e);
 #pragma unroll
         for (int k = 0; k < S; ++k) Ey[k * 128 + t] = ok ? e[k] : 0.f;
-        es_weights<W>(u.z, ep, w);
-        shift_weights<W, S>(w, oz, e);
+        shift_weights<W, S>(wz, oz, e);
 #pragma unroll
         for (int k = 0; k < S; ++k) Ez[k * 128 + t] = ok ? e[k] : 0.f;
       }
@@ -837,9 +860,8 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
     const uint2 e = queue[lane];
     v = __uint_as_float(e.y);
     const float3 u = pts(e.x);
-    const int lx = es_weights<W>(u.x, ep, wx);
-    const int ly = es_weights<W>(u.y, ep, wy);
-    const int lz = es_weights<W>(u.z, ep, wz);
+    const int3 l0 = es_weights3<W>(u, ep, wx, wy, wz);
+    const int lx = l0.x, ly = l0.y, lz = l0.z;
     // tap-origin cell, wrapped; its position inside the bin is the local origin
     const int cx = wrap1(lx + C::H, nf), cy = wrap1(ly + C::H, nf), cz = wrap1(lz + C::H, nf);
     const int ox = cx & (kBin - 1), oy = cy & (kBin - 1), oz = cz & (kBin - 1);

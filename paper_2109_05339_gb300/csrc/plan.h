@@ -33,6 +33,7 @@ struct BinSort {
 // of degree es_degree(w) (see es_poly).
 struct EsPoly {
   float c[8][10];
+  float2 c2[8][10];   // each coefficient twice: two points or axes per packed FMA
 };
 __host__ __device__ constexpr int es_degree(int w) { return w < 7 ? w + 1 : w; }
 
