@@ -10,6 +10,12 @@ driver streams instead: each chunk's points are sorted (for slicing only,
 4 bytes per point), sliced and matched, then released, and the merge spreads
 the images at their matched orientations (image chunks accumulate).
 
+The driver numbers the reference orientations along a space-filling (Morton)
+curve of their quaternions, so that orientations close in index are close on
+SO(3): images re-ranked together then share candidate model images, which
+stay in L2. Indices returned to the caller are in the caller's numbering
+(an exact distance tie resolves to the lower index in the driver's numbering).
+
 1. Slicing (Sec. II-A) and matching (Sec. II-B), streamed in orientation
    chunks: each chunk of model images is sliced into one reusable buffer and
    matched against every image; the running top-k survives across chunks, so
@@ -22,9 +28,22 @@ the images at their matched orientations (image chunks accumulate).
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from .api import Matcher, Plan, PointSet
+
+
+def morton_order(quats_host):
+    """Permutation sorting unit quaternions (w, x, y, z; w >= 0) by the Morton
+    code of (x, y, z) quantised to 10 bits per axis."""
+    q = np.asarray(quats_host, dtype=np.float64)
+    c = np.clip(((q[:, 1:4] + 1.0) * 0.5 * 1023.0).round(), 0, 1023).astype(np.uint64)
+    key = np.zeros(q.shape[0], dtype=np.uint64)
+    for bit in range(10):
+        for a in range(3):
+            key |= ((c[:, a] >> np.uint64(bit)) & np.uint64(1)) << np.uint64(3 * bit + a)
+    return np.argsort(key, kind="stable")
 
 
 POINT_SET_BYTES = 16   # per (orientation, pixel): two sort orders, inverse order, class sum
@@ -65,9 +84,23 @@ class MTIP:
         self.N, self.P2, self.n_img, self.n_orient = N, P2, n_img, n_orient
         self.sets = None
         self._key = None
+        self._okey = None
+        self.order = None   # sorted index -> caller's orientation index (int64, device)
+        self.quats_sorted = None
+
+    def _order_orientations(self, quats):
+        """Renumber the orientation set along the Morton curve (once per set)."""
+        okey = (quats.data_ptr(), tuple(quats.shape))
+        if self._okey == okey:
+            return
+        order = morton_order(quats.detach().cpu().numpy())
+        self.order = torch.as_tensor(order, dtype=torch.int64, device=quats.device)
+        self.quats_sorted = quats.index_select(0, self.order).contiguous()
+        self._okey = okey
 
     def set_orientations(self, quats, q_lab):
         """Sort the points of every orientation chunk once (reused by later calls)."""
+        self._order_orientations(quats)
         key = (quats.data_ptr(), tuple(quats.shape), q_lab.data_ptr(), tuple(q_lab.shape))
         if self._key == key:
             return
@@ -75,13 +108,28 @@ class MTIP:
             for _, s in self.sets:
                 s.close()
         self.sets = []
-        M = quats.shape[0]
+        qs = self.quats_sorted
+        M = qs.shape[0]
         for c0 in range(0, M, self.orient_chunk):
             c1 = min(M, c0 + self.orient_chunk)
-            self.sets.append((c0, PointSet(self.plan, quats[c0:c1].contiguous(), q_lab)))
+            self.sets.append((c0, PointSet(self.plan, qs[c0:c1].contiguous(), q_lab)))
         self._key = key
 
-    def match(self, A, quats, q_lab, images, img_scale):
+    def _to_caller(self, res):
+        """Match results with orientation indices in the caller's numbering;
+        the sorted-numbering best index is kept under 'best_sorted'."""
+        out = dict(res)
+        out["best_sorted"] = res["best"]
+        out["best"] = self.order.index_select(0, res["best"].long()).to(torch.int32)
+        if "topk_idx" in res:
+            ti = res["topk_idx"].long()
+            out["topk_idx"] = self.order.index_select(0, ti.clamp(min=0).reshape(-1)).reshape(ti.shape) \
+                .to(torch.int32).masked_fill(ti < 0, -1)
+        return out
+
+    def match(self, A, quats, q_lab, images, img_scale, with_topk=False):
+        """Match every image against the orientation set; indices in the
+        caller's numbering ('best_sorted': the driver's own numbering)."""
         m = self.matcher
         m.set_images(images, img_scale)
         if self.cache_points:
@@ -90,37 +138,42 @@ class MTIP:
                 sl = self.slices[: ps.M]
                 ps.slice(A, out=sl)
                 m.add_slices(sl, orient_offset=c0)
-            return m.results()
-        M = quats.shape[0]
+            return self._to_caller(m.results(with_topk))
+        self._order_orientations(quats)
+        qs = self.quats_sorted
+        M = qs.shape[0]
         for c0 in range(0, M, self.orient_chunk):
             c1 = min(M, c0 + self.orient_chunk)
-            ps = PointSet(self.plan, quats[c0:c1].contiguous(), q_lab, slice_only=True)
+            ps = PointSet(self.plan, qs[c0:c1].contiguous(), q_lab, slice_only=True)
             sl = self.slices[: c1 - c0]
             ps.slice(A, out=sl)
             m.add_slices(sl, orient_offset=c0)
             ps.close()
-        return m.results()
+        return self._to_caller(m.results(with_topk))
 
-    def merge(self, images, quats, best, q_lab, img_scale, D=None):
+    def merge(self, images, quats, best_sorted, q_lab, img_scale, D=None):
+        """Merge at the matched orientations, given in the driver's numbering
+        (the 'best_sorted' of match)."""
         if self.cache_points:
             self.set_orientations(quats, q_lab)
             for k, (c0, ps) in enumerate(self.sets):
-                ps.merge(images, best, orient_offset=c0, D=D, b_scale=img_scale, rhs=self.rhs,
+                ps.merge(images, best_sorted, orient_offset=c0, D=D, b_scale=img_scale, rhs=self.rhs,
                          kernel_hat=self.khat, accumulate=k > 0)
             return self.rhs, self.khat
+        self._order_orientations(quats)
         n = images.shape[0]
         for i0 in range(0, n, self.img_chunk):
             i1 = min(n, i0 + self.img_chunk)
-            self.plan.merge_images(images[i0:i1], quats, q_lab, D=D, b_scale=img_scale, rhs=self.rhs,
-                                   kernel_hat=self.khat, accumulate=i0 > 0,
-                                   orient_idx=best[i0:i1].contiguous())
+            self.plan.merge_images(images[i0:i1], self.quats_sorted, q_lab, D=D, b_scale=img_scale,
+                                   rhs=self.rhs, kernel_hat=self.khat, accumulate=i0 > 0,
+                                   orient_idx=best_sorted[i0:i1].contiguous())
         return self.rhs, self.khat
 
     def iteration(self, A, quats, q_lab, images, img_scale, cg_iters, lam_rel=1e-3, D=None,
                   d_sum=None, res_hist=None):
         """Returns (match results, merged model x, lambda); d_sum = sum of D over one image."""
         res = self.match(A, quats, q_lab, images, img_scale)
-        self.merge(images, quats, res["best"], q_lab, img_scale, D)
+        self.merge(images, quats, res["best_sorted"], q_lab, img_scale, D)
         per_img = float(self.P2) if D is None else float(d_sum)
         lam = lam_rel * per_img * images.shape[0]
         x = self.plan.cg_solve(self.khat, lam, self.rhs, A, cg_iters, x=self.x, res_hist=res_hist)
