@@ -510,9 +510,9 @@ __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G
 // its row back and contracts it with its z and y weights.
 //
 // FP32 accuracy from TF32 inputs: every operand value v is split into
-// hi = tf32(v) and lo = tf32(v - hi), and T = A_hi B_hi + A_hi B_lo +
-// A_lo B_hi; the dropped A_lo B_lo term and the rounding of lo are
-// O(2^-22) relative. Both parts share a 128-byte swizzled row of the operand
+// hi = tf32(v) and lo = v - hi, and T = A_hi B_hi + A_hi B_lo + A_lo B_hi;
+// the dropped A_lo B_lo term and the tensor core's truncation of lo are
+// O(2^-21) relative. Both parts share a 128-byte swizzled row of the operand
 // tile: hi at K 0..15, lo at K 16..31.
 template <int W>
 struct InterpTcCfg {
@@ -523,13 +523,13 @@ struct InterpTcCfg {
   static constexpr int PTS = 128;                   // points per MMA (M)
   static constexpr uint32_t TILE = 128 * 128;       // one operand tile (bytes)
   static constexpr int TCOLS = 128;                 // tensor-memory columns
-  // CTAs per SM: 3 x 128 threads leave 170 registers a thread (no spills)
-  // and 3 x 128 of the 512 TMEM columns; operand tiles, barriers and the
-  // per-point y and z weights take 48 KB, which also caps residency at four
-  // CTAs, so the TMEM columns of every resident CTA always fit
-  static constexpr int CTAS = 3;
+  // CTAs per SM: 4 x 128 threads leave 128 registers a thread and take all
+  // 4 x 128 of the 512 TMEM columns; the operand tiles and barriers take
+  // 33 KB, and 48 KB are requested so that residency stays below five CTAs
+  // (their TMEM columns always fit)
+  static constexpr int CTAS = 4;
   static constexpr size_t SMEM = 48 * 1024;
-  static_assert(1024 + 2 * TILE + 64 + 2 * S * 128 * 4 <= SMEM, "shared memory layout");
+  static_assert(1024 + 2 * TILE + 64 <= SMEM, "shared memory layout");
   static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NN >> 3) << 17) |
                                     ((128u >> 4) << 24);
   static_assert(NN <= TCOLS && NN <= 128, "window rows exceed one tile");
@@ -542,10 +542,12 @@ __device__ __forceinline__ float tf32_round(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
 }
 
-// v = hi + lo with hi = tf32(v) and lo = tf32(v - hi) (v - hi is exact).
+// v = hi + lo with hi = tf32(v) and lo = v - hi (exact; |lo| <= 2^-11 |v|).
+// The tensor core reads lo at TF32 precision (truncation), an error of at
+// most 2^-21 |v|.
 __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
   hi = tf32_round(v);
-  lo = tf32_round(v - hi);
+  lo = v - hi;
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -587,8 +589,6 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   int* next = reinterpret_cast<int*>(tslot + 2);
-  float* Ey = reinterpret_cast<float*>(smem + 2 * C::TILE + 64);   // [S][128]
-  float* Ez = Ey + S * 128;
   const int t = threadIdx.x, warp = t >> 5;
   const int nf = g.nf;
 
@@ -685,16 +685,10 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
           *reinterpret_cast<float4*>(As + swz128(t, c + 4)) = lo;
         }
       }
-      {
-        // y and z weights at their window rows, parked in shared memory
-        float e[S];
-        shift_weights<W, S>(wy, oy, e);
-#pragma unroll
-        for (int k = 0; k < S; ++k) Ey[k * 128 + t] = ok ? e[k] : 0.f;
-        shift_weights<W, S>(wz, oz, e);
-#pragma unroll
-        for (int k = 0; k < S; ++k) Ez[k * 128 + t] = ok ? e[k] : 0.f;
-      }
+      // y and z weights at their window rows, kept in registers over the MMA
+      float ey_r[S], ez_r[S];
+      shift_weights<W, S>(wy, oy, ey_r);
+      shift_weights<W, S>(wz, oz, ez_r);
       fence_proxy_async_smem();
       tc_fence_before();
       __syncthreads();
@@ -726,7 +720,7 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
       if constexpr (S % 2 == 0) {
         float2 az[S], ey[S / 2];
 #pragma unroll
-        for (int k = 0; k < S / 2; ++k) ey[k] = make_float2(Ey[(2 * k) * 128 + t], Ey[(2 * k + 1) * 128 + t]);
+        for (int k = 0; k < S / 2; ++k) ey[k] = make_float2(ey_r[2 * k], ey_r[2 * k + 1]);
 #pragma unroll
         for (int z = 0; z < S; ++z) az[z] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -740,14 +734,12 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
           }
         }
 #pragma unroll
-        for (int z = 0; z < S; ++z) acc = fmaf(az[z].x + az[z].y, Ez[z * 128 + t], acc);
+        for (int z = 0; z < S; ++z) acc = fmaf(az[z].x + az[z].y, ez_r[z], acc);
       } else {
-        float az[S], ey[S];
+        float az[S];
+        const float* ey = ey_r;
 #pragma unroll
-        for (int z = 0; z < S; ++z) {
-          az[z] = 0.f;
-          ey[z] = Ey[z * 128 + t];
-        }
+        for (int z = 0; z < S; ++z) az[z] = 0.f;
 #pragma unroll
         for (int ch = 0; ch < C::NN / 16; ++ch) {
           float v[16];
@@ -759,7 +751,7 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
           }
         }
 #pragma unroll
-        for (int z = 0; z < S; ++z) acc = fmaf(az[z], Ez[z * 128 + t], acc);
+        for (int z = 0; z < S; ++z) acc = fmaf(az[z], ez_r[z], acc);
       }
       if (ok) out[id] = acc;
       id = id_next;
