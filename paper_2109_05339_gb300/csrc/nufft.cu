@@ -885,13 +885,8 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
     }
   }
   __syncwarp();
-  for (int k = 0; k < nrec; ++k) {
-    const float* rec = stage + k * C::REC;
-    const int key_k = __float_as_int(rec[0]);   // uniform: every lane reads record k
-    if (key_k != cur) {
-      if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
-      cur = key_k;
-    }
+  // add record `rec` to the accumulators (its window is the current one)
+  auto add = [&](const float* rec) {
     const float a = rec[12 + dx];
     const float2 wy = *reinterpret_cast<const float2*>(rec + 20 + 2 * r);
     const float c0 = a * wy.x, c1 = a * wy.y;
@@ -905,6 +900,24 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
       acc[q][0] = __ffma2_rn(zp[q], c00, acc[q][0]);
       acc[q][1] = __ffma2_rn(zp[q], c11, acc[q][1]);
     }
+  };
+  int k = 0;
+  while (k < nrec) {
+    const float* rec = stage + k * C::REC;
+    const int key_k = __float_as_int(rec[0]);   // uniform: every lane reads record k
+    // two records in the current window: no write-back check between them
+    if (key_k == cur && k + 1 < nrec && __float_as_int(rec[C::REC]) == cur) {
+      add(rec);
+      add(rec + C::REC);
+      k += 2;
+      continue;
+    }
+    if (key_k != cur) {
+      if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
+      cur = key_k;
+    }
+    add(rec);
+    ++k;
   }
   __syncwarp();
 }
