@@ -282,9 +282,14 @@ int spf_match_orientations_static(const float* images, int n_img, float img_scal
  * spf_profile_read: for kernel number `index` (0 ..), its name (copied into
  *   name[0..name_len-1]), launches and summed device milliseconds since the
  *   last enable. Waits for the recorded events. SPF_ERR_ARG past the last.
+ * spf_profile_select: restrict the event pairs to the kernels named in the
+ *   comma-separated list `names` (NULL or "" selects every kernel); the
+ *   other launches are still counted by spf_launch_count. Lets a caller time
+ *   one kernel inside a timed region without an event pair on every launch.
  * spf_launch_count: kernels launched by this library since the process began.
  * ------------------------------------------------------------------------- */
 int spf_profile_enable(int on);
+int spf_profile_select(const char* names);
 int spf_profile_read(int index, char* name, int name_len, long long* launches, double* total_ms);
 long long spf_launch_count(void);
 

@@ -67,6 +67,7 @@ PROTOTYPES = {
     "spf_match_orientations": (I, [P, P, I, F, P, I, P, P, P, P]),
     "spf_match_orientations_static": (I, [P, I, F, P, I, I, P, P, P, P]),
     "spf_profile_enable": (I, [I]),
+    "spf_profile_select": (I, [C.c_char_p]),
     "spf_profile_read": (I, [I, C.c_char_p, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
     "spf_launch_count": (C.c_longlong, []),
 }
@@ -97,6 +98,11 @@ def check(code):
 
 def profile_enable(on=True):
     lib.spf_profile_enable(1 if on else 0)
+
+
+def profile_select(names=None):
+    """Trace only the named kernels (None: all)."""
+    lib.spf_profile_select(",".join(names).encode() if names else None)
 
 
 def profile_read():

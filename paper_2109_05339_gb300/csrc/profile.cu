@@ -34,6 +34,7 @@ struct Prof {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
   size_t pool_used = 0;
   long long dropped = 0;
+  std::vector<std::string> selected;   // empty: every kernel
 };
 
 Prof& prof() {
@@ -69,6 +70,11 @@ int prof_begin(const char* name, cudaStream_t s) {
   Prof& P = prof();
   std::lock_guard<std::mutex> g(P.mu);
   if (!P.on) return -1;
+  if (!P.selected.empty()) {
+    bool hit = false;
+    for (const auto& n : P.selected) hit = hit || n == name;
+    if (!hit) return -1;
+  }
   if (P.pool_used == P.pool.size()) {
     if (P.pool.size() >= 8192) {
       ++P.dropped;
@@ -112,6 +118,24 @@ int spf_profile_enable(int on) {
     P.dropped = 0;
   }
   P.on = on != 0;
+  return SPF_OK;
+}
+
+int spf_profile_select(const char* names) {
+  Prof& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  P.selected.clear();
+  if (!names) return SPF_OK;
+  std::string cur;
+  for (const char* c = names;; ++c) {
+    if (*c == ',' || *c == 0) {
+      if (!cur.empty()) P.selected.push_back(cur);
+      cur.clear();
+      if (*c == 0) break;
+    } else if (*c != ' ') {
+      cur.push_back(*c);
+    }
+  }
   return SPF_OK;
 }
 
