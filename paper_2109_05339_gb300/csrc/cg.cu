@@ -40,17 +40,16 @@ __device__ double block_sum(double v) {
 }
 
 // cube (PT^3 complex) = x at n mod PT (|n| <= Mh), zero elsewhere.
+// x (N^3) into the circulant-embedding cube at n mod PT. Only those N^3
+// entries are written: the pruned forward FFT reads nothing else.
 __global__ void pad_kernel(const float* __restrict__ x, int N, int PT, float2* __restrict__ cube) {
-  int64_t total = (int64_t)PT * PT * PT;
+  int64_t total = (int64_t)N * N * N;
   int Mh = (N - 1) / 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int a = (int)(i % PT), b = (int)((i / PT) % PT), c = (int)(i / ((int64_t)PT * PT));
-    int kx = a <= Mh ? a : a - PT, ky = b <= Mh ? b : b - PT, kz = c <= Mh ? c : c - PT;
-    float v = 0.f;
-    if (kx >= -Mh && kx <= Mh && ky >= -Mh && ky <= Mh && kz >= -Mh && kz <= Mh)
-      v = x[((kz + Mh) * N + (ky + Mh)) * N + (kx + Mh)];
-    cube[i] = make_float2(v, 0.f);
+    int a = (int)(i % N), b = (int)((i / N) % N), c = (int)(i / ((int64_t)N * N));
+    int gx = wrapi(a - Mh, PT), gy = wrapi(b - Mh, PT), gz = wrapi(c - Mh, PT);
+    cube[((size_t)gz * PT + gy) * PT + gx] = make_float2(x[i], 0.f);
   }
 }
 
@@ -213,7 +212,7 @@ int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x
                    double* part, cudaStream_t s) {
   const int N = P->N, PT = P->PT;
   int64_t PT3 = (int64_t)PT * PT * PT;
-  SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for(PT3), 256, 0, s>>>(x, N, PT, P->cubeP); }));
+  SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for((int64_t)N * N * N), 256, 0, s>>>(x, N, PT, P->cubeP); }));
   SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, nullptr, khat, -1, P->Mh + 1, 0, s));
   SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, nullptr, nullptr, +1, 0, P->Mh + 1, s));
   SPF_TRY(launch("crop_apply_kernel", s, [&] { crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3),

@@ -171,6 +171,7 @@ struct PassArgs {
   int64_t es;            // element stride along the line
   int64_t sa, sb;        // strides of the line coordinates a and b
   LineSet ls;
+  int in_lo[2], in_hi[2];  // positions along the line that are read; the rest count as zero
   int lines_per_cta;     // contiguous: lines per CTA; strided: b-lines per CTA
   int nrad;
   int radix[16];
@@ -179,6 +180,11 @@ struct PassArgs {
 };
 
 __device__ __forceinline__ int range_count(int lo, int hi) { return hi > lo ? hi - lo : 0; }
+
+// Position i of a line is read (else it counts as zero: pruned input).
+__device__ __forceinline__ bool in_read_range(const PassArgs& A, int i) {
+  return (i >= A.in_lo[0] && i < A.in_hi[0]) || (i >= A.in_lo[1] && i < A.in_hi[1]);
+}
 
 // Map the i-th selected coordinate to its value, over two ranges.
 __device__ __forceinline__ int pick(int i, const int* lo, const int* hi) {
@@ -216,7 +222,8 @@ __global__ void __launch_bounds__(kThreads) fft_strided_kernel(PassArgs A) {
     int l = e % nlines, i = e / nlines;
     int b = pick(first + l, A.ls.b_lo, A.ls.b_hi);
     int64_t g = base_a + (int64_t)b * A.sb + (int64_t)i * A.es;
-    sbuf[l * n + i] = A.in_real ? make_float2(A.in_real[g], 0.f) : A.data[g];
+    sbuf[l * n + i] = !in_read_range(A, i) ? make_float2(0.f, 0.f)
+                      : A.in_real ? make_float2(A.in_real[g], 0.f) : A.data[g];
   }
   __syncthreads();
   run_passes(A, sbuf, nlines);
@@ -250,7 +257,8 @@ __global__ void __launch_bounds__(kThreads) fft_contig_kernel(PassArgs A) {
     int a = pick(li / nbs, A.ls.a_lo, A.ls.a_hi);
     int b = pick(li % nbs, A.ls.b_lo, A.ls.b_hi);
     int64_t g = (int64_t)a * A.sa + (int64_t)b * A.sb + i;
-    sbuf[e] = A.in_real ? make_float2(A.in_real[g], 0.f) : A.data[g];
+    sbuf[e] = !in_read_range(A, i) ? make_float2(0.f, 0.f)
+              : A.in_real ? make_float2(A.in_real[g], 0.f) : A.data[g];
   }
   __syncthreads();
   run_passes(A, sbuf, nlines);
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) fft_contig_ct(PassArgs A) {
   __syncthreads();
   for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
     const int l = e / N, i = e - l * N;
-    sbuf[e] = load_elem(A, lbase[l] + i);
+    sbuf[e] = in_read_range(A, i) ? load_elem(A, lbase[l] + i) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   passes_ct<N, L, 1>(sbuf, nlines, A.tw, A.sign, typename RadixPlan<N>::type{});
@@ -402,7 +410,8 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
   __syncthreads();
   for (int e = threadIdx.x; e < T * N; e += kThreads) {
     const int l = e % T, i = e / T;
-    if (l < nlines) sbuf[l * N + i] = load_elem(A, lbase[l] + (int64_t)i * A.es);
+    if (l < nlines)
+      sbuf[l * N + i] = in_read_range(A, i) ? load_elem(A, lbase[l] + (int64_t)i * A.es) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   passes_ct<N, T, 1>(sbuf, nlines, A.tw, A.sign, typename RadixPlan<N>::type{});
@@ -516,9 +525,12 @@ void fft3_destroy(FFT3* p) {
 }
 
 // Generic pass launcher over axis `axis` (0 = x, 1 = y, 2 = z).
+// One axis pass over the lines (a, b) in the given ranges; positions along
+// the line outside [in_lo, in_hi) (two ranges; nullptr: all) read as zero.
 static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real, float* out_real,
                      const float* post_mul, int sign, const int* a_lo, const int* a_hi,
-                     const int* b_lo, const int* b_hi, cudaStream_t s) {
+                     const int* b_lo, const int* b_hi, cudaStream_t s, const int* in_lo = nullptr,
+                     const int* in_hi = nullptr) {
   PassArgs A;
   A.data = data;
   A.in_real = in_real;
@@ -534,6 +546,8 @@ static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real
   for (int i = 0; i < 2; ++i) {
     A.ls.a_lo[i] = a_lo[i]; A.ls.a_hi[i] = a_hi[i];
     A.ls.b_lo[i] = b_lo[i]; A.ls.b_hi[i] = b_hi[i];
+    A.in_lo[i] = in_lo ? in_lo[i] : 0;
+    A.in_hi[i] = in_hi ? in_hi[i] : (i == 0 ? ax.n : 0);
   }
   if (axis == 0) {          // lines (z, y): a = z, b = y
     A.es = 1; A.sa = n1 * n0; A.sb = n0;
@@ -561,11 +575,18 @@ int fft3_exec_ex(const FFT3* p, float2* data, const float* in_real, float* out_r
   full_range(p->n2, fz_lo, fz_hi);
   int rx_lo[2], rx_hi[2], ry_lo[2], ry_hi[2];
   if (zero_hw_in > 0) {
+    // Only the wrapped index range of half width zero_hw_in along each axis
+    // holds data: each pass reads its line only there (so the caller need
+    // not zero the rest of the cube) and only the lines whose other
+    // coordinates lie in the ranges already transformed.
+    int rz_lo[2], rz_hi[2];
     wrapped_range(p->n0, zero_hw_in, rx_lo, rx_hi);
     wrapped_range(p->n1, zero_hw_in, ry_lo, ry_hi);
-    SPF_TRY(axis_pass(p, 2, data, nullptr, nullptr, nullptr, sign, ry_lo, ry_hi, rx_lo, rx_hi, s));
-    SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, sign, fz_lo, fz_hi, rx_lo, rx_hi, s));
-    SPF_TRY(axis_pass(p, 0, data, nullptr, out_real, post_mul, sign, fz_lo, fz_hi, fy_lo, fy_hi, s));
+    wrapped_range(p->n2, zero_hw_in, rz_lo, rz_hi);
+    SPF_TRY(axis_pass(p, 2, data, nullptr, nullptr, nullptr, sign, ry_lo, ry_hi, rx_lo, rx_hi, s, rz_lo, rz_hi));
+    SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, sign, fz_lo, fz_hi, rx_lo, rx_hi, s, ry_lo, ry_hi));
+    SPF_TRY(axis_pass(p, 0, data, nullptr, out_real, post_mul, sign, fz_lo, fz_hi, fy_lo, fy_hi, s, rx_lo,
+                      rx_hi));
     return SPF_OK;
   }
   wrapped_range(p->n0, need_hw_out, rx_lo, rx_hi);

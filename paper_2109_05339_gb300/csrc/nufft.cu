@@ -209,20 +209,21 @@ __device__ __forceinline__ int3 es_weights3(float3 u, const EsPoly& ep, float* w
 
 // ------------------------------------------------------------ type 2 ------
 // cube[k mod nf] = A[k] p_kx p_ky p_kz for |k| <= Mh, zero elsewhere.
+// Only the N^3 mode entries are written: the pruned forward FFT reads
+// nothing else of the cube.
 __global__ void deconv_pad_kernel(const float* __restrict__ A, int N, const float* __restrict__ p,
                                   int nf, float2* __restrict__ cube) {
-  int64_t total = (int64_t)nf * nf * nf;
+  int64_t total = (int64_t)N * N * N;
   int Mh = (N - 1) / 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int x = (int)(i % nf), y = (int)((i / nf) % nf), z = (int)(i / ((int64_t)nf * nf));
-    int kx = x <= Mh ? x : x - nf, ky = y <= Mh ? y : y - nf, kz = z <= Mh ? z : z - nf;
-    float v = 0.f;
-    if (kx >= -Mh && kx <= Mh && ky >= -Mh && ky <= Mh && kz >= -Mh && kz <= Mh) {
-      int a = ((kz + Mh) * N + (ky + Mh)) * N + (kx + Mh);
-      v = A[a] * p[kx + Mh] * p[ky + Mh] * p[kz + Mh];
-    }
-    cube[i] = make_float2(v, 0.f);
+    int a = (int)(i % N), b = (int)((i / N) % N), c = (int)(i / ((int64_t)N * N));
+    const float v = A[i] * p[a] * p[b] * p[c];
+    int gx = a - Mh, gy = b - Mh, gz = c - Mh;
+    gx += gx < 0 ? nf : 0;
+    gy += gy < 0 ? nf : 0;
+    gz += gz < 0 ? nf : 0;
+    cube[((size_t)gz * nf + gy) * nf + gx] = make_float2(v, 0.f);
   }
 }
 
@@ -1175,9 +1176,9 @@ int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cud
 // Fine-grid real part G of the deconvolved, padded model (type-2 set-up).
 int type2_setup(spf_plan* P, const float* A, cudaStream_t s, bool halo) {
   Grid& g = P->g;
-  int64_t n3 = (int64_t)g.nf * g.nf * g.nf;
+  const int64_t nm3 = (int64_t)P->N * P->N * P->N;
   SPF_TRY(launch("deconv_pad_kernel", s,
-                 [&] { deconv_pad_kernel<<<grid_for(n3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); }));
+                 [&] { deconv_pad_kernel<<<grid_for(nm3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); }));
   SPF_TRY(fft3_exec_ex(&g.fft, g.cube, nullptr, g.real, nullptr, -1, P->Mh + 1, 0, s));
   if (!halo) return SPF_OK;
   const int np = g.nf + P->w, npx = halo_npx(g.nf, P->w);
@@ -1253,7 +1254,7 @@ static int kernel_finish(spf_plan* P, float* kernel_hat, int accumulate, cudaStr
   int h = (g.n_modes + 1) / 2;
   SPF_TRY(fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s));
   int64_t PT3 = (int64_t)P->PT * P->PT * P->PT;
-  SPF_CUDA(cudaMemsetAsync(P->cubeP, 0, sizeof(float2) * PT3, s));
+  // the embedding fills the (2N-1)^3 wrapped range the pruned FFT reads
   int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
   SPF_TRY(launch("crop_embed_kernel", s, [&] {
     crop_embed_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, P->PT, P->cubeP);
