@@ -326,7 +326,7 @@ __device__ __forceinline__ void pass_ct(float2* buf, int nlines, const float2* _
       if (Ns > 1 && k != 0) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(&tw[k * r * TSTEP]);
+          float2 w = tw[k * r * TSTEP];   // shared-memory table
           w.y *= -sign;
           v[q][r] = cmul(v[q][r], w);
         }
@@ -352,8 +352,27 @@ __host__ __device__ constexpr int ct_lines() { return kMaxElems / N; }
 template <int N>
 __host__ __device__ constexpr int ct_tile() { return (kMaxElems / N) < 16 ? (kMaxElems / N) : 16; }
 
-__device__ __forceinline__ float2 load_elem(const PassArgs& A, int64_t g) {
-  return A.in_real ? make_float2(__ldg(A.in_real + g), 0.f) : A.data[g];
+// Element (position i, global offset g) of a line into shared memory: complex
+// input by an asynchronous copy (no register round trip, every copy of the
+// thread in flight at once), real input through registers, zero outside the
+// read range. cp_async_wait() before the CTA synchronises.
+__device__ __forceinline__ void stage_elem(const PassArgs& A, float2* dst, int i, int64_t g) {
+  if (!in_read_range(A, i)) {
+    *dst = make_float2(0.f, 0.f);
+  } else if (A.in_real) {
+    *dst = make_float2(__ldg(A.in_real + g), 0.f);
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(A.data + g)
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Twiddle table of one axis into shared memory (n entries).
+__device__ __forceinline__ void stage_twiddles(float2* stw, const float2* __restrict__ tw, int n) {
+  for (int k = threadIdx.x; k < n; k += kThreads) stw[k] = __ldg(tw + k);
 }
 
 __device__ __forceinline__ void store_elem(const PassArgs& A, int64_t g, float2 v) {
@@ -382,12 +401,15 @@ __global__ void __launch_bounds__(kThreads) fft_contig_ct(PassArgs A) {
     lbase[threadIdx.x] = (int64_t)a * A.sa + (int64_t)b * A.sb;
   }
   __syncthreads();
+  float2* stw = sbuf + L * N;
+  stage_twiddles(stw, A.tw, N);
   for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
     const int l = e / N, i = e - l * N;
-    sbuf[e] = in_read_range(A, i) ? load_elem(A, lbase[l] + i) : make_float2(0.f, 0.f);
+    stage_elem(A, sbuf + e, i, lbase[l] + i);
   }
+  cp_async_wait();
   __syncthreads();
-  passes_ct<N, L, 1>(sbuf, nlines, A.tw, A.sign, typename RadixPlan<N>::type{});
+  passes_ct<N, L, 1>(sbuf, nlines, stw, A.sign, typename RadixPlan<N>::type{});
   for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
     const int l = e / N, i = e - l * N;
     store_elem(A, lbase[l] + i, sbuf[e]);
@@ -408,13 +430,15 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
   if (threadIdx.x < nlines)
     lbase[threadIdx.x] = (int64_t)a * A.sa + (int64_t)pick(first + threadIdx.x, A.ls.b_lo, A.ls.b_hi) * A.sb;
   __syncthreads();
+  float2* stw = sbuf + T * N;
+  stage_twiddles(stw, A.tw, N);
   for (int e = threadIdx.x; e < T * N; e += kThreads) {
     const int l = e % T, i = e / T;
-    if (l < nlines)
-      sbuf[l * N + i] = in_read_range(A, i) ? load_elem(A, lbase[l] + (int64_t)i * A.es) : make_float2(0.f, 0.f);
+    if (l < nlines) stage_elem(A, sbuf + l * N + i, i, lbase[l] + (int64_t)i * A.es);
   }
+  cp_async_wait();
   __syncthreads();
-  passes_ct<N, T, 1>(sbuf, nlines, A.tw, A.sign, typename RadixPlan<N>::type{});
+  passes_ct<N, T, 1>(sbuf, nlines, stw, A.sign, typename RadixPlan<N>::type{});
   for (int e = threadIdx.x; e < T * N; e += kThreads) {
     const int l = e % T, i = e / T;
     if (l < nlines) store_elem(A, lbase[l] + (int64_t)i * A.es, sbuf[l * N + i]);
@@ -426,12 +450,12 @@ int launch_ct(PassArgs& A, bool contiguous, int na, int nb, cudaStream_t s) {
   if (contiguous) {
     constexpr int L = ct_lines<N>();
     const int grid = (int)ceil_div((int64_t)na * nb, L);
-    const size_t smem = (size_t)L * N * sizeof(float2);
+    const size_t smem = (size_t)(L + 1) * N * sizeof(float2);   // lines and the twiddle table
     return launch("fft_contig_kernel", s, [&] { fft_contig_ct<N><<<grid, kThreads, smem, s>>>(A); });
   }
   constexpr int T = ct_tile<N>();
   const int64_t grid = ceil_div(nb, T) * (int64_t)na;
-  const size_t smem = (size_t)T * N * sizeof(float2);
+  const size_t smem = (size_t)(T + 1) * N * sizeof(float2);   // lines and the twiddle table
   return launch("fft_strided_kernel", s,
                 [&] { fft_strided_ct<N><<<(unsigned)grid, kThreads, smem, s>>>(A); });
 }
