@@ -376,6 +376,7 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
   for (int q = 0; q < K; ++q) acc[q] = 0.f;
   bool vec = !wsq && (P2 % 4) == 0 && (((uintptr_t)x) & 15) == 0 && (((uintptr_t)Y) & 15) == 0;
   if (vec) {
+#pragma unroll 2
     for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
       float4 xv = __ldg(reinterpret_cast<const float4*>(x) + p);
       xv.x *= xscale; xv.y *= xscale; xv.z *= xscale; xv.w *= xscale;

@@ -408,11 +408,20 @@ __global__ void class_sum_kernel(const float* __restrict__ img, const int* __res
   if (j < 0 || j >= M) return;
   const float* row = img + (size_t)i * P2;
   const uint32_t* pos = inv + (size_t)j * P2;
-  for (int p = c * 1024 + threadIdx.x; p < min(P2, (c + 1) * 1024); p += blockDim.x) {
-    float v = b_scale * __ldg(row + p);
-    if (D) v *= __ldg(D + p);
-    if (v != 0.f) atomicAdd(cls + __ldg(pos + p), v);
+  // 4 pixels per thread (blockDim 256): loads first, then the scatter
+  const int p_end = min(P2, (c + 1) * 1024);
+  float v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int p = c * 1024 + threadIdx.x + 256 * k;
+    v[k] = p < p_end ? b_scale * __ldg(row + p) * (D ? __ldg(D + p) : 1.f) : 0.f;
   }
+  uint32_t at[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) at[k] = v[k] != 0.f ? __ldg(pos + c * 1024 + threadIdx.x + 256 * k) : 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (v[k] != 0.f) atomicAdd(cls + at[k], v[k]);
   if (c == 0 && threadIdx.x == 0) atomicAdd(cnt + j, 1.f);
 }
 
@@ -627,24 +636,37 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
     const int4 sub = subs[sidx];
     const int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
     const int ox0 = bx * kBin - C::H, oy0 = by * kBin - C::H, oz0 = bz * kBin - C::H;
-    // window -> B (hi | lo), 4 columns per task
-    for (int task = t; task < S * S * 4; task += 128) {
-      const int n = task >> 2, c = task & 3;
-      const int z = n / S, y = n - z * S;
-      const float* row = G + ((size_t)wrap1(oz0 + z, nf) * nf + wrap1(oy0 + y, nf)) * nf;
-      float v[4];
+    // window -> B (hi | lo), 4 columns per task; every load of the thread is
+    // issued before the first is used
+    {
+      constexpr int TASKS = S * S * 4, ITER = (TASKS + 127) / 128;
+      float v[ITER][4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int x = 4 * c + e;
-        v[e] = x < S ? __ldg(row + wrap1(ox0 + x, nf)) : 0.f;
+      for (int k = 0; k < ITER; ++k) {
+        const int task = t + 128 * k;
+        const int n = task >> 2, c = task & 3;
+        const int z = n / S, y = n - z * S;
+        const float* row = G + ((size_t)wrap1(oz0 + z, nf) * nf + wrap1(oy0 + y, nf)) * nf;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int x = 4 * c + e;
+          v[k][e] = task < TASKS && x < S ? __ldg(row + wrap1(ox0 + x, nf)) : 0.f;
+        }
       }
-      float4 hi, lo;
-      split_tf32(v[0], hi.x, lo.x);
-      split_tf32(v[1], hi.y, lo.y);
-      split_tf32(v[2], hi.z, lo.z);
-      split_tf32(v[3], hi.w, lo.w);
-      *reinterpret_cast<float4*>(Bs + swz128(n, c)) = hi;
-      *reinterpret_cast<float4*>(Bs + swz128(n, c + 4)) = lo;
+#pragma unroll
+      for (int k = 0; k < ITER; ++k) {
+        const int task = t + 128 * k;
+        if (task < TASKS) {
+          const int n = task >> 2, c = task & 3;
+          float4 hi, lo;
+          split_tf32(v[k][0], hi.x, lo.x);
+          split_tf32(v[k][1], hi.y, lo.y);
+          split_tf32(v[k][2], hi.z, lo.z);
+          split_tf32(v[k][3], hi.w, lo.w);
+          *reinterpret_cast<float4*>(Bs + swz128(n, c)) = hi;
+          *reinterpret_cast<float4*>(Bs + swz128(n, c + 4)) = lo;
+        }
+      }
     }
     bool aborted = false;
     // loads run one block ahead: the next block's id is fetched while this
