@@ -122,14 +122,17 @@ struct ExplicitPts {
 // ---------------------------------------------------------- strengths -----
 // Strength of the point with id `id` at position `pos` of the sorted order.
 struct StrPtr {        // v[id]
+  static constexpr bool kByPos = false;
   const float* v;
   __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const { return __ldg(v + id); }
 };
 struct StrSorted {     // v[pos]: strengths stored in the sorted order (coalesced)
+  static constexpr bool kByPos = true;
   const float* v;
   __device__ __forceinline__ float operator()(uint32_t, uint32_t pos) const { return __ldg(v + pos); }
 };
 struct StrImage {      // D[p] * scale * image[id]
+  static constexpr bool kByPos = false;
   const float* img;
   const float* D;
   FastDiv P2;
@@ -140,6 +143,7 @@ struct StrImage {      // D[p] * scale * image[id]
   }
 };
 struct StrWeights {    // D[p] (ones if D is NULL)
+  static constexpr bool kByPos = false;
   const float* D;
   FastDiv P2;
   __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const {
@@ -148,6 +152,7 @@ struct StrWeights {    // D[p] (ones if D is NULL)
 };
 
 struct StrCount {     // D[p] * count[j] for point id = j * P2 + p
+  static constexpr bool kByPos = false;
   const float* cnt;
   const float* D;
   FastDiv P2;
@@ -974,36 +979,54 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
     for (int q = 0; q < C::WZ2; ++q) acc[q][0] = acc[q][1] = make_float2(0.f, 0.f);
     // Points with nonzero strength are queued (in order) and staged 32 at a
     // time, so the weights are computed for contributing points only. The
-    // global loads run ahead: ids two chunks, strengths one chunk.
+    // points are read 128 at a time (lane + 32 e, e < 4: coalesced), the
+    // next 128's ids (and sorted-order strengths) while these are queued.
     const uint32_t* ids = sorted + sub.y;
     const uint32_t pos0 = (uint32_t)sub.y;
-    uint32_t idA = 0, idB = 0;
-    float vA = 0.f;
-    if (lane < sub.z) {
-      idA = __ldg(ids + lane);
-      vA = str(idA, pos0 + lane);
-    }
-    if (32 + lane < sub.z) idB = __ldg(ids + 32 + lane);
+    uint32_t idn[4];
+    float vn[4];
+    auto fetch = [&](int b) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = b + lane + 32 * e;
+        idn[e] = i < sub.z ? __ldg(ids + i) : 0u;
+        if constexpr (Str::kByPos) vn[e] = i < sub.z ? str(0u, pos0 + i) : 0.f;
+      }
+    };
+    fetch(0);
     int q = 0;   // queued points
-    for (int base = 0; base < sub.z; base += 32) {
-      const uint32_t id = idA;
-      const float v = vA;
-      vA = base + 32 + lane < sub.z ? str(idB, pos0 + base + 32 + lane) : 0.f;
-      idA = idB;
-      if (base + 64 + lane < sub.z) idB = __ldg(ids + base + 64 + lane);
-      const bool nz = base + lane < sub.z && v != 0.f;
-      const unsigned m = __ballot_sync(0xffffffffu, nz);
-      if (nz) queue[q + __popc(m & ((1u << lane) - 1u))] = make_uint2(id, __float_as_uint(v));
-      q += __popc(m);
-      __syncwarp();
-      if (q >= 32) {
-        spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, 32, stage, grid, lane, r, dx, cur, acc, err);
-        uint2 tail = make_uint2(0u, 0u);
-        if (lane < q - 32) tail = queue[32 + lane];
+    for (int base = 0; base < sub.z; base += 128) {
+      uint32_t idc[4];
+      float vc[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        idc[e] = idn[e];
+        if constexpr (Str::kByPos) vc[e] = vn[e];
+      }
+      if (base + 128 < sub.z) fetch(base + 128);
+      if constexpr (!Str::kByPos) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) vc[e] = base + lane + 32 * e < sub.z ? str(idc[e], 0u) : 0.f;
+      }
+      // one copy of the batch code (not unrolled: it is large)
+#pragma unroll 1
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t id_e = e == 0 ? idc[0] : e == 1 ? idc[1] : e == 2 ? idc[2] : idc[3];
+        const float v_e = e == 0 ? vc[0] : e == 1 ? vc[1] : e == 2 ? vc[2] : vc[3];
+        const bool nz = base + lane + 32 * e < sub.z && v_e != 0.f;
+        const unsigned m = __ballot_sync(0xffffffffu, nz);
+        if (nz) queue[q + __popc(m & ((1u << lane) - 1u))] = make_uint2(id_e, __float_as_uint(v_e));
+        q += __popc(m);
         __syncwarp();
-        if (lane < q - 32) queue[lane] = tail;
-        q -= 32;
-        __syncwarp();
+        if (q >= 32) {
+          spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, 32, stage, grid, lane, r, dx, cur, acc, err);
+          uint2 tail = make_uint2(0u, 0u);
+          if (lane < q - 32) tail = queue[32 + lane];
+          __syncwarp();
+          if (lane < q - 32) queue[lane] = tail;
+          q -= 32;
+          __syncwarp();
+        }
       }
     }
     if (q > 0) spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, q, stage, grid, lane, r, dx, cur, acc, err);
