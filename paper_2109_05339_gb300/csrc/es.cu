@@ -79,7 +79,11 @@ void es_poly(int w, double beta, EsPoly* out) {
   *out = EsPoly();
   const int P = es_degree(w), n = P + 1;
   if (w < 1 || w > 8) return;
-  for (int d = 0; d < w; ++d) {
+  // taps d < (w+1)/2 are interpolated; tap w-1-d is tap d at -t (the
+  // kernel is even and the taps are placed symmetrically), so its
+  // coefficients are c[d][i] (-1)^i exactly
+  const int half = (w + 1) / 2;
+  for (int d = 0; d < half; ++d) {
     std::vector<double> f(n), a(n, 0.0);
     for (int k = 0; k < n; ++k) {
       const double t = std::cos(M_PI * (k + 0.5) / n), x = 0.5 * (t + 1.0);
@@ -105,9 +109,19 @@ void es_poly(int w, double beta, EsPoly* out) {
       t0 = t1;
       t1 = t2;
     }
+    if (2 * d + 1 == w) {   // the middle tap is even in t
+      for (int i = 1; i < n; i += 2) m[i] = 0.0;
+    }
     for (int i = 0; i < n; ++i) {
-      out->c[d][i] = (float)m[i];
-      out->c2[d][i] = make_float2((float)m[i], (float)m[i]);
+      const float c = (float)m[i], cm = (i & 1) ? -c : c;
+      out->c[d][i] = c;
+      out->c2[d][i] = make_float2(c, c);
+      out->c[w - 1 - d][i] = cm;
+      out->c2[w - 1 - d][i] = make_float2(cm, cm);
+      if (i / 2 < 5) {
+        if (i & 1) out->o2[d][i / 2] = make_float2(c, c);
+        else out->e2[d][i / 2] = make_float2(c, c);
+      }
     }
   }
 }

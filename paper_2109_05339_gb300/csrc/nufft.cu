@@ -195,19 +195,40 @@ __device__ __forceinline__ int3 es_weights3(float3 u, const EsPoly& ep, float* w
   const int lx = (int)ceilf(u.x - 0.5f * W), ly = (int)ceilf(u.y - 0.5f * W), lz = (int)ceilf(u.z - 0.5f * W);
   const float2 txy = make_float2(2.f * ((float)lx - u.x + 0.5f * W) - 1.f, 2.f * ((float)ly - u.y + 0.5f * W) - 1.f);
   const float tz = 2.f * ((float)lz - u.z + 0.5f * W) - 1.f;
+  // mirror form: taps d and W-1-d from the even and odd halves in s = t^2
   constexpr int P = es_degree(W);
+  constexpr int NE = P / 2 + 1, NO = (P + 1) / 2;   // even / odd coefficient counts
+  const float2 sxy = __fmul2_rn(txy, txy);
+  const float sz = tz * tz;
 #pragma unroll
-  for (int d = 0; d < W; ++d) {
-    float2 v = ep.c2[d][P];
-    float vz = ep.c[d][P];
+  for (int d = 0; d < (W + 1) / 2; ++d) {
+    float2 e = ep.e2[d][NE - 1];
+    float ez = ep.e2[d][NE - 1].x;
 #pragma unroll
-    for (int i = P - 1; i >= 0; --i) {
-      v = __ffma2_rn(v, txy, ep.c2[d][i]);
-      vz = fmaf(vz, tz, ep.c[d][i]);
+    for (int k = NE - 2; k >= 0; --k) {
+      e = __ffma2_rn(e, sxy, ep.e2[d][k]);
+      ez = fmaf(ez, sz, ep.e2[d][k].x);
     }
-    wx[d] = v.x;
-    wy[d] = v.y;
-    wz[d] = vz;
+    if (2 * d + 1 == W) {   // middle tap: even
+      wx[d] = e.x;
+      wy[d] = e.y;
+      wz[d] = ez;
+    } else {
+      float2 o = ep.o2[d][NO - 1];
+      float oz = ep.o2[d][NO - 1].x;
+#pragma unroll
+      for (int k = NO - 2; k >= 0; --k) {
+        o = __ffma2_rn(o, sxy, ep.o2[d][k]);
+        oz = fmaf(oz, sz, ep.o2[d][k].x);
+      }
+      const float2 to = __fmul2_rn(txy, o);
+      wx[d] = e.x + to.x;
+      wy[d] = e.y + to.y;
+      wz[d] = fmaf(tz, oz, ez);
+      wx[W - 1 - d] = e.x - to.x;
+      wy[W - 1 - d] = e.y - to.y;
+      wz[W - 1 - d] = fmaf(-tz, oz, ez);
+    }
   }
   return make_int3(lx, ly, lz);
 }

@@ -34,6 +34,11 @@ struct BinSort {
 struct EsPoly {
   float c[8][10];
   float2 c2[8][10];   // each coefficient twice: two points or axes per packed FMA
+  // Mirror form: tap w-1-d is tap d at -t, so for d < (w+1)/2 the taps are
+  // E_d(t^2) +- t O_d(t^2) with the even and odd coefficient halves
+  // e2[d][k] = c[d][2k], o2[d][k] = c[d][2k+1] (each twice, packed FMAs).
+  float2 e2[4][5];
+  float2 o2[4][5];
 };
 __host__ __device__ constexpr int es_degree(int w) { return w < 7 ? w + 1 : w; }
 
