@@ -213,8 +213,7 @@ int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x
   const int N = P->N, PT = P->PT;
   int64_t PT3 = (int64_t)PT * PT * PT;
   SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for((int64_t)N * N * N), 256, 0, s>>>(x, N, PT, P->cubeP); }));
-  SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, nullptr, khat, -1, P->Mh + 1, 0, s));
-  SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, nullptr, nullptr, +1, 0, P->Mh + 1, s));
+  SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
   SPF_TRY(launch("crop_apply_kernel", s, [&] { crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3),
                                                        (float)lambda, x, out, part); }));
   return SPF_OK;

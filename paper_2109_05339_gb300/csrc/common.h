@@ -112,8 +112,14 @@ int fft3_exec(const FFT3* p, float2* data, int sign, int zero_halfwidth_in,
 // cube instead of `data` (not with zero_halfwidth_in > 0); out_real
 // (optional) -- the last pass writes only the real part there; post_mul
 // (optional) -- the last pass multiplies every output by this real cube.
+// With zero_halfwidth_in > 0 the input outside its range is never read.
 int fft3_exec_ex(const FFT3* p, float2* data, const float* in_real, float* out_real,
                  const float* post_mul, int sign, int zero_halfwidth_in,
                  int needed_halfwidth_out, cudaStream_t s);
+// IFFT(kernel * FFT(data)) in place (no 1/n^3 factor; forward sign -1), the
+// input zero outside the half width zero_halfwidth_in range (never read) and
+// outputs needed inside needed_halfwidth_out.
+int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_halfwidth_in,
+                  int needed_halfwidth_out, cudaStream_t s);
 
 }  // namespace spf

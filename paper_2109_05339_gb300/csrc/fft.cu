@@ -172,6 +172,7 @@ struct PassArgs {
   int64_t sa, sb;        // strides of the line coordinates a and b
   LineSet ls;
   int in_lo[2], in_hi[2];  // positions along the line that are read; the rest count as zero
+  int convolve;          // contiguous pass: transform, multiply by post_mul, transform back (-sign)
   int lines_per_cta;     // contiguous: lines per CTA; strided: b-lines per CTA
   int nrad;
   int radix[16];
@@ -410,6 +411,22 @@ __global__ void __launch_bounds__(kThreads) fft_contig_ct(PassArgs A) {
   cp_async_wait();
   __syncthreads();
   passes_ct<N, L, 1>(sbuf, nlines, stw, A.sign, typename RadixPlan<N>::type{});
+  if (A.convolve) {
+    // the last forward pass and the first inverse pass of a convolution act
+    // on the same lines: multiply in shared memory and transform back
+    for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
+      const int l = e / N, i = e - l * N;
+      const float f = __ldg(A.post_mul + lbase[l] + i);
+      sbuf[e] = make_float2(sbuf[e].x * f, sbuf[e].y * f);
+    }
+    __syncthreads();
+    passes_ct<N, L, 1>(sbuf, nlines, stw, -A.sign, typename RadixPlan<N>::type{});
+    for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
+      const int l = e / N, i = e - l * N;
+      A.data[lbase[l] + i] = sbuf[e];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
     const int l = e / N, i = e - l * N;
     store_elem(A, lbase[l] + i, sbuf[e]);
@@ -554,12 +571,13 @@ void fft3_destroy(FFT3* p) {
 static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real, float* out_real,
                      const float* post_mul, int sign, const int* a_lo, const int* a_hi,
                      const int* b_lo, const int* b_hi, cudaStream_t s, const int* in_lo = nullptr,
-                     const int* in_hi = nullptr) {
+                     const int* in_hi = nullptr, bool convolve = false) {
   PassArgs A;
   A.data = data;
   A.in_real = in_real;
   A.out_real = out_real;
   A.post_mul = post_mul;
+  A.convolve = convolve ? 1 : 0;
   const FFTAxisPlan& ax = p->ax[axis];
   A.n = ax.n;
   A.nrad = ax.nrad;
@@ -619,6 +637,38 @@ int fft3_exec_ex(const FFT3* p, float2* data, const float* in_real, float* out_r
   SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, sign, fz_lo, fz_hi, rx_lo, rx_hi, s));
   SPF_TRY(axis_pass(p, 2, data, nullptr, out_real, post_mul, sign, ry_lo, ry_hi, rx_lo, rx_hi, s));
   return SPF_OK;
+}
+
+// Circular convolution in place: IFFT(kernel * FFT(data)) without the 1/n^3,
+// forward sign -1. Input data only in the wrapped range of half width
+// zero_hw_in along each axis (the rest is never read), output needed only in
+// the range of half width need_hw_out. The forward x pass, the product and
+// the inverse x pass run as one pass over the same lines.
+int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_hw_in, int need_hw_out,
+                  cudaStream_t s) {
+  const int n0 = p->n0;
+  const bool fused = n0 == 36 || n0 == 72 || n0 == 162 || n0 == 216 || n0 == 320 || n0 == 324 ||
+                     n0 == 432 || n0 == 640;
+  if (!fused || zero_hw_in <= 0) {
+    SPF_TRY(fft3_exec_ex(p, data, nullptr, nullptr, kernel, -1, zero_hw_in, 0, s));
+    return fft3_exec_ex(p, data, nullptr, nullptr, nullptr, +1, 0, need_hw_out, s);
+  }
+  int fy_lo[2], fy_hi[2], fz_lo[2], fz_hi[2];
+  full_range(p->n1, fy_lo, fy_hi);
+  full_range(p->n2, fz_lo, fz_hi);
+  int rx_lo[2], rx_hi[2], ry_lo[2], ry_hi[2], rz_lo[2], rz_hi[2];
+  wrapped_range(p->n0, zero_hw_in, rx_lo, rx_hi);
+  wrapped_range(p->n1, zero_hw_in, ry_lo, ry_hi);
+  wrapped_range(p->n2, zero_hw_in, rz_lo, rz_hi);
+  SPF_TRY(axis_pass(p, 2, data, nullptr, nullptr, nullptr, -1, ry_lo, ry_hi, rx_lo, rx_hi, s, rz_lo, rz_hi));
+  SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, -1, fz_lo, fz_hi, rx_lo, rx_hi, s, ry_lo, ry_hi));
+  SPF_TRY(axis_pass(p, 0, data, nullptr, nullptr, kernel, -1, fz_lo, fz_hi, fy_lo, fy_hi, s, rx_lo, rx_hi,
+                    /*convolve=*/true));
+  int ox_lo[2], ox_hi[2], oy_lo[2], oy_hi[2];
+  wrapped_range(p->n0, need_hw_out, ox_lo, ox_hi);
+  wrapped_range(p->n1, need_hw_out, oy_lo, oy_hi);
+  SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, +1, fz_lo, fz_hi, ox_lo, ox_hi, s));
+  return axis_pass(p, 2, data, nullptr, nullptr, nullptr, +1, oy_lo, oy_hi, ox_lo, ox_hi, s);
 }
 
 }  // namespace spf
