@@ -86,3 +86,38 @@ def test_cg_matches_oracle(c1_merge, iters):
     xr, hr = merge.cg(lambda v: merge.apply_toeplitz(v, c["ref_khat"], N, lam), bt, f32(x0), iters)
     assert rel_l2(x, xr) < 1e-4
     np.testing.assert_allclose(hist.cpu().numpy(), hr, rtol=1e-4)
+
+
+def test_toeplitz_and_cg_at_generic_fft_sides():
+    """N = 21: fine grid 48, Toeplitz grid 90, embedding 48 -- no precompiled
+    FFT plan, so the generic passes and the unfused convolution run."""
+    import torch
+    from paper_2109_05339_gb300 import Plan
+    N = 21
+    pb = problem("c1")
+    qlab = pb.q_lab.astype(np.float32)
+    rng = np.random.default_rng(91)
+    q = rng.standard_normal((40, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q[q[:, 0] < 0] *= -1
+    quats = q.astype(np.float32)
+    plan = Plan(N, 1.0, 1e-6, max_points=quats.shape[0] * qlab.shape[0])
+    assert plan.PT == 48
+    images = rng.poisson(20.0, (quats.shape[0], qlab.shape[0])).astype(np.float32)
+    rhs, khat = plan.merge_images(to_dev(images), to_dev(quats), to_dev(qlab), b_scale=0.01)
+    plan.status()
+    t = rotation.nufft_points(f32(quats), f32(qlab), N, 1.0).reshape(-1, 3)
+    ones = np.ones(t.shape[0])
+    ref_rhs = merge.rhs(f32(images).reshape(-1) * 0.01, t, ones, N)
+    ref_khat = merge.kernel_hat(merge.toeplitz_kernel(t, ones, N), N)
+    assert rel_l2(rhs.cpu().numpy(), ref_rhs) < 1e-5
+    assert rel_l2(khat.cpu().numpy(), ref_khat) < 1e-5
+    lam = 1e-3 * float(ones.sum())
+    x0 = (rng.standard_normal((N, N, N)) * 0.01).astype(np.float32)
+    y = plan.toeplitz_apply(khat, lam, to_dev(x0)).cpu().numpy()
+    assert rel_l2(y, merge.apply_toeplitz(f32(x0), ref_khat, N, lam)) < 1e-5
+    hist = torch.zeros(4, dtype=torch.float64, device="cuda")
+    x = plan.cg_solve(khat, lam, rhs, to_dev(x0), 3, res_hist=hist).cpu().numpy()
+    xr, hr = merge.cg(lambda v: merge.apply_toeplitz(v, ref_khat, N, lam), ref_rhs + lam * f32(x0), f32(x0), 3)
+    assert rel_l2(x, xr) < 1e-4
+    plan.close()
