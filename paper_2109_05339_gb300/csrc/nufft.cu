@@ -1,4 +1,4 @@
-// Type-2 (slicing) and type-1 (merging) NUFFT kernels, FP32 (sm_103a).
+// Type-2 (slicing) and type-1 (merging) NUFFT kernels (sm_103a).
 //
 // Slicing (Sec. II-A) evaluates Re sum_n A_n exp(-i n.t) at the rotated
 // detector points; merging (Sec. II-C) needs the adjoint sums. Both follow the
@@ -7,20 +7,24 @@
 //   * points are never stored: each kernel recomputes t = R(quat) q_lab on
 //     the fly from the orientation and pixel index (rotation fused into the
 //     interpolation and spreading kernels);
-//   * both directions first counting-sort the points by the fine-grid cell
-//     of their tap origin (bin-major, warp-aggregated atomics, multi-block
-//     scan). Every slice passes through q = 0, so cells are dense: points with
-//     equal keys share their whole w^3 window;
-//   * type 2 deconvolves into a zero-padded complex cube, runs the pruned
-//     hand-written FFT, keeps the real part (the model is real) and gathers
-//     w^3 taps per point from that L2-resident real grid in sorted order, so
-//     the lanes of a warp mostly read the same addresses (L1 broadcasts);
-//   * type 1 gives each warp a private shared-memory subgrid of one bin: a
-//     lane owns a fixed (dy, dx) tap column and accumulates its w x 2 cells in
-//     registers while consecutive points share a tap origin, writing them back
-//     (plain read-modify-write: no two lanes touch one cell) only when the
-//     origin changes; subgrids are added to the fine grid with red.add once
-//     per subproblem. No shared-memory atomics are used.
+//   * kernel weights come from per-tap polynomials in mirror form (see
+//     es_poly) instead of sqrt / exp per tap;
+//   * points are counting-sorted by the fine-grid cell of their tap origin
+//     (bin-major; within a 4^3-cell bin by 2^3 cell block), once per fixed
+//     orientation set (point sets);
+//   * type 2 deconvolves into the zero-padded cube (mode entries only), runs
+//     the pruned hand-written FFT and keeps the real part. On point sets the
+//     window of each bin is contracted with the points' x weights on the
+//     tensor cores (tcgen05 kind::tf32 with hi/lo split operands) and each
+//     point finishes its y and z sums in registers; the per-call path
+//     gathers w^3 taps per point from x-shifted halo copies of the grid;
+//   * type 1 gives each warp a private shared-memory subgrid of one bin:
+//     contributing points are queued, staged 32 at a time, and a lane owns a
+//     fixed column of two window rows over 8 planes, accumulating a whole 2^3
+//     cell block of points in registers (packed FP32 FMAs) before a plain
+//     read-modify-write of the subgrid (no two lanes touch one cell);
+//     subgrids go back to the fine grid as vector reductions once per
+//     subproblem. No shared-memory atomics are used.
 #include <cmath>
 #include <vector>
 
