@@ -280,14 +280,31 @@ __device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
   return (bin << (3 * B)) | (pair << 3) | sub;
 }
 
+// Runs of equal keys in adjacent lanes (consecutive ids: neighbouring pixels
+// of one orientation, mostly one cell) share one atomic. For lane l: its
+// run's first lane, its rank in the run and the run's length (valid in the
+// first lane).
+struct KeyRun {
+  int leader, rank, len;
+};
+__device__ __forceinline__ KeyRun key_run(int key) {
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+  const unsigned upto = lane == 31 ? heads : heads & ((2u << lane) - 1u);   // heads at or below lane
+  const int leader = 31 - __clz(upto);
+  const unsigned above = lane == 31 ? 0u : heads & ~((2u << lane) - 1u);   // heads above lane
+  const int next = above ? __ffs(above) - 1 : 32;
+  return {leader, lane - leader, next - lane};
+}
+
 template <int W, class Pts>
 __global__ void key_count_kernel(Pts pts, int64_t npts, SortGeom g, int* __restrict__ count) {
   int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int key = -1;
   if (id < npts) key = point_key<W>(pts((uint32_t)id), g);
-  unsigned grp = __match_any_sync(0xffffffffu, key);
-  int lane = threadIdx.x & 31;
-  if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(count + key, __popc(grp));
+  const KeyRun run = key_run(key);
+  if (key >= 0 && run.rank == 0) atomicAdd(count + key, run.len);
 }
 
 template <int W, class Pts>
@@ -296,15 +313,12 @@ __global__ void key_scatter_kernel(Pts pts, int64_t npts, SortGeom g, const int*
   int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int key = -1;
   if (id < npts) key = point_key<W>(pts((uint32_t)id), g);
-  unsigned grp = __match_any_sync(0xffffffffu, key);
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(grp) - 1;
-  int rank = __popc(grp & ((1u << lane) - 1u));
+  const KeyRun run = key_run(key);
   int base = 0;
-  if (key >= 0 && lane == leader) base = atomicAdd(fill + key, __popc(grp));
-  base = __shfl_sync(grp, base, leader);
+  if (key >= 0 && run.rank == 0) base = atomicAdd(fill + key, run.len);
+  base = __shfl_sync(0xffffffffu, base, run.leader);
   if (key >= 0) {
-    int pos = start[key] + base + rank;
+    int pos = start[key] + base + run.rank;
     if (pos < start[key + 1]) sorted[pos] = (uint32_t)id;
     else atomicOr(err, 1);   // counting and scattering disagreed: skip, never overrun
   }
