@@ -117,6 +117,7 @@ static void plan_free(spf_plan* P) {
   cudaFree(P->cg_Ap);
   cudaFree(P->cg_sc);
   cudaFree(P->cg_part);
+  cudaFree(P->cg_count);
   cudaFree(P->err);
   delete P;
 }

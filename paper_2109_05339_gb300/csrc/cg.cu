@@ -39,6 +39,48 @@ __device__ double block_sum(double v) {
   return r;
 }
 
+// CG scalars from the reduced sum s: mode 0 r.r (and beta = 0), mode 1 p.Ap
+// and alpha, mode 2 the new r.r and beta.
+__device__ __forceinline__ void cg_scalars(double s, double* __restrict__ sc, int mode,
+                                           double* __restrict__ res_out) {
+  if (mode == 0) {
+    sc[0] = s;
+    sc[3] = 0.0;
+  } else if (mode == 1) {
+    sc[1] = s;
+    sc[2] = s > 0.0 ? sc[0] / s : 0.0;
+  } else {
+    sc[4] = s;
+    sc[3] = sc[0] > 0.0 ? s / sc[0] : 0.0;
+    sc[0] = s;
+  }
+  sc[5] = sqrt(sc[0]);
+  if (res_out) *res_out = sc[5];
+}
+
+// Store this block's partial; the last block to finish sums all partials (in
+// the fixed order of finalize_kernel: the same result) and updates the CG
+// scalars, so no separate reduction launch is needed.
+__device__ void partial_and_finalize(double s_block, double* __restrict__ part, double* __restrict__ sc,
+                                     int mode, double* __restrict__ res_out, unsigned* __restrict__ count) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s_block;
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(part + i);
+  const double s = block_sum(v);
+  if (threadIdx.x == 0) {
+    cg_scalars(s, sc, mode, res_out);
+    *count = 0u;
+  }
+}
+
 // cube (PT^3 complex) = x at n mod PT (|n| <= Mh), zero elsewhere.
 // x (N^3) into the circulant-embedding cube at n mod PT. Only those N^3
 // entries are written: the pruned forward FFT reads nothing else.
@@ -53,10 +95,11 @@ __global__ void pad_kernel(const float* __restrict__ x, int N, int PT, float2* _
   }
 }
 
-// out = Re(cube[n mod PT]) / PT^3 + lambda x; partial sums of x . out.
+// out = Re(cube[n mod PT]) / PT^3 + lambda x; partial sums of x . out
+// (finalised in the kernel, mode 1, when `count` is given).
 __global__ void crop_apply_kernel(const float2* __restrict__ cube, int N, int PT, float inv_n,
                                   float lambda, const float* __restrict__ x, float* __restrict__ out,
-                                  double* __restrict__ part) {
+                                  double* __restrict__ part, double* __restrict__ sc, unsigned* count) {
   int64_t n3 = (int64_t)N * N * N;
   int Mh = (N - 1) / 2;
   double acc = 0.0;
@@ -69,7 +112,8 @@ __global__ void crop_apply_kernel(const float2* __restrict__ cube, int N, int PT
     acc += (double)x[i] * (double)v;
   }
   double s = block_sum(acc);
-  if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
+  if (count) partial_and_finalize(s, part, sc, 1, nullptr, count);
+  else if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
 }
 
 // x = x0; r = rhs + lambda x0 - Hx0; p = r; partial |r|^2.
@@ -99,26 +143,15 @@ __global__ void finalize_kernel(const double* __restrict__ part, int nparts, dou
   double v = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
   double s = block_sum(v);
-  if (threadIdx.x == 0) {
-    if (mode == 0) {
-      sc[0] = s;
-    } else if (mode == 1) {
-      sc[1] = s;
-      sc[2] = s > 0.0 ? sc[0] / s : 0.0;
-    } else {
-      sc[4] = s;
-      sc[3] = sc[0] > 0.0 ? s / sc[0] : 0.0;
-      sc[0] = s;
-    }
-    sc[5] = sqrt(sc[0]);
-    if (res_out) *res_out = sc[5];
-  }
+  if (threadIdx.x == 0) cg_scalars(s, sc, mode, res_out);
 }
+
 
 // x += alpha p; r -= alpha Ap; partial |r|^2.
 __global__ void cg_update_kernel(float* __restrict__ x, float* __restrict__ r,
                                  const float* __restrict__ p, const float* __restrict__ Ap,
-                                 const double* __restrict__ sc, int64_t n, double* __restrict__ part) {
+                                 double* __restrict__ sc, int64_t n, double* __restrict__ part,
+                                 double* __restrict__ res_out, unsigned* count) {
   const float alpha = (float)sc[2];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -128,18 +161,26 @@ __global__ void cg_update_kernel(float* __restrict__ x, float* __restrict__ r,
     r[i] = rv;
     acc += (double)rv * (double)rv;
   }
-  double s = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  partial_and_finalize(block_sum(acc), part, sc, 2, res_out, count);
 }
 
-// p = r + beta p
-__global__ void cg_dir_kernel(const float* __restrict__ r, float* __restrict__ p,
-                              const double* __restrict__ sc, int64_t n) {
+// p = r + beta p (beta from the last step; 0 after cg_begin), and p into the
+// circulant-embedding cube at n mod PT (as pad_kernel).
+__global__ void pad_dir_kernel(const float* __restrict__ r, float* __restrict__ p,
+                               const double* __restrict__ sc, int N, int PT, float2* __restrict__ cube) {
   const float beta = (float)sc[3];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fmaf(beta, p[i], r[i]);
+  const int64_t total = (int64_t)N * N * N;
+  const int Mh = (N - 1) / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float pv = fmaf(beta, p[i], r[i]);
+    p[i] = pv;
+    const int a = (int)(i % N), b = (int)((i / N) % N), c = (int)(i / ((int64_t)N * N));
+    const int gx = wrapi(a - Mh, PT), gy = wrapi(b - Mh, PT), gz = wrapi(c - Mh, PT);
+    cube[((size_t)gz * PT + gy) * PT + gx] = make_float2(pv, 0.f);
+  }
 }
+
 
 // Per-block partials of x.Tx, x.rhs and |x - x0|^2 (FP64).
 __global__ void objective_kernel(const float* __restrict__ x, const float* __restrict__ Tx,
@@ -215,7 +256,7 @@ int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x
   SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for((int64_t)N * N * N), 256, 0, s>>>(x, N, PT, P->cubeP); }));
   SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
   SPF_TRY(launch("crop_apply_kernel", s, [&] { crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3),
-                                                       (float)lambda, x, out, part); }));
+                                                       (float)lambda, x, out, part, nullptr, nullptr); }));
   return SPF_OK;
 }
 
@@ -230,14 +271,20 @@ int cg_begin(spf_plan* P, const float* khat, double lambda, const float* rhs, co
 }
 
 int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res, cudaStream_t s) {
-  int64_t n3 = (int64_t)P->N * P->N * P->N;
-  SPF_TRY(toeplitz_apply(P, khat, lambda, P->cg_p, P->cg_Ap, P->cg_part, s));
-  SPF_TRY(launch("finalize_kernel", s, [&] { finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks, P->cg_sc, 1, nullptr); }));
-  SPF_TRY(launch("cg_update_kernel", s, [&] { cg_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, P->cg_r, P->cg_p, P->cg_Ap, P->cg_sc, n3,
-                                                      P->cg_part); }));
-  SPF_TRY(launch("finalize_kernel", s, [&] { finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks, P->cg_sc, 2, res); }));
-  SPF_TRY(launch("cg_dir_kernel", s, [&] { cg_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, n3); }));
-  return SPF_OK;
+  // p = r + beta p is applied while padding p (beta of the previous step, 0
+  // after cg_begin); both inner products are finalised inside their kernels
+  const int N = P->N, PT = P->PT;
+  const int64_t n3 = (int64_t)N * N * N, PT3 = (int64_t)PT * PT * PT;
+  SPF_TRY(launch("pad_kernel", s, [&] { pad_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, N, PT, P->cubeP); }));
+  SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
+  SPF_TRY(launch("crop_apply_kernel", s, [&] {
+    crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3), (float)lambda,
+                                                         P->cg_p, P->cg_Ap, P->cg_part, P->cg_sc, P->cg_count);
+  }));
+  return launch("cg_update_kernel", s, [&] {
+    cg_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, P->cg_r, P->cg_p, P->cg_Ap, P->cg_sc, n3, P->cg_part,
+                                                        res, P->cg_count);
+  });
 }
 
 int cg_alloc(spf_plan* P) {
@@ -247,7 +294,9 @@ int cg_alloc(spf_plan* P) {
   SPF_TRY(dev_alloc((void**)&P->cg_Ap, sizeof(float) * n3, "cg Ap"));
   SPF_TRY(dev_alloc((void**)&P->cg_sc, sizeof(double) * 8, "cg scalars"));
   SPF_TRY(dev_alloc((void**)&P->cg_part, sizeof(double) * kRedBlocks, "cg partials"));
+  SPF_TRY(dev_alloc((void**)&P->cg_count, sizeof(unsigned), "cg reduction counter"));
   SPF_CUDA(cudaMemset(P->cg_sc, 0, sizeof(double) * 8));
+  SPF_CUDA(cudaMemset(P->cg_count, 0, sizeof(unsigned)));
   return SPF_OK;
 }
 

@@ -87,6 +87,7 @@ struct spf_plan {
   float* cg_Ap = nullptr;
   double* cg_sc = nullptr;    // [rr, pAp, alpha, beta, rr_new, res]
   double* cg_part = nullptr;  // per-block partial sums
+  unsigned* cg_count = nullptr;  // blocks done with a fused reduction (last one finalises)
   int* err = nullptr;         // device error word (bit 1: point outside its bin)
 };
 
