@@ -969,6 +969,20 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
     }
   };
   int k = 0;
+  // a batch whose records all share one window (the usual case: points are
+  // sorted by cell block) is added with no per-record window check
+  if (nrec > 0) {
+    const int key0 = __float_as_int(stage[0]);
+    const bool same = lane >= nrec || __float_as_int(stage[lane * C::REC]) == key0;
+    if (__all_sync(0xffffffffu, same)) {
+      if (key0 != cur) {
+        if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
+        cur = key0;
+      }
+#pragma unroll 8
+      for (; k < nrec; ++k) add(stage + k * C::REC);
+    }
+  }
   while (k < nrec) {
     const float* rec = stage + k * C::REC;
     const int key_k = __float_as_int(rec[0]);   // uniform: every lane reads record k
