@@ -822,8 +822,10 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
       }
       if (ok) out[id] = acc;
       id = id_next;
-      tc_fence_before();
-      __syncthreads();
+      // no barrier here: a thread rewrites its A row only after the MMA that
+      // read it has completed (the wait above), and the next MMA overwrites
+      // tensor memory only after the next block's barrier, which every
+      // thread reaches after its tensor-memory loads of this block
     }
     if (aborted) break;
   }
