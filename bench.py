@@ -292,7 +292,7 @@ def run_ours(args, rank, world):
                                         "results")) else
                "sort" if k.startswith(("key_", "scan_", "build_subs")) else
                "merge" if k.startswith(("spread", "crop_deconv", "crop_embed", "accumulate")) else
-               "cg" if k.startswith(("pad_kernel", "crop_apply", "cg_", "finalize")) else
+               "cg" if k.startswith(("pad_kernel", "crop_apply", "apply_kernel", "cg_", "finalize")) else
                "fft" if k.startswith("fft") else "other")
         stage[grp] = stage.get(grp, 0.0) + v["ms_per_step"]
 

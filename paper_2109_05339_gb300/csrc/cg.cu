@@ -116,6 +116,25 @@ __global__ void crop_apply_kernel(const float2* __restrict__ cube, int N, int PT
   else if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
 }
 
+// out = raw / PT^3 + lambda x, raw the real convolution output at the model
+// indices (out may be raw itself); partial sums of x . out (finalised in the
+// kernel, mode 1, when `count` is given).
+__global__ void apply_kernel(const float* raw, int64_t n3, float inv_n, float lambda,
+                             const float* __restrict__ x, float* out, double* __restrict__ part,
+                             double* __restrict__ sc, unsigned* count) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float xv = x[i];
+    const float v = raw[i] * inv_n + lambda * xv;
+    out[i] = v;
+    acc += (double)xv * (double)v;
+  }
+  double s = block_sum(acc);
+  if (count) partial_and_finalize(s, part, sc, 1, nullptr, count);
+  else if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
+}
+
 // x = x0; r = rhs + lambda x0 - Hx0; p = r; partial |r|^2.
 __global__ void cg_init_kernel(const float* __restrict__ rhs, const float* __restrict__ x0,
                                const float* __restrict__ Hx0, float lambda, int64_t n,
@@ -253,6 +272,14 @@ int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x
                    double* part, cudaStream_t s) {
   const int N = P->N, PT = P->PT;
   int64_t PT3 = (int64_t)PT * PT * PT;
+  if (fft3_real_conv_supported(&P->fftP)) {
+    const int64_t n3 = (int64_t)N * N * N;
+    SPF_TRY(fft3_convolve_real(&P->fftP, N, x, nullptr, nullptr, nullptr, khat, P->cubeP, P->realP, s));
+    return launch("apply_kernel", s, [&] {
+      apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->realP, n3, (float)(1.0 / (double)PT3), (float)lambda, x,
+                                                      out, part, nullptr, nullptr);
+    });
+  }
   SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for((int64_t)N * N * N), 256, 0, s>>>(x, N, PT, P->cubeP); }));
   SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
   SPF_TRY(launch("crop_apply_kernel", s, [&] { crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3),
@@ -275,12 +302,21 @@ int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res
   // after cg_begin); both inner products are finalised inside their kernels
   const int N = P->N, PT = P->PT;
   const int64_t n3 = (int64_t)N * N * N, PT3 = (int64_t)PT * PT * PT;
-  SPF_TRY(launch("pad_kernel", s, [&] { pad_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, N, PT, P->cubeP); }));
-  SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
-  SPF_TRY(launch("crop_apply_kernel", s, [&] {
-    crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3), (float)lambda,
-                                                         P->cg_p, P->cg_Ap, P->cg_part, P->cg_sc, P->cg_count);
-  }));
+  if (fft3_real_conv_supported(&P->fftP)) {
+    // real-input transforms; the direction update rides on the first pass
+    SPF_TRY(fft3_convolve_real(&P->fftP, N, P->cg_p, P->cg_r, P->cg_sc + 3, P->cg_p, khat, P->cubeP, P->cg_Ap, s));
+    SPF_TRY(launch("apply_kernel", s, [&] {
+      apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cg_Ap, n3, (float)(1.0 / (double)PT3), (float)lambda,
+                                                      P->cg_p, P->cg_Ap, P->cg_part, P->cg_sc, P->cg_count);
+    }));
+  } else {
+    SPF_TRY(launch("pad_kernel", s, [&] { pad_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, N, PT, P->cubeP); }));
+    SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
+    SPF_TRY(launch("crop_apply_kernel", s, [&] {
+      crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3), (float)lambda,
+                                                           P->cg_p, P->cg_Ap, P->cg_part, P->cg_sc, P->cg_count);
+    }));
+  }
   return launch("cg_update_kernel", s, [&] {
     cg_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, P->cg_r, P->cg_p, P->cg_Ap, P->cg_sc, n3, P->cg_part,
                                                         res, P->cg_count);

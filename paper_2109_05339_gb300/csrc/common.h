@@ -121,5 +121,16 @@ int fft3_exec_ex(const FFT3* p, float2* data, const float* in_real, float* out_r
 // outputs needed inside needed_halfwidth_out.
 int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_halfwidth_in,
                   int needed_halfwidth_out, cudaStream_t s);
+// Real-input circular convolution: the real vector x (Nm^3, Nm odd,
+// 2 Nm - 1 <= side) embedded at wrapped positions of the cube (model index a
+// -> (a - (Nm - 1) / 2) mod side), y = IFFT(kernel * FFT(embed x)) read back
+// at the same positions (no 1/n^3 factor; forward sign -1; kernel is a real
+// cube in the full layout and must be real and even). With `add` given the
+// transformed vector is add + (*beta) x, also stored to x_new. work holds
+// side^2 (side / 2 + 1) complex values. Only for the cube sides that
+// fft3_real_conv_supported accepts.
+bool fft3_real_conv_supported(const FFT3* p);
+int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, const double* beta,
+                       float* x_new, const float* kernel, float2* work, float* y, cudaStream_t s);
 
 }  // namespace spf

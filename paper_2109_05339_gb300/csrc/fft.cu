@@ -172,7 +172,8 @@ struct PassArgs {
   int64_t sa, sb;        // strides of the line coordinates a and b
   LineSet ls;
   int in_lo[2], in_hi[2];  // positions along the line that are read; the rest count as zero
-  int convolve;          // contiguous pass: transform, multiply by post_mul, transform back (-sign)
+  int convolve;          // transform, multiply by post_mul, transform back (-sign)
+  int64_t pm_es, pm_sa, pm_sb;  // strided convolution: post_mul strides (along the line, a, b)
   int lines_per_cta;     // contiguous: lines per CTA; strided: b-lines per CTA
   int nrad;
   int radix[16];
@@ -444,8 +445,12 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
   const int a = pick(blockIdx.x / tiles_b, A.ls.a_lo, A.ls.a_hi);
   const int first = tile * T;
   const int nlines = min(T, nb_sel - first);
-  if (threadIdx.x < nlines)
-    lbase[threadIdx.x] = (int64_t)a * A.sa + (int64_t)pick(first + threadIdx.x, A.ls.b_lo, A.ls.b_hi) * A.sb;
+  __shared__ int64_t pbase[T];
+  if (threadIdx.x < nlines) {
+    const int b = pick(first + threadIdx.x, A.ls.b_lo, A.ls.b_hi);
+    lbase[threadIdx.x] = (int64_t)a * A.sa + (int64_t)b * A.sb;
+    pbase[threadIdx.x] = (int64_t)a * A.pm_sa + (int64_t)b * A.pm_sb;
+  }
   __syncthreads();
   float2* stw = sbuf + T * N;
   stage_twiddles(stw, A.tw, N);
@@ -456,10 +461,157 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
   cp_async_wait();
   __syncthreads();
   passes_ct<N, T, 1>(sbuf, nlines, stw, A.sign, typename RadixPlan<N>::type{});
+  if (A.convolve) {
+    // forward transform, product with the kernel (its own strides), inverse
+    for (int e = threadIdx.x; e < T * N; e += kThreads) {
+      const int l = e % T, i = e / T;
+      if (l < nlines) {
+        const float f = __ldg(A.post_mul + pbase[l] + (int64_t)i * A.pm_es);
+        const float2 v = sbuf[l * N + i];
+        sbuf[l * N + i] = make_float2(v.x * f, v.y * f);
+      }
+    }
+    __syncthreads();
+    passes_ct<N, T, 1>(sbuf, nlines, stw, -A.sign, typename RadixPlan<N>::type{});
+    for (int e = threadIdx.x; e < T * N; e += kThreads) {
+      const int l = e % T, i = e / T;
+      if (l < nlines) A.data[lbase[l] + (int64_t)i * A.es] = sbuf[l * N + i];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < T * N; e += kThreads) {
     const int l = e % T, i = e / T;
     if (l < nlines) store_elem(A, lbase[l] + (int64_t)i * A.es, sbuf[l * N + i]);
   }
+}
+
+// ------------------------------------------------------ real-input rows -----
+// Transforms along x for the circulant convolution of a real vector x
+// (Nm^3, [z][y][x]) embedded at wrapped positions of an N-point cube (model
+// index a -> (a - Mh) mod N, Mh = (Nm - 1) / 2). Two rows u, w of x share one
+// complex line c = u + i w; with C = FFT(c) the rows' own transforms are
+// U[k] = (C[k] + conj C[-k]) / 2 and W[k] = (C[k] - conj C[-k]) / (2i). Only
+// k = 0 .. N/2 is kept (the rest is the conjugate mirror of a real row), in
+// the half-spectrum cube [N][N][N/2 + 1]. The inverse rebuilds C from the
+// two half spectra and takes u = Re c, w = Im c.
+template <int N>
+__host__ __device__ constexpr int rc_lines() { return (kMaxElems / N) < 8 ? (kMaxElems / N) : 8; }
+
+// Model index held at line position i of the wrapped embedding, or -1.
+__device__ __forceinline__ int model_index(int i, int N, int Nm, int Mh) {
+  const int a = i <= Mh ? i + Mh : i - N + Mh;
+  return (i <= Mh || i >= N - Mh) && a >= 0 && a < Nm ? a : -1;
+}
+
+// Line position of model index b.
+__device__ __forceinline__ int wrap_pos(int b, int N, int Mh) { return b >= Mh ? b - Mh : b - Mh + N; }
+
+// Forward transform of row pairs (2m, 2m + 1) of plane c (line li = c HP + m,
+// HP = (Nm + 1) / 2; a missing last row reads as zero). The row value is
+// x, or add + beta x when `add` is given (then also stored to x_new).
+template <int N>
+__global__ void __launch_bounds__(kThreads) r2c_rows_ct(const float* x, const float* __restrict__ add,
+                                                         const double* __restrict__ beta, float* x_new,
+                                                         const float2* __restrict__ tw, int Nm,
+                                                         float2* __restrict__ out) {
+  constexpr int L = rc_lines<N>(), H = N / 2 + 1;
+  extern __shared__ float2 sbuf[];
+  const int Mh = (Nm - 1) / 2, HP = (Nm + 1) / 2;
+  const int first = blockIdx.x * L;
+  const int nlines = min(L, Nm * HP - first);
+  float2* stw = sbuf + L * N;
+  stage_twiddles(stw, tw, N);
+  const float bt = add ? (float)__ldg(beta) : 0.f;
+  for (int e = threadIdx.x; e < L * N; e += kThreads) {
+    const int l = e / N, i = e - l * N;
+    const int a = model_index(i, N, Nm, Mh);
+    float2 v = make_float2(0.f, 0.f);
+    if (l < nlines && a >= 0) {
+      const int li = first + l, c = li / HP, m = li - c * HP;
+      const int64_t r0 = ((int64_t)c * Nm + 2 * m) * Nm + a;
+      float u = x[r0], w = 0.f;
+      const bool second = 2 * m + 1 < Nm;
+      if (second) w = x[r0 + Nm];
+      if (add) {
+        u = fmaf(bt, u, __ldg(add + r0));
+        x_new[r0] = u;
+        if (second) {
+          w = fmaf(bt, w, __ldg(add + r0 + Nm));
+          x_new[r0 + Nm] = w;
+        }
+      }
+      v = make_float2(u, w);
+    }
+    sbuf[e] = v;
+  }
+  __syncthreads();
+  passes_ct<N, L, 1>(sbuf, nlines, stw, -1.f, typename RadixPlan<N>::type{});
+  for (int e = threadIdx.x; e < L * H; e += kThreads) {
+    const int l = e / H, k = e - l * H;
+    if (l >= nlines) continue;
+    const int li = first + l, c = li / HP, m = li - c * HP;
+    const float2 ck = sbuf[l * N + k], cm = sbuf[l * N + (k == 0 ? 0 : N - k)];
+    const int64_t plane = (int64_t)wrap_pos(c, N, Mh) * N;
+    out[(plane + wrap_pos(2 * m, N, Mh)) * H + k] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
+    if (2 * m + 1 < Nm)
+      out[(plane + wrap_pos(2 * m + 1, N, Mh)) * H + k] =
+          make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
+  }
+}
+
+// Inverse of the above: row pairs of the half-spectrum cube back to the
+// real rows (no 1/N factor), written at model indices into y (Nm^3).
+template <int N>
+__global__ void __launch_bounds__(kThreads) c2r_rows_ct(const float2* __restrict__ in,
+                                                         const float2* __restrict__ tw, int Nm,
+                                                         float* __restrict__ y) {
+  constexpr int L = rc_lines<N>(), H = N / 2 + 1;
+  extern __shared__ float2 sbuf[];
+  const int Mh = (Nm - 1) / 2, HP = (Nm + 1) / 2;
+  const int first = blockIdx.x * L;
+  const int nlines = min(L, Nm * HP - first);
+  float2* stw = sbuf + L * N;
+  stage_twiddles(stw, tw, N);
+  for (int e = threadIdx.x; e < L * N; e += kThreads) {
+    const int l = e / N, k = e - l * N;
+    float2 v = make_float2(0.f, 0.f);
+    if (l < nlines) {
+      const int li = first + l, c = li / HP, m = li - c * HP;
+      const int64_t plane = (int64_t)wrap_pos(c, N, Mh) * N;
+      const int kk = k < H ? k : N - k;
+      const float2 u = __ldg(in + (plane + wrap_pos(2 * m, N, Mh)) * H + kk);
+      const float2 w = 2 * m + 1 < Nm ? __ldg(in + (plane + wrap_pos(2 * m + 1, N, Mh)) * H + kk)
+                                      : make_float2(0.f, 0.f);
+      // C[k] = U[k] + i W[k]; past N/2, U[k] = conj U[N - k] (and W alike)
+      v = k < H ? make_float2(u.x - w.y, u.y + w.x) : make_float2(u.x + w.y, w.x - u.y);
+    }
+    sbuf[e] = v;
+  }
+  __syncthreads();
+  passes_ct<N, L, 1>(sbuf, nlines, stw, 1.f, typename RadixPlan<N>::type{});
+  for (int e = threadIdx.x; e < L * Nm; e += kThreads) {
+    const int l = e / Nm, a = e - l * Nm;
+    if (l >= nlines) continue;
+    const int li = first + l, c = li / HP, m = li - c * HP;
+    const float2 v = sbuf[l * N + wrap_pos(a, N, Mh)];
+    const int64_t r0 = ((int64_t)c * Nm + 2 * m) * Nm + a;
+    y[r0] = v.x;
+    if (2 * m + 1 < Nm) y[r0 + Nm] = v.y;
+  }
+}
+
+template <int N>
+int launch_rows_ct(bool forward, const FFT3* p, int Nm, const float* x, const float* add,
+                   const double* beta, float* x_new, float2* work, float* y, cudaStream_t s) {
+  constexpr int L = rc_lines<N>();
+  const unsigned grid = (unsigned)ceil_div((int64_t)Nm * ((Nm + 1) / 2), L);
+  const size_t smem = (size_t)(L + 1) * N * sizeof(float2);   // lines and the twiddle table
+  const float2* tw = p->ax[0].twiddle;
+  if (forward)
+    return launch("fft_r2c_rows_kernel", s,
+                  [&] { r2c_rows_ct<N><<<grid, kThreads, smem, s>>>(x, add, beta, x_new, tw, Nm, work); });
+  return launch("fft_c2r_rows_kernel", s,
+                [&] { c2r_rows_ct<N><<<grid, kThreads, smem, s>>>(work, tw, Nm, y); });
 }
 
 template <int N>
@@ -571,7 +723,7 @@ void fft3_destroy(FFT3* p) {
 static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real, float* out_real,
                      const float* post_mul, int sign, const int* a_lo, const int* a_hi,
                      const int* b_lo, const int* b_hi, cudaStream_t s, const int* in_lo = nullptr,
-                     const int* in_hi = nullptr, bool convolve = false) {
+                     const int* in_hi = nullptr, bool convolve = false, int row = 0) {
   PassArgs A;
   A.data = data;
   A.in_real = in_real;
@@ -584,7 +736,10 @@ static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real
   for (int i = 0; i < ax.nrad; ++i) A.radix[i] = ax.radix[i];
   A.tw = ax.twiddle;
   A.sign = (float)sign;
-  const int64_t n0 = p->n0, n1 = p->n1;
+  // row > 0: the data is the half-spectrum cube of a real-input transform,
+  // rows of `row` entries; post_mul keeps the full cube's strides
+  const int64_t n0 = row > 0 ? row : p->n0, n1 = p->n1;
+  const int64_t f0 = p->n0, f1 = p->n1;
   for (int i = 0; i < 2; ++i) {
     A.ls.a_lo[i] = a_lo[i]; A.ls.a_hi[i] = a_hi[i];
     A.ls.b_lo[i] = b_lo[i]; A.ls.b_hi[i] = b_hi[i];
@@ -593,12 +748,15 @@ static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real
   }
   if (axis == 0) {          // lines (z, y): a = z, b = y
     A.es = 1; A.sa = n1 * n0; A.sb = n0;
+    A.pm_es = 1; A.pm_sa = f1 * f0; A.pm_sb = f0;
     return launch_pass(A, true, s);
   } else if (axis == 1) {   // lines (z, x): a = z, b = x
     A.es = n0; A.sa = n1 * n0; A.sb = 1;
+    A.pm_es = f0; A.pm_sa = f1 * f0; A.pm_sb = 1;
     return launch_pass(A, false, s);
   } else {                  // lines (y, x): a = y, b = x
     A.es = n1 * n0; A.sa = n0; A.sb = 1;
+    A.pm_es = f1 * f0; A.pm_sa = f0; A.pm_sb = 1;
     return launch_pass(A, false, s);
   }
 }
@@ -669,6 +827,49 @@ int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_hw_
   wrapped_range(p->n1, need_hw_out, oy_lo, oy_hi);
   SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, +1, fz_lo, fz_hi, ox_lo, ox_hi, s));
   return axis_pass(p, 2, data, nullptr, nullptr, nullptr, +1, oy_lo, oy_hi, ox_lo, ox_hi, s);
+}
+
+static int launch_rows(bool forward, const FFT3* p, int Nm, const float* x, const float* add,
+                       const double* beta, float* x_new, float2* work, float* y, cudaStream_t s) {
+  switch (p->n0) {
+    case 36: return launch_rows_ct<36>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    case 72: return launch_rows_ct<72>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    case 162: return launch_rows_ct<162>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    case 216: return launch_rows_ct<216>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    case 320: return launch_rows_ct<320>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    case 324: return launch_rows_ct<324>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    case 432: return launch_rows_ct<432>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    case 640: return launch_rows_ct<640>(forward, p, Nm, x, add, beta, x_new, work, y, s);
+    default: break;
+  }
+  set_error("fft: no real-input row transform for side %d", p->n0);
+  return SPF_ERR_UNSUPPORTED;
+}
+
+bool fft3_real_conv_supported(const FFT3* p) {
+  const int n = p->n0;
+  return p->n1 == n && p->n2 == n &&
+         (n == 36 || n == 72 || n == 162 || n == 216 || n == 320 || n == 324 || n == 432 || n == 640);
+}
+
+// y = IFFT(kernel * FFT(embed x)) at the model indices, for real x: real-
+// input row transforms along x, then y and z passes on the half spectrum
+// (the z pass forward, times the kernel, and back in one launch).
+int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, const double* beta,
+                       float* x_new, const float* kernel, float2* work, float* y, cudaStream_t s) {
+  SPF_CHECK_ARG(fft3_real_conv_supported(p), "fft: side %d has no real-input convolution", p->n0);
+  const int n = p->n0, H = n / 2 + 1, Mh = (Nm - 1) / 2;
+  SPF_CHECK_ARG(Nm >= 1 && Nm % 2 == 1 && 2 * Nm - 1 <= n, "fft: vector side %d does not embed in %d", Nm, n);
+  int r_lo[2], r_hi[2], f_lo[2], f_hi[2], k_lo[2], k_hi[2];
+  wrapped_range(n, Mh + 1, r_lo, r_hi);   // rows and planes holding data, and those needed
+  full_range(n, f_lo, f_hi);
+  full_range(H, k_lo, k_hi);
+  SPF_TRY(launch_rows(true, p, Nm, x, add, beta, x_new, work, nullptr, s));
+  SPF_TRY(axis_pass(p, 1, work, nullptr, nullptr, nullptr, -1, r_lo, r_hi, k_lo, k_hi, s, r_lo, r_hi, false, H));
+  SPF_TRY(axis_pass(p, 2, work, nullptr, nullptr, kernel, -1, f_lo, f_hi, k_lo, k_hi, s, r_lo, r_hi, true, H));
+  SPF_TRY(axis_pass(p, 1, work, nullptr, nullptr, nullptr, +1, r_lo, r_hi, k_lo, k_hi, s, nullptr, nullptr, false,
+                    H));
+  return launch_rows(false, p, Nm, nullptr, nullptr, nullptr, nullptr, work, y, s);
 }
 
 }  // namespace spf

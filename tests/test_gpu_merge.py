@@ -121,3 +121,38 @@ def test_toeplitz_and_cg_at_generic_fft_sides():
     xr, hr = merge.cg(lambda v: merge.apply_toeplitz(v, ref_khat, N, lam), ref_rhs + lam * f32(x0), f32(x0), 3)
     assert rel_l2(x, xr) < 1e-4
     plan.close()
+
+
+@pytest.mark.parametrize("N,PT", [(35, 72), (101, 216)])
+def test_real_input_toeplitz_apply_and_cg(N, PT):
+    """Precompiled cube sides: the Toeplitz apply runs as real-input row
+    transforms (two rows per complex line), half-spectrum y and z passes with
+    the kernel product inside the z pass, and the inverse row transforms.
+    Checked against the oracle's complex convolution with the same kernel,
+    then three CG steps against the oracle's CG."""
+    import torch
+    from paper_2109_05339_gb300 import Plan
+    pb = problem("c1")
+    qlab = pb.q_lab.astype(np.float32)
+    rng = np.random.default_rng(N)
+    q = rng.standard_normal((40, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q[q[:, 0] < 0] *= -1
+    quats = q.astype(np.float32)
+    plan = Plan(N, 1.0, 1e-6, max_points=quats.shape[0] * qlab.shape[0])
+    assert plan.PT == PT
+    images = rng.poisson(20.0, (quats.shape[0], qlab.shape[0])).astype(np.float32)
+    rhs, khat = plan.merge_images(to_dev(images), to_dev(quats), to_dev(qlab), b_scale=0.01)
+    plan.status()
+    kh = khat.cpu().numpy().astype(np.float64)
+    lam = 1e-3 * float(images.size)
+    x0 = (rng.standard_normal((N, N, N)) * 0.01).astype(np.float32)
+    y = plan.toeplitz_apply(khat, lam, to_dev(x0)).cpu().numpy()
+    assert rel_l2(y, merge.apply_toeplitz(f32(x0), kh, N, lam)) < 1e-5
+    hist = torch.zeros(4, dtype=torch.float64, device="cuda")
+    x = plan.cg_solve(khat, lam, rhs, to_dev(x0), 3, res_hist=hist).cpu().numpy()
+    b = f32(rhs.cpu().numpy()) + lam * f32(x0)
+    xr, hr = merge.cg(lambda v: merge.apply_toeplitz(v, kh, N, lam), b, f32(x0), 3)
+    assert rel_l2(x, xr) < 1e-4
+    np.testing.assert_allclose(hist.cpu().numpy(), hr, rtol=1e-4)
+    plan.close()
