@@ -1,10 +1,15 @@
 // Toeplitz normal operator and conjugate gradient (Sec. II-C, Eq. 2).
 //
 // H x = crop(IFFT(K^ * FFT(pad x))) / P_T^3 + lambda x, with K^ the FFT of
-// the circulant embedding of the "type-1 with ones" kernel. The FFT of the
-// zero-padded vector skips the lines that stay zero, the multiply by K^ is
-// fused into the last forward pass, and the inverse skips lines that cannot
-// reach the cropped N^3 output. Inner products and residual norms are
+// the circulant embedding of the "type-1 with ones" kernel (real and even).
+// On the precompiled cube sides the convolution is real-input: the rows of
+// x are transformed in pairs along x to half spectra, the y and z passes run
+// on the half spectrum with the product by K^ inside the z pass (forward,
+// multiply, inverse in one launch), and paired rows come back real. Other
+// sides transform the padded cube as complex data with the product fused
+// into the x pass. Either way lines that stay zero are skipped on the way in
+// and lines that cannot reach the cropped N^3 output on the way out. Inner
+// products and residual norms are
 // accumulated in FP64 (per-block partials reduced in a fixed order, so the
 // result is deterministic); alpha and beta are computed on the device and
 // never read by the host.
@@ -272,7 +277,7 @@ int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x
                    double* part, cudaStream_t s) {
   const int N = P->N, PT = P->PT;
   int64_t PT3 = (int64_t)PT * PT * PT;
-  if (fft3_real_conv_supported(&P->fftP)) {
+  if (fft3_real_supported(&P->fftP)) {
     const int64_t n3 = (int64_t)N * N * N;
     SPF_TRY(fft3_convolve_real(&P->fftP, N, x, nullptr, nullptr, nullptr, khat, P->cubeP, P->realP, s));
     return launch("apply_kernel", s, [&] {
@@ -302,7 +307,7 @@ int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res
   // after cg_begin); both inner products are finalised inside their kernels
   const int N = P->N, PT = P->PT;
   const int64_t n3 = (int64_t)N * N * N, PT3 = (int64_t)PT * PT * PT;
-  if (fft3_real_conv_supported(&P->fftP)) {
+  if (fft3_real_supported(&P->fftP)) {
     // real-input transforms; the direction update rides on the first pass
     SPF_TRY(fft3_convolve_real(&P->fftP, N, P->cg_p, P->cg_r, P->cg_sc + 3, P->cg_p, khat, P->cubeP, P->cg_Ap, s));
     SPF_TRY(launch("apply_kernel", s, [&] {

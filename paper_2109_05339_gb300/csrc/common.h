@@ -128,8 +128,13 @@ int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_hal
 // cube in the full layout and must be real and even). With `add` given the
 // transformed vector is add + (*beta) x, also stored to x_new. work holds
 // side^2 (side / 2 + 1) complex values. Only for the cube sides that
-// fft3_real_conv_supported accepts.
-bool fft3_real_conv_supported(const FFT3* p);
+// fft3_real_supported accepts.
+bool fft3_real_supported(const FFT3* p);
+// Modes |k| < h (every axis) of the transform (sign `sign`) of the real cube
+// `in` (side^3): out[side][side][h] holds the columns kx = 0 .. h-1 at
+// wrapped ky, kz (only ky in the wrapped range of half width h are final);
+// kx < 0 follows from F(-k) = conj F(k). Sides as fft3_real_supported.
+int fft3_r2c_modes(const FFT3* p, const float* in, int h, int sign, float2* out, cudaStream_t s);
 int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, const double* beta,
                        float* x_new, const float* kernel, float2* work, float* y, cudaStream_t s);
 

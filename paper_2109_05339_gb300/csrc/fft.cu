@@ -600,6 +600,52 @@ __global__ void __launch_bounds__(kThreads) c2r_rows_ct(const float2* __restrict
   }
 }
 
+// Forward transform (sign `sign`) of the rows of a real N^3 cube in pairs
+// (2m, 2m + 1) of plane c (line li = c N/2 + m), keeping the half-spectrum
+// columns k < h (row stride h) in out[N][N][h].
+template <int N>
+__global__ void __launch_bounds__(kThreads) r2c_cube_ct(const float* __restrict__ in,
+                                                         const float2* __restrict__ tw, float sign, int h,
+                                                         float2* __restrict__ out) {
+  constexpr int L = rc_lines<N>(), HP = N / 2;
+  extern __shared__ float2 sbuf[];
+  const int first = blockIdx.x * L;
+  const int nlines = min(L, N * HP - first);
+  float2* stw = sbuf + L * N;
+  stage_twiddles(stw, tw, N);
+  for (int e = threadIdx.x; e < L * N; e += kThreads) {
+    const int l = e / N, i = e - l * N;
+    float2 v = make_float2(0.f, 0.f);
+    if (l < nlines) {
+      const int li = first + l, c = li / HP, m = li - c * HP;
+      const int64_t r0 = ((int64_t)c * N + 2 * m) * N + i;
+      v = make_float2(__ldg(in + r0), __ldg(in + r0 + N));
+    }
+    sbuf[e] = v;
+  }
+  __syncthreads();
+  passes_ct<N, L, 1>(sbuf, nlines, stw, sign, typename RadixPlan<N>::type{});
+  for (int e = threadIdx.x; e < L * h; e += kThreads) {
+    const int l = e / h, k = e - l * h;
+    if (l >= nlines) continue;
+    const int li = first + l, c = li / HP, m = li - c * HP;
+    const float2 ck = sbuf[l * N + k], cm = sbuf[l * N + (k == 0 ? 0 : N - k)];
+    const int64_t r0 = ((int64_t)c * N + 2 * m) * h + k;
+    out[r0] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
+    out[r0 + h] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
+  }
+}
+
+template <int N>
+int launch_r2c_cube_ct(const FFT3* p, const float* in, int sign, int h, float2* out, cudaStream_t s) {
+  constexpr int L = rc_lines<N>();
+  const unsigned grid = (unsigned)ceil_div((int64_t)N * (N / 2), L);
+  const size_t smem = (size_t)(L + 1) * N * sizeof(float2);
+  const float2* tw = p->ax[0].twiddle;
+  return launch("fft_r2c_cube_kernel", s,
+                [&] { r2c_cube_ct<N><<<grid, kThreads, smem, s>>>(in, tw, (float)sign, h, out); });
+}
+
 template <int N>
 int launch_rows_ct(bool forward, const FFT3* p, int Nm, const float* x, const float* add,
                    const double* beta, float* x_new, float2* work, float* y, cudaStream_t s) {
@@ -846,7 +892,38 @@ static int launch_rows(bool forward, const FFT3* p, int Nm, const float* x, cons
   return SPF_ERR_UNSUPPORTED;
 }
 
-bool fft3_real_conv_supported(const FFT3* p) {
+// Modes |k| < h of the transform of a real cube: real-input row transforms
+// along x keeping columns kx < h, then y and z passes on those columns (z
+// only on the lines whose y frequency is in the wrapped range of half
+// width h). out[nf][nf][h]; kx < 0 follows from F(-k) = conj F(k).
+int fft3_r2c_modes(const FFT3* p, const float* in, int h, int sign, float2* out, cudaStream_t s) {
+  SPF_CHECK_ARG(fft3_real_supported(p), "fft: side %d has no real-input transform", p->n0);
+  const int n = p->n0;
+  SPF_CHECK_ARG(h >= 1 && 2 * h - 1 <= n, "fft: %d modes do not fit side %d", 2 * h - 1, n);
+  int f_lo[2], f_hi[2], k_lo[2], k_hi[2], r_lo[2], r_hi[2];
+  full_range(n, f_lo, f_hi);
+  full_range(h, k_lo, k_hi);
+  wrapped_range(n, h, r_lo, r_hi);
+  int rc;
+  switch (n) {
+    case 36: rc = launch_r2c_cube_ct<36>(p, in, sign, h, out, s); break;
+    case 72: rc = launch_r2c_cube_ct<72>(p, in, sign, h, out, s); break;
+    case 162: rc = launch_r2c_cube_ct<162>(p, in, sign, h, out, s); break;
+    case 216: rc = launch_r2c_cube_ct<216>(p, in, sign, h, out, s); break;
+    case 320: rc = launch_r2c_cube_ct<320>(p, in, sign, h, out, s); break;
+    case 324: rc = launch_r2c_cube_ct<324>(p, in, sign, h, out, s); break;
+    case 432: rc = launch_r2c_cube_ct<432>(p, in, sign, h, out, s); break;
+    case 640: rc = launch_r2c_cube_ct<640>(p, in, sign, h, out, s); break;
+    default: rc = SPF_ERR_UNSUPPORTED; break;
+  }
+  SPF_TRY(rc);
+  SPF_TRY(axis_pass(p, 1, out, nullptr, nullptr, nullptr, sign, f_lo, f_hi, k_lo, k_hi, s, nullptr, nullptr, false,
+                    h));
+  return axis_pass(p, 2, out, nullptr, nullptr, nullptr, sign, r_lo, r_hi, k_lo, k_hi, s, nullptr, nullptr, false,
+                   h);
+}
+
+bool fft3_real_supported(const FFT3* p) {
   const int n = p->n0;
   return p->n1 == n && p->n2 == n &&
          (n == 36 || n == 72 || n == 162 || n == 216 || n == 320 || n == 324 || n == 432 || n == 640);
@@ -857,7 +934,7 @@ bool fft3_real_conv_supported(const FFT3* p) {
 // (the z pass forward, times the kernel, and back in one launch).
 int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, const double* beta,
                        float* x_new, const float* kernel, float2* work, float* y, cudaStream_t s) {
-  SPF_CHECK_ARG(fft3_real_conv_supported(p), "fft: side %d has no real-input convolution", p->n0);
+  SPF_CHECK_ARG(fft3_real_supported(p), "fft: side %d has no real-input convolution", p->n0);
   const int n = p->n0, H = n / 2 + 1, Mh = (Nm - 1) / 2;
   SPF_CHECK_ARG(Nm >= 1 && Nm % 2 == 1 && 2 * Nm - 1 <= n, "fft: vector side %d does not embed in %d", Nm, n);
   int r_lo[2], r_hi[2], f_lo[2], f_hi[2], k_lo[2], k_hi[2];

@@ -1121,7 +1121,20 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
 }
 
 // out[k] (+)= Re(cube[k mod nf]) p_kx p_ky p_kz for the n_modes^3 modes.
-__global__ void crop_deconv_kernel(const float2* __restrict__ cube, int nf, int n_modes,
+// Re F at the signed mode (kx, ky, kz): from the full cube (hx = 0) or from
+// the half spectrum of a real input (columns kx = 0 .. hx-1; F(-k) =
+// conj F(k) supplies kx < 0).
+__device__ __forceinline__ float mode_re(const float2* __restrict__ F, int nf, int hx, int kx, int ky, int kz) {
+  if (hx == 0) return F[((size_t)wrap_index(kz, nf) * nf + wrap_index(ky, nf)) * nf + wrap_index(kx, nf)].x;
+  if (kx < 0) {
+    kx = -kx;
+    ky = -ky;
+    kz = -kz;
+  }
+  return F[((size_t)wrap_index(kz, nf) * nf + wrap_index(ky, nf)) * hx + kx].x;
+}
+
+__global__ void crop_deconv_kernel(const float2* __restrict__ cube, int nf, int hx, int n_modes,
                                    const float* __restrict__ p, float* __restrict__ out,
                                    int accumulate) {
   int64_t total = (int64_t)n_modes * n_modes * n_modes;
@@ -1129,23 +1142,21 @@ __global__ void crop_deconv_kernel(const float2* __restrict__ cube, int nf, int 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     int x = (int)(i % n_modes), y = (int)((i / n_modes) % n_modes), z = (int)(i / ((int64_t)n_modes * n_modes));
-    int gx = wrap_index(x - Mh, nf), gy = wrap_index(y - Mh, nf), gz = wrap_index(z - Mh, nf);
-    float v = cube[((size_t)gz * nf + gy) * nf + gx].x * p[x] * p[y] * p[z];
+    float v = mode_re(cube, nf, hx, x - Mh, y - Mh, z - Mh) * p[x] * p[y] * p[z];
     out[i] = accumulate ? out[i] + v : v;
   }
 }
 
 // Toeplitz kernel: K(d) = Re(cube[d mod nfT]) p_dx p_dy p_dz embedded at
 // d mod PT of a zeroed complex PT^3 cube.
-__global__ void crop_embed_kernel(const float2* __restrict__ cube, int nf, int n_modes,
+__global__ void crop_embed_kernel(const float2* __restrict__ cube, int nf, int hx, int n_modes,
                                   const float* __restrict__ p, int PT, float2* __restrict__ emb) {
   int64_t total = (int64_t)n_modes * n_modes * n_modes;
   int Mh = (n_modes - 1) / 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     int x = (int)(i % n_modes), y = (int)((i / n_modes) % n_modes), z = (int)(i / ((int64_t)n_modes * n_modes));
-    int gx = wrap_index(x - Mh, nf), gy = wrap_index(y - Mh, nf), gz = wrap_index(z - Mh, nf);
-    float v = cube[((size_t)gz * nf + gy) * nf + gx].x * p[x] * p[y] * p[z];
+    float v = mode_re(cube, nf, hx, x - Mh, y - Mh, z - Mh) * p[x] * p[y] * p[z];
     int ex = wrap_index(x - Mh, PT), ey = wrap_index(y - Mh, PT), ez = wrap_index(z - Mh, PT);
     emb[((size_t)ez * PT + ey) * PT + ex] = make_float2(v, 0.f);
   }
@@ -1338,12 +1349,23 @@ int type1_explicit(spf_plan* P, const float* v, const float* t, int64_t npts, fl
 }
 
 // FFT of the spread grid g.real, then real part and deconvolution into out.
+// Transform of the real spread grid, modes |k| < h only: real-input (half
+// spectrum, hx = h columns) on the precompiled sides, else complex.
+static int type1_modes(Grid& g, int h, int* hx, cudaStream_t s) {
+  if (fft3_real_supported(&g.fft)) {
+    *hx = h;
+    return fft3_r2c_modes(&g.fft, g.real, h, +1, g.cube, s);
+  }
+  *hx = 0;
+  return fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s);
+}
+
 static int type1_finish(spf_plan* P, Grid& g, float* out, int accumulate, cudaStream_t s) {
-  int h = (g.n_modes + 1) / 2;
-  SPF_TRY(fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s));
+  int h = (g.n_modes + 1) / 2, hx = 0;
+  SPF_TRY(type1_modes(g, h, &hx, s));
   int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
   return launch("crop_deconv_kernel", s, [&] {
-    crop_deconv_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, out, accumulate);
+    crop_deconv_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, hx, g.n_modes, g.deconv, out, accumulate);
   });
 }
 
@@ -1351,13 +1373,13 @@ static int type1_finish(spf_plan* P, Grid& g, float* out, int accumulate, cudaSt
 // embedding, FFT, real part (+)-> kernel_hat.
 static int kernel_finish(spf_plan* P, float* kernel_hat, int accumulate, cudaStream_t s) {
   Grid& g = P->gT;
-  int h = (g.n_modes + 1) / 2;
-  SPF_TRY(fft3_exec_ex(&g.fft, g.cube, g.real, nullptr, nullptr, +1, 0, h, s));
+  int h = (g.n_modes + 1) / 2, hx = 0;
+  SPF_TRY(type1_modes(g, h, &hx, s));
   int64_t PT3 = (int64_t)P->PT * P->PT * P->PT;
   // the embedding fills the (2N-1)^3 wrapped range the pruned FFT reads
   int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
   SPF_TRY(launch("crop_embed_kernel", s, [&] {
-    crop_embed_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, g.n_modes, g.deconv, P->PT, P->cubeP);
+    crop_embed_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, hx, g.n_modes, g.deconv, P->PT, P->cubeP);
   }));
   SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, P->realP, nullptr, -1, P->N, 0, s));
   return launch("accumulate_kernel", s, [&] {
