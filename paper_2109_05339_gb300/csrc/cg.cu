@@ -13,9 +13,11 @@
 // accumulated in FP64 (per-block partials reduced in a fixed order, so the
 // result is deterministic); alpha and beta are computed on the device and
 // never read by the host.
+#include <algorithm>
 #include <cmath>
 
 #include "plan.h"
+#include "reduce.h"
 
 namespace spf {
 
@@ -27,63 +29,6 @@ constexpr int kRedThreads = 256;
 __device__ __forceinline__ int wrapi(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
-}
-
-__device__ double block_sum(double v) {
-  __shared__ double sh[32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (wid == 0) {
-    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-  }
-  __syncthreads();
-  return r;
-}
-
-// CG scalars from the reduced sum s: mode 0 r.r (and beta = 0), mode 1 p.Ap
-// and alpha, mode 2 the new r.r and beta.
-__device__ __forceinline__ void cg_scalars(double s, double* __restrict__ sc, int mode,
-                                           double* __restrict__ res_out) {
-  if (mode == 0) {
-    sc[0] = s;
-    sc[3] = 0.0;
-  } else if (mode == 1) {
-    sc[1] = s;
-    sc[2] = s > 0.0 ? sc[0] / s : 0.0;
-  } else {
-    sc[4] = s;
-    sc[3] = sc[0] > 0.0 ? s / sc[0] : 0.0;
-    sc[0] = s;
-  }
-  sc[5] = sqrt(sc[0]);
-  if (res_out) *res_out = sc[5];
-}
-
-// Store this block's partial; the last block to finish sums all partials (in
-// the fixed order of finalize_kernel: the same result) and updates the CG
-// scalars, so no separate reduction launch is needed.
-__device__ void partial_and_finalize(double s_block, double* __restrict__ part, double* __restrict__ sc,
-                                     int mode, double* __restrict__ res_out, unsigned* __restrict__ count) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = s_block;
-    __threadfence();
-    last = atomicAdd(count, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double v = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(part + i);
-  const double s = block_sum(v);
-  if (threadIdx.x == 0) {
-    cg_scalars(s, sc, mode, res_out);
-    *count = 0u;
-  }
 }
 
 // cube (PT^3 complex) = x at n mod PT (|n| <= Mh), zero elsewhere.
@@ -115,25 +60,6 @@ __global__ void crop_apply_kernel(const float2* __restrict__ cube, int N, int PT
     float v = cube[((size_t)gz * PT + gy) * PT + gx].x * inv_n + lambda * x[i];
     out[i] = v;
     acc += (double)x[i] * (double)v;
-  }
-  double s = block_sum(acc);
-  if (count) partial_and_finalize(s, part, sc, 1, nullptr, count);
-  else if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
-}
-
-// out = raw / PT^3 + lambda x, raw the real convolution output at the model
-// indices (out may be raw itself); partial sums of x . out (finalised in the
-// kernel, mode 1, when `count` is given).
-__global__ void apply_kernel(const float* raw, int64_t n3, float inv_n, float lambda,
-                             const float* __restrict__ x, float* out, double* __restrict__ part,
-                             double* __restrict__ sc, unsigned* count) {
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float xv = x[i];
-    const float v = raw[i] * inv_n + lambda * xv;
-    out[i] = v;
-    acc += (double)xv * (double)v;
   }
   double s = block_sum(acc);
   if (count) partial_and_finalize(s, part, sc, 1, nullptr, count);
@@ -278,12 +204,12 @@ int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x
   const int N = P->N, PT = P->PT;
   int64_t PT3 = (int64_t)PT * PT * PT;
   if (fft3_real_supported(&P->fftP)) {
-    const int64_t n3 = (int64_t)N * N * N;
-    SPF_TRY(fft3_convolve_real(&P->fftP, N, x, nullptr, nullptr, nullptr, khat, P->cubeP, P->realP, s));
-    return launch("apply_kernel", s, [&] {
-      apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->realP, n3, (float)(1.0 / (double)PT3), (float)lambda, x,
-                                                      out, part, nullptr, nullptr);
-    });
+    RealConvEpilogue ep;
+    ep.scale = (float)(1.0 / (double)PT3);
+    ep.lambda = (float)lambda;
+    ep.xin = x;
+    ep.part = part;
+    return fft3_convolve_real(&P->fftP, N, x, nullptr, nullptr, nullptr, khat, P->cubeP, out, ep, s);
   }
   SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for((int64_t)N * N * N), 256, 0, s>>>(x, N, PT, P->cubeP); }));
   SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
@@ -308,12 +234,17 @@ int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res
   const int N = P->N, PT = P->PT;
   const int64_t n3 = (int64_t)N * N * N, PT3 = (int64_t)PT * PT * PT;
   if (fft3_real_supported(&P->fftP)) {
-    // real-input transforms; the direction update rides on the first pass
-    SPF_TRY(fft3_convolve_real(&P->fftP, N, P->cg_p, P->cg_r, P->cg_sc + 3, P->cg_p, khat, P->cubeP, P->cg_Ap, s));
-    SPF_TRY(launch("apply_kernel", s, [&] {
-      apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cg_Ap, n3, (float)(1.0 / (double)PT3), (float)lambda,
-                                                      P->cg_p, P->cg_Ap, P->cg_part, P->cg_sc, P->cg_count);
-    }));
+    // real-input transforms: the direction update rides on the first pass,
+    // Ap = Hp + lambda p and p.Ap (finalised: alpha) on the last
+    RealConvEpilogue ep;
+    ep.scale = (float)(1.0 / (double)PT3);
+    ep.lambda = (float)lambda;
+    ep.xin = P->cg_p;
+    ep.part = P->cg_part;
+    ep.sc = P->cg_sc;
+    ep.count = P->cg_count;
+    SPF_TRY(fft3_convolve_real(&P->fftP, N, P->cg_p, P->cg_r, P->cg_sc + 3, P->cg_p, khat, P->cubeP, P->cg_Ap, ep,
+                               s));
   } else {
     SPF_TRY(launch("pad_kernel", s, [&] { pad_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, N, PT, P->cubeP); }));
     SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
@@ -334,7 +265,9 @@ int cg_alloc(spf_plan* P) {
   SPF_TRY(dev_alloc((void**)&P->cg_p, sizeof(float) * n3, "cg p"));
   SPF_TRY(dev_alloc((void**)&P->cg_Ap, sizeof(float) * n3, "cg Ap"));
   SPF_TRY(dev_alloc((void**)&P->cg_sc, sizeof(double) * 8, "cg scalars"));
-  SPF_TRY(dev_alloc((void**)&P->cg_part, sizeof(double) * kRedBlocks, "cg partials"));
+  // partials of the reduction kernels and of the convolution's last launch
+  const int nparts = std::max(kRedBlocks, fft3_real_conv_blocks(&P->fftP, P->N));
+  SPF_TRY(dev_alloc((void**)&P->cg_part, sizeof(double) * nparts, "cg partials"));
   SPF_TRY(dev_alloc((void**)&P->cg_count, sizeof(unsigned), "cg reduction counter"));
   SPF_CUDA(cudaMemset(P->cg_sc, 0, sizeof(double) * 8));
   SPF_CUDA(cudaMemset(P->cg_count, 0, sizeof(unsigned)));

@@ -123,19 +123,33 @@ int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_hal
                   int needed_halfwidth_out, cudaStream_t s);
 // Real-input circular convolution: the real vector x (Nm^3, Nm odd,
 // 2 Nm - 1 <= side) embedded at wrapped positions of the cube (model index a
-// -> (a - (Nm - 1) / 2) mod side), y = IFFT(kernel * FFT(embed x)) read back
-// at the same positions (no 1/n^3 factor; forward sign -1; kernel is a real
-// cube in the full layout and must be real and even). With `add` given the
-// transformed vector is add + (*beta) x, also stored to x_new. work holds
-// side^2 (side / 2 + 1) complex values. Only for the cube sides that
-// fft3_real_supported accepts.
+// -> (a - (Nm - 1) / 2) mod side), IFFT(kernel * FFT(embed x)) read back at
+// the same positions (forward sign -1, no 1/n^3 factor) and passed through
+// the epilogue ep into y. kernel is a real cube in the full layout and must
+// be real and even. With `add` given the transformed vector is
+// add + (*beta) x, also stored to x_new. work holds side^2 (side / 2 + 1)
+// complex values. Only for the cube sides that fft3_real_supported accepts.
 bool fft3_real_supported(const FFT3* p);
+// Last step of fft3_convolve_real: y = scale * conv + lambda * xin at the
+// model indices; with `part`, FP64 per-block partial sums of xin . y (xin
+// required; part holds fft3_real_conv_blocks entries), and with `count` too
+// the last block adds them in block order and updates the CG scalars sc
+// (p.Ap and alpha).
+struct RealConvEpilogue {
+  float scale = 1.f, lambda = 0.f;
+  const float* xin = nullptr;
+  double* part = nullptr;
+  double* sc = nullptr;
+  unsigned* count = nullptr;
+};
+int fft3_real_conv_blocks(const FFT3* p, int Nm);
 // Modes |k| < h (every axis) of the transform (sign `sign`) of the real cube
 // `in` (side^3): out[side][side][h] holds the columns kx = 0 .. h-1 at
 // wrapped ky, kz (only ky in the wrapped range of half width h are final);
 // kx < 0 follows from F(-k) = conj F(k). Sides as fft3_real_supported.
 int fft3_r2c_modes(const FFT3* p, const float* in, int h, int sign, float2* out, cudaStream_t s);
 int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, const double* beta,
-                       float* x_new, const float* kernel, float2* work, float* y, cudaStream_t s);
+                       float* x_new, const float* kernel, float2* work, float* y, const RealConvEpilogue& ep,
+                       cudaStream_t s);
 
 }  // namespace spf

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "common.h"
+#include "reduce.h"
 
 namespace spf {
 
@@ -560,11 +561,12 @@ __global__ void __launch_bounds__(kThreads) r2c_rows_ct(const float* x, const fl
 }
 
 // Inverse of the above: row pairs of the half-spectrum cube back to the
-// real rows (no 1/N factor), written at model indices into y (Nm^3).
+// real rows, y = ep.scale * row + ep.lambda * ep.xin at the model indices
+// (Nm^3), with the epilogue's FP64 partial sums of xin . y.
 template <int N>
 __global__ void __launch_bounds__(kThreads) c2r_rows_ct(const float2* __restrict__ in,
-                                                         const float2* __restrict__ tw, int Nm,
-                                                         float* __restrict__ y) {
+                                                         const float2* __restrict__ tw, int Nm, float* y,
+                                                         RealConvEpilogue ep) {
   constexpr int L = rc_lines<N>(), H = N / 2 + 1;
   extern __shared__ float2 sbuf[];
   const int Mh = (Nm - 1) / 2, HP = (Nm + 1) / 2;
@@ -589,14 +591,29 @@ __global__ void __launch_bounds__(kThreads) c2r_rows_ct(const float2* __restrict
   }
   __syncthreads();
   passes_ct<N, L, 1>(sbuf, nlines, stw, 1.f, typename RadixPlan<N>::type{});
+  double acc = 0.0;
+  auto put = [&](int64_t r, float v) {
+    float o = v * ep.scale;
+    if (ep.xin) {
+      const float xv = ep.xin[r];
+      o = fmaf(ep.lambda, xv, o);
+      acc += (double)xv * (double)o;
+    }
+    y[r] = o;
+  };
   for (int e = threadIdx.x; e < L * Nm; e += kThreads) {
     const int l = e / Nm, a = e - l * Nm;
     if (l >= nlines) continue;
     const int li = first + l, c = li / HP, m = li - c * HP;
     const float2 v = sbuf[l * N + wrap_pos(a, N, Mh)];
     const int64_t r0 = ((int64_t)c * Nm + 2 * m) * Nm + a;
-    y[r0] = v.x;
-    if (2 * m + 1 < Nm) y[r0 + Nm] = v.y;
+    put(r0, v.x);
+    if (2 * m + 1 < Nm) put(r0 + Nm, v.y);
+  }
+  if (ep.part) {
+    const double sblk = block_sum(acc);
+    if (ep.count) partial_and_finalize(sblk, ep.part, ep.sc, 1, nullptr, ep.count);
+    else if (threadIdx.x == 0) ep.part[blockIdx.x] = sblk;
   }
 }
 
@@ -647,17 +664,23 @@ int launch_r2c_cube_ct(const FFT3* p, const float* in, int sign, int h, float2* 
 }
 
 template <int N>
+unsigned rows_grid(int Nm) {
+  return (unsigned)ceil_div((int64_t)Nm * ((Nm + 1) / 2), rc_lines<N>());
+}
+
+template <int N>
 int launch_rows_ct(bool forward, const FFT3* p, int Nm, const float* x, const float* add,
-                   const double* beta, float* x_new, float2* work, float* y, cudaStream_t s) {
+                   const double* beta, float* x_new, float2* work, float* y, const RealConvEpilogue& ep,
+                   cudaStream_t s) {
   constexpr int L = rc_lines<N>();
-  const unsigned grid = (unsigned)ceil_div((int64_t)Nm * ((Nm + 1) / 2), L);
+  const unsigned grid = rows_grid<N>(Nm);
   const size_t smem = (size_t)(L + 1) * N * sizeof(float2);   // lines and the twiddle table
   const float2* tw = p->ax[0].twiddle;
   if (forward)
     return launch("fft_r2c_rows_kernel", s,
                   [&] { r2c_rows_ct<N><<<grid, kThreads, smem, s>>>(x, add, beta, x_new, tw, Nm, work); });
   return launch("fft_c2r_rows_kernel", s,
-                [&] { c2r_rows_ct<N><<<grid, kThreads, smem, s>>>(work, tw, Nm, y); });
+                [&] { c2r_rows_ct<N><<<grid, kThreads, smem, s>>>(work, tw, Nm, y, ep); });
 }
 
 template <int N>
@@ -875,21 +898,30 @@ int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_hw_
   return axis_pass(p, 2, data, nullptr, nullptr, nullptr, +1, oy_lo, oy_hi, ox_lo, ox_hi, s);
 }
 
-static int launch_rows(bool forward, const FFT3* p, int Nm, const float* x, const float* add,
-                       const double* beta, float* x_new, float2* work, float* y, cudaStream_t s) {
-  switch (p->n0) {
-    case 36: return launch_rows_ct<36>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    case 72: return launch_rows_ct<72>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    case 162: return launch_rows_ct<162>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    case 216: return launch_rows_ct<216>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    case 320: return launch_rows_ct<320>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    case 324: return launch_rows_ct<324>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    case 432: return launch_rows_ct<432>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    case 640: return launch_rows_ct<640>(forward, p, Nm, x, add, beta, x_new, work, y, s);
-    default: break;
+#define SPF_SIDE_SWITCH(n, expr)       \
+  switch (n) {                         \
+    case 36: { constexpr int S = 36; expr; }   \
+    case 72: { constexpr int S = 72; expr; }   \
+    case 162: { constexpr int S = 162; expr; } \
+    case 216: { constexpr int S = 216; expr; } \
+    case 320: { constexpr int S = 320; expr; } \
+    case 324: { constexpr int S = 324; expr; } \
+    case 432: { constexpr int S = 432; expr; } \
+    case 640: { constexpr int S = 640; expr; } \
+    default: break;                    \
   }
+
+static int launch_rows(bool forward, const FFT3* p, int Nm, const float* x, const float* add,
+                       const double* beta, float* x_new, float2* work, float* y, const RealConvEpilogue& ep,
+                       cudaStream_t s) {
+  SPF_SIDE_SWITCH(p->n0, return launch_rows_ct<S>(forward, p, Nm, x, add, beta, x_new, work, y, ep, s));
   set_error("fft: no real-input row transform for side %d", p->n0);
   return SPF_ERR_UNSUPPORTED;
+}
+
+int fft3_real_conv_blocks(const FFT3* p, int Nm) {
+  SPF_SIDE_SWITCH(p->n0, return (int)rows_grid<S>(Nm));
+  return 0;
 }
 
 // Modes |k| < h of the transform of a real cube: real-input row transforms
@@ -933,7 +965,8 @@ bool fft3_real_supported(const FFT3* p) {
 // input row transforms along x, then y and z passes on the half spectrum
 // (the z pass forward, times the kernel, and back in one launch).
 int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, const double* beta,
-                       float* x_new, const float* kernel, float2* work, float* y, cudaStream_t s) {
+                       float* x_new, const float* kernel, float2* work, float* y, const RealConvEpilogue& ep,
+                       cudaStream_t s) {
   SPF_CHECK_ARG(fft3_real_supported(p), "fft: side %d has no real-input convolution", p->n0);
   const int n = p->n0, H = n / 2 + 1, Mh = (Nm - 1) / 2;
   SPF_CHECK_ARG(Nm >= 1 && Nm % 2 == 1 && 2 * Nm - 1 <= n, "fft: vector side %d does not embed in %d", Nm, n);
@@ -941,12 +974,13 @@ int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, 
   wrapped_range(n, Mh + 1, r_lo, r_hi);   // rows and planes holding data, and those needed
   full_range(n, f_lo, f_hi);
   full_range(H, k_lo, k_hi);
-  SPF_TRY(launch_rows(true, p, Nm, x, add, beta, x_new, work, nullptr, s));
+  SPF_CHECK_ARG(!ep.part || ep.xin, "fft: epilogue partial sums need xin");
+  SPF_TRY(launch_rows(true, p, Nm, x, add, beta, x_new, work, nullptr, ep, s));
   SPF_TRY(axis_pass(p, 1, work, nullptr, nullptr, nullptr, -1, r_lo, r_hi, k_lo, k_hi, s, r_lo, r_hi, false, H));
   SPF_TRY(axis_pass(p, 2, work, nullptr, nullptr, kernel, -1, f_lo, f_hi, k_lo, k_hi, s, r_lo, r_hi, true, H));
   SPF_TRY(axis_pass(p, 1, work, nullptr, nullptr, nullptr, +1, r_lo, r_hi, k_lo, k_hi, s, nullptr, nullptr, false,
                     H));
-  return launch_rows(false, p, Nm, nullptr, nullptr, nullptr, nullptr, work, y, s);
+  return launch_rows(false, p, Nm, nullptr, nullptr, nullptr, nullptr, work, y, ep, s);
 }
 
 }  // namespace spf
