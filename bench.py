@@ -410,13 +410,18 @@ def run_e2e(args, drv, pb, images, img_scale, dev, M, Ni, world):
     (best orientation per image, merged model) inside the timed region. The
     model and images of step i + 1 are copied on a second stream while step i
     computes (two device buffers); every step's copies stay inside the timed
-    region."""
+    region. Integral images (photon counts) travel as 16-bit counts and the
+    driver converts them to FP32 on the device inside the step."""
     import torch
     cfg = pb.cfg
     h_A = torch.from_numpy(pb.A.astype(np.float32)).pin_memory()
     h_q = torch.from_numpy(pb.quats.astype(np.float32)).pin_memory()
     h_l = torch.from_numpy(pb.q_lab.astype(np.float32)).pin_memory()
-    h_img = images.cpu().pin_memory()
+    # photon-count frames travel as 16-bit counts (the driver converts them on
+    # the device inside the step); non-integral images would travel as FP32
+    as_counts = bool(torch.equal(images, images.round())) and float(images.min()) >= 0.0 \
+        and float(images.max()) <= 65535.0
+    h_img = (images.to(torch.int32).to(torch.int16) if as_counts else images).cpu().pin_memory()
     d_q, d_l = torch.empty_like(h_q, device=dev), torch.empty_like(h_l, device=dev)
     d_A = [torch.empty_like(h_A, device=dev) for _ in range(2)]
     d_img = [torch.empty_like(h_img, device=dev) for _ in range(2)]
@@ -463,7 +468,9 @@ def run_e2e(args, drv, pb, images, img_scale, dev, M, Ni, world):
     ms = e0.elapsed_time(e1) / args.steps
     return {"value": Ni * M * world / (ms / 1e3), "unit": "matches/s", "ms_per_step": ms,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "note": "inputs of step i+1 copied on a second stream while step i computes"}
+            "note": "inputs of step i+1 copied on a second stream while step i computes; images "
+                    + ("as 16-bit photon counts, converted to FP32 on the device in the step" if as_counts
+                       else "as FP32")}
 
 
 # -------------------------------------------------------- oracle (CPU) ---

@@ -249,6 +249,18 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
                            float* best_d, float* second_d, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Photon-count images (no counterpart in the paper's equations; its images
+ * are photon counts). Moving frames as 16-bit counts halves the
+ * host-to-device bytes of FP32 images; the FP32 copy the other calls take is
+ * made on the device.
+ * spf_counts_to_f32: out[i] = (float)counts[i] for 0 <= i < n. counts: n
+ *   unsigned 16-bit values, 2-byte aligned; out: n floats; both device
+ *   pointers, not overlapping, caller-owned. Asynchronous on `stream`.
+ *   SPF_ERR_ARG for n < 0 or a NULL pointer with n > 0.
+ * ------------------------------------------------------------------------- */
+int spf_counts_to_f32(const uint16_t* counts, int64_t n, float* out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Matching without device allocation. The paper has no counterpart: this is
  * for callers that cannot call cudaMalloc when they match -- code running
  * while its stream is being captured into a CUDA graph, code inside a host

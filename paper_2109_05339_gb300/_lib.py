@@ -66,6 +66,7 @@ PROTOTYPES = {
     "spf_matcher_results": (I, [P, P, P, P, P, P, P]),
     "spf_match_orientations": (I, [P, P, I, F, P, I, P, P, P, P]),
     "spf_match_orientations_static": (I, [P, I, F, P, I, I, P, P, P, P]),
+    "spf_counts_to_f32": (I, [P, I64, P, P]),
     "spf_profile_enable": (I, [I]),
     "spf_profile_select": (I, [C.c_char_p]),
     "spf_profile_read": (I, [I, C.c_char_p, I, C.POINTER(C.c_longlong), C.POINTER(D)]),

@@ -12,7 +12,8 @@ import torch
 
 from ._lib import SPF_BF16, SPF_FP8, SPF_FP32, SpfError, check, lib
 
-__all__ = ["Plan", "PointSet", "Matcher", "SliceModel", "slice_model", "SpfError", "PRECISIONS"]
+__all__ = ["Plan", "PointSet", "Matcher", "SliceModel", "slice_model", "counts_to_f32", "SpfError",
+           "PRECISIONS"]
 
 PRECISIONS = {"fp32": SPF_FP32, "bf16": SPF_BF16, "fp8": SPF_FP8}
 
@@ -392,3 +393,22 @@ class SliceModel(torch.autograd.Function):
 
 def slice_model(A, quats, q_lab, plan: Plan):
     return SliceModel.apply(A, quats, q_lab, plan)
+
+
+COUNT_DTYPES = (torch.int16, torch.uint16) if hasattr(torch, "uint16") else (torch.int16,)
+
+
+def counts_to_f32(counts, out=None):
+    """FP32 copy of 16-bit photon-count images on their device. An int16
+    tensor is read as the unsigned 16-bit pattern (0 .. 65535), so counts
+    above 32767 survive a round trip through int16."""
+    if not isinstance(counts, torch.Tensor) or counts.dtype not in COUNT_DTYPES:
+        raise TypeError("counts must be an int16 or uint16 torch.Tensor")
+    if counts.device.type != "cuda" or not counts.is_contiguous():
+        raise ValueError("counts must be a contiguous CUDA tensor")
+    d = counts.device.index
+    if out is None:
+        out = torch.empty(counts.shape, dtype=torch.float32, device=counts.device)
+    _f32(out, "out", d, counts.shape)
+    check(lib.spf_counts_to_f32(_ptr(counts), counts.numel(), _ptr(out), _stream(d)))
+    return out

@@ -547,6 +547,14 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
   return spf_matcher_results(m, best_idx, best_d, second_d, nullptr, nullptr, stream);
 }
 
+int spf_counts_to_f32(const uint16_t* counts, int64_t n, float* out, void* stream) {
+  clear_error();
+  SPF_CHECK_ARG(n >= 0, "n must be >= 0 (got %lld)", (long long)n);
+  SPF_CHECK_ARG(n == 0 || (counts && out), "counts and out must be non-NULL");
+  SPF_CHECK_ARG(((uintptr_t)counts & 1) == 0, "counts must be 2-byte aligned");
+  return counts_to_f32(counts, n, out, as_stream(stream));
+}
+
 // ------------------------------------------------------------ point sets --
 static void points_free(spf_points* S) {
   if (!S) return;

@@ -454,10 +454,22 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
   }
   __syncthreads();
   float2* stw = sbuf + T * N;
+  float* skern = reinterpret_cast<float*>(sbuf + (T + 1) * N);   // convolution: the kernel's lines
   stage_twiddles(stw, A.tw, N);
   for (int e = threadIdx.x; e < T * N; e += kThreads) {
     const int l = e % T, i = e / T;
     if (l < nlines) stage_elem(A, sbuf + l * N + i, i, lbase[l] + (int64_t)i * A.es);
+  }
+  if (A.convolve) {
+    // the kernel's values are copied alongside the data, ahead of the passes
+    for (int e = threadIdx.x; e < T * N; e += kThreads) {
+      const int l = e % T, i = e / T;
+      if (l < nlines)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(
+                         skern + l * N + i)),
+                     "l"(A.post_mul + pbase[l] + (int64_t)i * A.pm_es)
+                     : "memory");
+    }
   }
   cp_async_wait();
   __syncthreads();
@@ -467,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
     for (int e = threadIdx.x; e < T * N; e += kThreads) {
       const int l = e % T, i = e / T;
       if (l < nlines) {
-        const float f = __ldg(A.post_mul + pbase[l] + (int64_t)i * A.pm_es);
+        const float f = skern[l * N + i];
         const float2 v = sbuf[l * N + i];
         sbuf[l * N + i] = make_float2(v.x * f, v.y * f);
       }
@@ -497,6 +509,7 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
 // two half spectra and takes u = Re c, w = Im c.
 template <int N>
 __host__ __device__ constexpr int rc_lines() { return (kMaxElems / N) < 8 ? (kMaxElems / N) : 8; }
+constexpr int RC_GROUP = 4;   // elements per thread whose loads are issued together
 
 // Model index held at line position i of the wrapped embedding, or -1.
 __device__ __forceinline__ int model_index(int i, int N, int Nm, int Mh) {
@@ -523,27 +536,51 @@ __global__ void __launch_bounds__(kThreads) r2c_rows_ct(const float* x, const fl
   float2* stw = sbuf + L * N;
   stage_twiddles(stw, tw, N);
   const float bt = add ? (float)__ldg(beta) : 0.f;
-  for (int e = threadIdx.x; e < L * N; e += kThreads) {
-    const int l = e / N, i = e - l * N;
-    const int a = model_index(i, N, Nm, Mh);
-    float2 v = make_float2(0.f, 0.f);
-    if (l < nlines && a >= 0) {
-      const int li = first + l, c = li / HP, m = li - c * HP;
-      const int64_t r0 = ((int64_t)c * Nm + 2 * m) * Nm + a;
-      float u = x[r0], w = 0.f;
-      const bool second = 2 * m + 1 < Nm;
-      if (second) w = x[r0 + Nm];
-      if (add) {
-        u = fmaf(bt, u, __ldg(add + r0));
-        x_new[r0] = u;
-        if (second) {
-          w = fmaf(bt, w, __ldg(add + r0 + Nm));
-          x_new[r0 + Nm] = w;
+  // groups of RC_GROUP elements per thread: every load of a group is issued
+  // before the first is used (x_new may alias x: each element is loaded and
+  // stored by one thread, loads first)
+  constexpr int IT = (L * N + kThreads - 1) / kThreads;
+#pragma unroll
+  for (int k0 = 0; k0 < IT; k0 += RC_GROUP) {
+    float u[RC_GROUP], w[RC_GROUP], au[RC_GROUP], aw[RC_GROUP];
+    int64_t r0[RC_GROUP];
+    bool has[RC_GROUP], second[RC_GROUP];
+#pragma unroll
+    for (int k = 0; k < RC_GROUP; ++k) {
+      const int e = threadIdx.x + (k0 + k) * kThreads;
+      const int l = e / N, i = e - l * N;
+      const int a = model_index(i, N, Nm, Mh);
+      u[k] = w[k] = au[k] = aw[k] = 0.f;
+      r0[k] = 0;
+      has[k] = k0 + k < IT && e < L * N && l < nlines && a >= 0;
+      second[k] = false;
+      if (has[k]) {
+        const int li = first + l, c = li / HP, m = li - c * HP;
+        r0[k] = ((int64_t)c * Nm + 2 * m) * Nm + a;
+        second[k] = 2 * m + 1 < Nm;
+        u[k] = x[r0[k]];
+        if (second[k]) w[k] = x[r0[k] + Nm];
+        if (add) {
+          au[k] = __ldg(add + r0[k]);
+          if (second[k]) aw[k] = __ldg(add + r0[k] + Nm);
         }
       }
-      v = make_float2(u, w);
     }
-    sbuf[e] = v;
+#pragma unroll
+    for (int k = 0; k < RC_GROUP; ++k) {
+      const int e = threadIdx.x + (k0 + k) * kThreads;
+      if (k0 + k >= IT || e >= L * N) continue;
+      float uu = u[k], ww = w[k];
+      if (has[k] && add) {
+        uu = fmaf(bt, uu, au[k]);
+        x_new[r0[k]] = uu;
+        if (second[k]) {
+          ww = fmaf(bt, ww, aw[k]);
+          x_new[r0[k] + Nm] = ww;
+        }
+      }
+      sbuf[e] = make_float2(uu, ww);
+    }
   }
   __syncthreads();
   passes_ct<N, L, 1>(sbuf, nlines, stw, -1.f, typename RadixPlan<N>::type{});
@@ -574,41 +611,80 @@ __global__ void __launch_bounds__(kThreads) c2r_rows_ct(const float2* __restrict
   const int nlines = min(L, Nm * HP - first);
   float2* stw = sbuf + L * N;
   stage_twiddles(stw, tw, N);
-  for (int e = threadIdx.x; e < L * N; e += kThreads) {
-    const int l = e / N, k = e - l * N;
-    float2 v = make_float2(0.f, 0.f);
-    if (l < nlines) {
-      const int li = first + l, c = li / HP, m = li - c * HP;
-      const int64_t plane = (int64_t)wrap_pos(c, N, Mh) * N;
-      const int kk = k < H ? k : N - k;
-      const float2 u = __ldg(in + (plane + wrap_pos(2 * m, N, Mh)) * H + kk);
-      const float2 w = 2 * m + 1 < Nm ? __ldg(in + (plane + wrap_pos(2 * m + 1, N, Mh)) * H + kk)
-                                      : make_float2(0.f, 0.f);
-      // C[k] = U[k] + i W[k]; past N/2, U[k] = conj U[N - k] (and W alike)
-      v = k < H ? make_float2(u.x - w.y, u.y + w.x) : make_float2(u.x + w.y, w.x - u.y);
+  // the half-spectrum loads of a group of elements go out together
+  constexpr int IT = (L * N + kThreads - 1) / kThreads;
+#pragma unroll
+  for (int k0 = 0; k0 < IT; k0 += RC_GROUP) {
+    float2 u[RC_GROUP], w[RC_GROUP];
+#pragma unroll
+    for (int q = 0; q < RC_GROUP; ++q) {
+      const int e = threadIdx.x + (k0 + q) * kThreads;
+      const int l = e / N, k = e - l * N;
+      u[q] = w[q] = make_float2(0.f, 0.f);
+      if (k0 + q < IT && e < L * N && l < nlines) {
+        const int li = first + l, c = li / HP, m = li - c * HP;
+        const int64_t plane = (int64_t)wrap_pos(c, N, Mh) * N;
+        const int kk = k < H ? k : N - k;
+        u[q] = __ldg(in + (plane + wrap_pos(2 * m, N, Mh)) * H + kk);
+        if (2 * m + 1 < Nm) w[q] = __ldg(in + (plane + wrap_pos(2 * m + 1, N, Mh)) * H + kk);
+      }
     }
-    sbuf[e] = v;
+#pragma unroll
+    for (int q = 0; q < RC_GROUP; ++q) {
+      const int e = threadIdx.x + (k0 + q) * kThreads;
+      if (k0 + q >= IT || e >= L * N) continue;
+      const int k = e % N;
+      // C[k] = U[k] + i W[k]; past N/2, U[k] = conj U[N - k] (and W alike)
+      sbuf[e] = k < H ? make_float2(u[q].x - w[q].y, u[q].y + w[q].x)
+                      : make_float2(u[q].x + w[q].y, w[q].x - u[q].y);
+    }
   }
   __syncthreads();
   passes_ct<N, L, 1>(sbuf, nlines, stw, 1.f, typename RadixPlan<N>::type{});
   double acc = 0.0;
-  auto put = [&](int64_t r, float v) {
-    float o = v * ep.scale;
-    if (ep.xin) {
-      const float xv = ep.xin[r];
-      o = fmaf(ep.lambda, xv, o);
-      acc += (double)xv * (double)o;
+  // epilogue over the Nm <= N/2 + 1 model positions of each line; y may
+  // alias xin (one thread loads, then stores, each element)
+  constexpr int OT = (L * (N / 2 + 1) + kThreads - 1) / kThreads;
+#pragma unroll
+  for (int k0 = 0; k0 < OT; k0 += RC_GROUP) {
+    float v[RC_GROUP][2], xv[RC_GROUP][2];
+    int64_t r0[RC_GROUP];
+    bool has[RC_GROUP], second[RC_GROUP];
+#pragma unroll
+    for (int q = 0; q < RC_GROUP; ++q) {
+      const int e = threadIdx.x + (k0 + q) * kThreads;
+      const int l = e / Nm, a = e - l * Nm;
+      has[q] = k0 + q < OT && e < L * Nm && l < nlines;
+      second[q] = false;
+      r0[q] = 0;
+      v[q][0] = v[q][1] = xv[q][0] = xv[q][1] = 0.f;
+      if (has[q]) {
+        const int li = first + l, c = li / HP, m = li - c * HP;
+        const float2 t = sbuf[l * N + wrap_pos(a, N, Mh)];
+        v[q][0] = t.x;
+        v[q][1] = t.y;
+        r0[q] = ((int64_t)c * Nm + 2 * m) * Nm + a;
+        second[q] = 2 * m + 1 < Nm;
+        if (ep.xin) {
+          xv[q][0] = ep.xin[r0[q]];
+          if (second[q]) xv[q][1] = ep.xin[r0[q] + Nm];
+        }
+      }
     }
-    y[r] = o;
-  };
-  for (int e = threadIdx.x; e < L * Nm; e += kThreads) {
-    const int l = e / Nm, a = e - l * Nm;
-    if (l >= nlines) continue;
-    const int li = first + l, c = li / HP, m = li - c * HP;
-    const float2 v = sbuf[l * N + wrap_pos(a, N, Mh)];
-    const int64_t r0 = ((int64_t)c * Nm + 2 * m) * Nm + a;
-    put(r0, v.x);
-    if (2 * m + 1 < Nm) put(r0 + Nm, v.y);
+#pragma unroll
+    for (int q = 0; q < RC_GROUP; ++q) {
+      if (!has[q]) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !second[q]) continue;
+        float o = v[q][h] * ep.scale;
+        if (ep.xin) {
+          o = fmaf(ep.lambda, xv[q][h], o);
+          acc += (double)xv[q][h] * (double)o;
+        }
+        y[r0[q] + h * Nm] = o;
+      }
+    }
   }
   if (ep.part) {
     const double sblk = block_sum(acc);
@@ -693,7 +769,10 @@ int launch_ct(PassArgs& A, bool contiguous, int na, int nb, cudaStream_t s) {
   }
   constexpr int T = ct_tile<N>();
   const int64_t grid = ceil_div(nb, T) * (int64_t)na;
-  const size_t smem = (size_t)(T + 1) * N * sizeof(float2);   // lines and the twiddle table
+  // lines and the twiddle table, and for a convolution the kernel's lines
+  const size_t smem = (size_t)(T + 1) * N * sizeof(float2) + (A.convolve ? (size_t)T * N * sizeof(float) : 0);
+  if (smem > 48 * 1024)
+    SPF_CUDA(cudaFuncSetAttribute(fft_strided_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return launch("fft_strided_kernel", s,
                 [&] { fft_strided_ct<N><<<(unsigned)grid, kThreads, smem, s>>>(A); });
 }

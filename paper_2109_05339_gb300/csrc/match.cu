@@ -549,3 +549,41 @@ int set_mask_weights(spf_matcher* m, const float* D, cudaStream_t s) {
   return SPF_OK;
 }
 }  // namespace spf
+
+namespace spf {
+namespace {
+
+// out[i] = counts[i] (16-bit photon counts to FP32), 8 per thread: one 16-byte
+// load and two 16-byte stores (both buffers 16-byte aligned), then the tail.
+__global__ void counts_to_f32_vec_kernel(const uint16_t* __restrict__ c, int64_t n, float* __restrict__ out) {
+  const int64_t n8 = n / 8;
+  const uint4* c8 = reinterpret_cast<const uint4*>(c);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n8; i += stride) {
+    const uint4 v = __ldg(c8 + i);
+    o4[2 * i] = make_float4((float)(v.x & 0xffffu), (float)(v.x >> 16), (float)(v.y & 0xffffu), (float)(v.y >> 16));
+    o4[2 * i + 1] =
+        make_float4((float)(v.z & 0xffffu), (float)(v.z >> 16), (float)(v.w & 0xffffu), (float)(v.w >> 16));
+  }
+  for (int64_t i = n8 * 8 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = (float)__ldg(c + i);
+}
+
+__global__ void counts_to_f32_kernel(const uint16_t* __restrict__ c, int64_t n, float* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)__ldg(c + i);
+}
+
+}  // namespace
+
+int counts_to_f32(const uint16_t* counts, int64_t n, float* out, cudaStream_t s) {
+  if (n == 0) return SPF_OK;
+  const bool vec = (((uintptr_t)counts | (uintptr_t)out) & 15) == 0;
+  const int64_t work = vec ? ceil_div(n, 8) : n;
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 152 * 16);
+  if (vec)
+    return launch("counts_to_f32_kernel", s, [&] { counts_to_f32_vec_kernel<<<grid, 256, 0, s>>>(counts, n, out); });
+  return launch("counts_to_f32_kernel", s, [&] { counts_to_f32_kernel<<<grid, 256, 0, s>>>(counts, n, out); });
+}
+}  // namespace spf

@@ -39,5 +39,7 @@ struct spf_matcher {
 namespace spf {
 int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit, cudaStream_t s);
 int match_tc_supported(int device);
+// out[i] = (float)counts[i], i < n (device buffers).
+int counts_to_f32(const uint16_t* counts, int64_t n, float* out, cudaStream_t s);
 void tc_geometry(int n_img, int n_orient, int n_sms, int* grid, int* nsplit);
 }  // namespace spf

@@ -31,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .api import Matcher, Plan, PointSet
+from .api import COUNT_DTYPES, Matcher, Plan, PointSet, counts_to_f32
 
 
 def morton_order(quats_host):
@@ -87,6 +87,7 @@ class MTIP:
         self._okey = None
         self.order = None   # sorted index -> caller's orientation index (int64, device)
         self.quats_sorted = None
+        self._img32 = None   # FP32 images converted from 16-bit counts
 
     def _order_orientations(self, quats):
         """Renumber the orientation set along the Morton curve (once per set)."""
@@ -169,9 +170,20 @@ class MTIP:
                                    orient_idx=best_sorted[i0:i1].contiguous())
         return self.rhs, self.khat
 
+    def _images_f32(self, images):
+        """The images as FP32: 16-bit photon counts are converted on the
+        device into a buffer kept by the driver."""
+        if images.dtype not in COUNT_DTYPES:
+            return images
+        if self._img32 is None or self._img32.shape != images.shape or self._img32.device != images.device:
+            self._img32 = torch.empty(images.shape, dtype=torch.float32, device=images.device)
+        return counts_to_f32(images, out=self._img32)
+
     def iteration(self, A, quats, q_lab, images, img_scale, cg_iters, lam_rel=1e-3, D=None,
                   d_sum=None, res_hist=None):
-        """Returns (match results, merged model x, lambda); d_sum = sum of D over one image."""
+        """Returns (match results, merged model x, lambda); d_sum = sum of D over one image.
+        images: FP32, or 16-bit photon counts (int16 read as unsigned, or uint16)."""
+        images = self._images_f32(images)
         res = self.match(A, quats, q_lab, images, img_scale)
         self.merge(images, quats, res["best_sorted"], q_lab, img_scale, D)
         per_img = float(self.P2) if D is None else float(d_sum)

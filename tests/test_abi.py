@@ -54,6 +54,9 @@ def test_argument_errors_without_gpu(lib):
     assert L.spf_matcher_create(C.byref(m), 10, 10, 16, 7, 8, 0) == lib.SPF_ERR_ARG  # precision
     assert L.spf_matcher_create(C.byref(m), 10, 10, 16, 0, 9, 0) == lib.SPF_ERR_ARG  # topk
     assert L.spf_matcher_add_slices(None, None, 1, 0, None) == lib.SPF_ERR_ARG
+    assert L.spf_counts_to_f32(None, 8, None, None) == lib.SPF_ERR_ARG      # NULL buffers
+    assert L.spf_counts_to_f32(None, -1, None, None) == lib.SPF_ERR_ARG     # negative size
+    assert L.spf_counts_to_f32(C.c_void_p(1), 1, C.c_void_p(16), None) == lib.SPF_ERR_ARG  # odd address
     assert L.spf_version() == 1
     # destroying NULL handles is a no-op
     assert L.spf_plan_destroy(None) == 0 and L.spf_matcher_destroy(None) == 0
