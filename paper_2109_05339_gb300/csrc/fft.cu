@@ -10,6 +10,14 @@
 // built table, and written back in natural order. Three launches make a 3D
 // transform. Lines known to be all zero (zero-padded input) or whose output
 // is not needed (cropped output) are skipped.
+//
+// Real data (the spread grids of type 1, the Toeplitz convolution of the
+// real CG vectors) start with a real-input pass along x on the precompiled
+// sides: two real rows form one complex line, the two half spectra are
+// separated after the line FFT, and the y and z passes then run on the
+// half spectrum only (the Toeplitz product with its real, even kernel
+// inside the z pass). The convolution ends with the matching inverse row
+// pass, which applies the CG operator's epilogue.
 #include <cmath>
 #include <vector>
 
