@@ -200,7 +200,8 @@ def run_ours(args, rank, world):
     qlab = torch.from_numpy(pb.q_lab.astype(np.float32)).to(dev)
     iq = torch.from_numpy(pb.img_quats.astype(np.float32)).to(dev)
     drv = MTIP(cfg.N, cfg.qmax, P2, Ni, M, orient_chunk=args.orient_chunk, img_chunk=args.img_chunk,
-               eps=cfg.eps, precision=args.precision, device=dev)
+               eps=cfg.eps, precision=args.precision, device=dev,
+               process_group=torch.distributed.group.WORLD if world > 1 else None)
     # noise-free slices at the image orientations, chunk by chunk
     gen = torch.Generator(device=dev)
     gen.manual_seed(cfg.seed * 1000 + rank)

@@ -32,6 +32,7 @@ import numpy as np
 import torch
 
 from .api import COUNT_DTYPES, Matcher, Plan, PointSet, counts_to_f32
+from .dist import allreduce_sum_, global_count
 
 
 def morton_order(quats_host):
@@ -52,10 +53,14 @@ POINT_SET_BYTES = 16   # per (orientation, pixel): two sort orders, inverse orde
 class MTIP:
     def __init__(self, N, qmax, P2, n_img, n_orient, orient_chunk=None, img_chunk=None,
                  eps=1e-6, precision="bf16", topk=8, device=None, cache_points=None,
-                 point_budget_bytes=None):
+                 point_budget_bytes=None, process_group=None):
         """cache_points: keep every chunk's sorted points across iterations
         (True), stream them (False), or decide from point_budget_bytes (None;
-        default budget: half of the device's free memory at construction)."""
+        default budget: half of the device's free memory at construction).
+        process_group: the images are one shard of a torch.distributed group;
+        the merge's sums and the image count are added over its ranks."""
+        self.group = process_group
+        self._n_total = {}   # local image count -> count over the group
         self.orient_chunk = min(n_orient, orient_chunk or n_orient)
         if device is None:
             dev = torch.device("cuda", torch.cuda.current_device())
@@ -186,8 +191,14 @@ class MTIP:
         images = self._images_f32(images)
         res = self.match(A, quats, q_lab, images, img_scale)
         self.merge(images, quats, res["best_sorted"], q_lab, img_scale, D)
+        n_img = images.shape[0]
+        if self.group is not None:
+            allreduce_sum_([self.rhs, self.khat], self.group)
+            if n_img not in self._n_total:
+                self._n_total[n_img] = global_count(n_img, images.device, self.group)
+            n_img = self._n_total[n_img]
         per_img = float(self.P2) if D is None else float(d_sum)
-        lam = lam_rel * per_img * images.shape[0]
+        lam = lam_rel * per_img * n_img
         x = self.plan.cg_solve(self.khat, lam, self.rhs, A, cg_iters, x=self.x, res_hist=res_hist)
         return res, x, lam
 

@@ -46,3 +46,34 @@ def test_iteration_matches_oracle(c1, cache, chunk):
     if np.all(res["best"].cpu().numpy() == m["best"]):
         assert rel_l2(x.cpu().numpy(), ref["x"]) < 1e-5
     drv.close()
+
+
+def test_iteration_with_a_process_group_equals_without(c1):
+    """The image-sharded driver path on one rank (gloo group of size 1): the
+    merge's sums go through the group reduction and lambda through the
+    global count; the result equals the driver without a group."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    from paper_2109_05339_gb300 import MTIP
+    pb, counts, s, ref = c1
+    N, P2, M, n = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0], counts.shape[0]
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    dist.init_process_group("gloo", rank=0, world_size=1, init_method=f"tcp://127.0.0.1:{port}")
+    try:
+        out = []
+        for group in (None, dist.group.WORLD):
+            drv = MTIP(N, 1.0, P2, n, M, cache_points=True, process_group=group)
+            res, x, lam = drv.iteration(to_dev(pb.A.astype(np.float32)), to_dev(pb.quats.astype(np.float32)),
+                                        to_dev(pb.q_lab.astype(np.float32)), to_dev(counts.astype(np.float32)),
+                                        1.0 / s, cg_iters=3)
+            torch.cuda.synchronize()
+            out.append((res["best"].cpu().numpy(), x.cpu().numpy().copy(), lam))
+            drv.close()
+    finally:
+        dist.destroy_process_group()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][2] == out[1][2]
+    assert rel_l2(out[1][1], out[0][1]) < 1e-6
