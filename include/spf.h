@@ -25,7 +25,8 @@
  *     gives a message for the last failure on the calling thread.
  *   - A plan or matcher is used by one stream at a time and is not thread
  *     safe; after any error it stays usable.
- *   - No call allocates device memory except the *_create functions.
+ *   - No call allocates device memory except the *_create functions and
+ *     spf_mtip_set_orientations (which creates point sets).
  */
 #ifndef SPF_H
 #define SPF_H
@@ -148,6 +149,33 @@ int spf_merge_points(spf_plan* plan, spf_points* pts, const float* images, const
                      float* kernel_hat, int accumulate, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Deferred merge over many chunks (Sec. II-C). The type-1 sums are linear,
+ * so the chunks' spread fine grids add up before any transform: the
+ * right-hand side and the Toeplitz kernel are transformed once, however many
+ * orientation or image chunks feed them (the kernel is "computed just once").
+ * spf_merge_begin: clears the plan's two fine grids and opens the merge.
+ * spf_merge_points_add: spf_merge_points for one point set, spreading onto
+ *   the open merge instead of producing rhs / kernel_hat; want_rhs and
+ *   want_kernel (0 / 1) select the sums.
+ * spf_merge_images_add: spf_merge_images likewise.
+ * spf_merge_finish: transforms the grids and closes the merge:
+ *   rhs (+)= the right-hand side, kernel_hat (+)= the kernel spectrum, exactly
+ *   as the single-call forms give them for all chunks together; either may
+ *   be NULL (its sum is dropped).
+ * While a merge is open, calls that write the fine grids (slicing, type-1,
+ * the single-call merges) return SPF_ERR_ARG; *_add and finish without an
+ * open merge return SPF_ERR_ARG. Stream-ordered like the other calls.
+ * ------------------------------------------------------------------------- */
+int spf_merge_begin(spf_plan* plan, void* stream);
+int spf_merge_points_add(spf_plan* plan, spf_points* pts, const float* images, const int32_t* orient_idx,
+                         int n_img, int orient_offset, const float* D, float b_scale, int want_rhs,
+                         int want_kernel, void* stream);
+int spf_merge_images_add(spf_plan* plan, const float* images, const float* quats, int n_quats,
+                         const int32_t* orient_idx, int n_img, const float* q_lab, int P2, const float* D,
+                         float b_scale, int want_rhs, int want_kernel, void* stream);
+int spf_merge_finish(spf_plan* plan, float* rhs, float* kernel_hat, int accumulate, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Merge, Sec. II-C (Eq. 2 with the Toeplitz method): from one chunk of
  * oriented images build
  *   rhs[n]        (+)= Re sum_{i,p} D[p] b_scale images[i*P2+p] exp(+i n.t_ip)
@@ -190,9 +218,47 @@ int spf_cg_merge_step(spf_plan* plan, const float* kernel_hat, double lambda, fl
  * between CG solves, not inside one. */
 int spf_cg_objective(spf_plan* plan, const float* kernel_hat, const float* rhs, const float* x,
                      const float* x0, const double* b_norm2, double* out, void* stream);
+/* L-curve corner (host; Sec. II-C): for a sweep of n >= 3 increasing
+ * lambdas with res2[k] = |A x_k - b|_D^2 and reg2[k] = |x_k - x0|^2 (all
+ * positive; host arrays, e.g. copied back from spf_cg_objective), *index is
+ * the interior point of maximum curvature of (log |A x - b|_D, log |x - x0|)
+ * as functions of log lambda (three-point derivatives on the uneven grid);
+ * kappa (host, n - 2 doubles, may be NULL) receives the curvature at the
+ * interior points 1 .. n - 2. */
+int spf_lcurve_corner(const double* lams, const double* res2, const double* reg2, int n, int* index,
+                      double* kappa);
 /* out[0] (+)= sum_{i,p} D[p] (scale images[i*P2+p])^2 in FP64 (D NULL: ones). */
 int spf_weighted_sumsq(spf_plan* plan, const float* images, int n_img, int P2, const float* D,
                        float scale, double* out, int accumulate, void* stream);
+
+/* Gradient-based merge (the differentiation pattern of slicing): with S_i
+ * the slice at image i's orientation (Sec. II-A) and S^T its type-1 adjoint
+ * (Sec. II-C),
+ *   L(x) = 1/2 sum_{i,p} D[p] (S_i x - b_scale images[i*P2+p])^2 + lambda/2 |x - x0|^2,
+ *   grad = S^T D (S x - b_scale images) + lambda (x - x0).
+ * For x even in n, S^T D S = Re(A^H D A): L is the objective of Eq. 2.
+ * Slices are recomputed chunk by chunk (chunk images at a time, chunk * P2 <=
+ * max_points) into `work` (chunk * P2 floats, caller-owned), never stored.
+ * quats: n_img x 4 (image i's orientation), images: n_img x P2, D: P2 or NULL.
+ * spf_slice_loss_grad: *loss (device double) = L(x), grad (N^3) = grad L(x);
+ *   x0 may be NULL when lambda = 0.
+ * spf_slice_normal_apply: out = S^T D S v + lambda v (N^3).
+ * spf_gradient_step: one steepest-descent step with exact line search on the
+ *   quadratic L: *loss = L(x) before the step, grad and Hg (N^3 work, written)
+ *   = g and H g with H = S^T D S + lambda I, then x -= (g.g / g.Hg) g (no step
+ *   when g.Hg <= 0 or g = 0). Inner products FP64, step length on the device.
+ * All three use the plan's fine grids (refused while a deferred merge is
+ * open) and reduction scratch; FP64 loss and inner products. */
+int spf_slice_loss_grad(spf_plan* plan, const float* x, const float* x0, const float* quats, int n_img,
+                        const float* q_lab, int P2, const float* images, float b_scale, const float* D,
+                        double lambda, int chunk, float* work, double* loss, float* grad, void* stream);
+int spf_slice_normal_apply(spf_plan* plan, const float* v, const float* quats, int n_img, const float* q_lab,
+                           int P2, const float* D, double lambda, int chunk, float* work, float* out,
+                           void* stream);
+int spf_gradient_step(spf_plan* plan, float* x, const float* x0, const float* quats, int n_img,
+                      const float* q_lab, int P2, const float* images, float b_scale, const float* D,
+                      double lambda, int chunk, float* work, float* grad, float* Hg, double* loss,
+                      void* stream);
 
 /* H x without the CG state (Toeplitz form): out = crop(IFFT(kernel_hat *
  * FFT(pad x))) + lambda x. Used to check the operator. */
@@ -238,6 +304,13 @@ int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float
 int spf_matcher_set_mask(spf_matcher* m, const float* D, void* stream);
 int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient,
                            int orient_offset, void* stream);
+/* Tile schedule of the tensor-core cross term (BF16 / FP8; host, takes effect
+ * at the next add_slices): 0 (default) lets a model of tensor-core time and
+ * HBM traffic choose, 1 forces contiguous ranges of the image-major tile
+ * order, 2 forces a grid of CTAs over image-tile x orientation-tile ranges
+ * (concurrent CTAs share operand tiles; the model's choice for many image
+ * tiles). The results differ only in which approximate candidates tie. */
+int spf_matcher_set_schedule(spf_matcher* m, int schedule);
 int spf_matcher_results(spf_matcher* m, int32_t* best_idx, float* best_d, float* second_d,
                         int32_t* topk_idx, float* topk_d, void* stream);
 
@@ -247,6 +320,119 @@ int spf_matcher_results(spf_matcher* m, int32_t* best_idx, float* best_d, float*
 int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float img_scale,
                            const float* slices, int n_orient, int32_t* best_idx,
                            float* best_d, float* second_d, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * M-TIP iteration driver (Fig. 3 without phasing; Sec. II-A to II-C): the
+ * slice -> match -> merge -> CG iteration over a fixed orientation set,
+ * orchestrated in the library.
+ *
+ * The orientation set is the run's configuration ("a predetermined set of
+ * orientations", Sec. II-A): spf_mtip_set_orientations takes it once and the
+ * driver renumbers it along a Morton curve of the quaternions (neighbouring
+ * indices are neighbours on SO(3), which keeps candidate model images of
+ * images re-ranked together in L2). Its points are either sorted per
+ * orientation chunk once and kept (about 16 bytes per orientation x pixel),
+ * or, beyond the memory budget, re-sorted per chunk for slicing on every
+ * iteration while the merge spreads image chunks at their matched
+ * orientations. Orientation indices passed in or out are in the caller's
+ * numbering; exact distance ties resolve to the lower index in the driver's.
+ *
+ * An iteration (spf_mtip_iteration): (1) the model A is sliced at every
+ * orientation chunk and every image is matched against each chunk (running
+ * top-k with the FP32 re-rank); (2) the images are merged at their best
+ * orientations -- every chunk spread onto the plan's fine grids, transformed
+ * once into the right-hand side and the Toeplitz kernel; (3) cg_iters CG
+ * steps on Eq. 2 from x0 = A, lambda = lam_rel * (sum of the pixel weights
+ * over all merged images). The three steps are also separate calls, so that
+ * image-sharded processes can add their right-hand sides and kernels between
+ * merge and solve.
+ *
+ * Images are FP32 (SPF_IMAGES_F32) or unsigned 16-bit photon counts
+ * (SPF_IMAGES_U16, converted to FP32 on the device inside the call).
+ *
+ * spf_mtip_config: N, qmax, eps as spf_plan_create; P2 pixels; max_images
+ *   per call; n_orient orientations; orient_chunk orientations sliced and
+ *   matched per chunk (0: all); img_chunk images merged per type-1 pass when
+ *   streaming (0: all); precision and topk as spf_matcher_create;
+ *   cache_points 1 keep the sorted point sets, 0 stream, -1 keep them when
+ *   16 * n_orient * P2 bytes fit point_budget_bytes (<= 0: half of the
+ *   device's free memory at create); host_image_type SPF_IMAGES_F32 /
+ *   SPF_IMAGES_U16 allocates two device input slots for
+ *   spf_mtip_iteration_host, -1 none; device ordinal.
+ * spf_mtip_create allocates the plan, the matcher, a slice chunk, an FP32
+ *   image buffer (max_images x P2), the merge and CG buffers and the host-path
+ *   slots. Synchronous. spf_mtip_set_orientations copies quats (n_orient x 4)
+ *   and q_lab (P2 x 3) and, when keeping point sets, creates and sorts them
+ *   (it allocates: a set-up call); synchronous. spf_mtip_set_mask: pixel
+ *   weights D (P2 floats, device, >= 0, caller-owned and kept until replaced)
+ *   for matching, merging and lambda, or NULL for ones; synchronous.
+ * spf_mtip_match: best (n_img, device) in the caller's numbering; best_d,
+ *   second_d (n_img) and topk_idx, topk_d (n_img x topk) optional (NULL).
+ * spf_mtip_merge: right-hand side (N^3) and kernel spectrum (P_T^3) of the
+ *   images at orientations best (caller's numbering) into rhs, kernel_hat
+ *   (device, caller-owned, overwritten).
+ * spf_mtip_solve: CG from x0 for cg_iters steps into x (N^3), lambda =
+ *   lam_rel * (sum of D over a pixel row) * n_img_total; *lambda_out (host,
+ *   may be NULL) receives it; res_hist (device, cg_iters + 1 doubles, may be
+ *   NULL) the residual norms.
+ * spf_mtip_iteration: the three steps; best (device, may be NULL) and x
+ *   (device) are written.
+ * spf_mtip_iteration_host: the same from and to HOST buffers: A_host (N^3
+ *   floats) and images_host (n_img x P2 of host_image_type) are copied into
+ *   one of two device slots on the driver's own copy stream, which waits until
+ *   the call two back is done with that slot, so that a call's copies overlap
+ *   the previous call's compute; best_host (n_img int32) and x_host (N^3
+ *   floats) are written back on `stream`. Asynchronous for page-locked host
+ *   buffers: the inputs must stay unchanged and the outputs are valid once
+ *   `stream` has completed the call's work (e.g. cudaStreamSynchronize).
+ * spf_mtip_status: the plan's, the matcher's and the driver's error words
+ *   (waits for the device). spf_mtip_plan / spf_mtip_matcher: the driver's
+ *   plan and matcher (owned by the driver) for the other calls of this header.
+ * spf_mtip_info: whether point sets are kept, and the chunk sizes in use.
+ * ------------------------------------------------------------------------- */
+#define SPF_IMAGES_F32 0
+#define SPF_IMAGES_U16 1
+typedef struct spf_mtip spf_mtip;
+typedef struct spf_mtip_config {
+  int N;
+  double qmax;
+  double eps;
+  int P2;
+  int max_images;
+  int n_orient;
+  int orient_chunk;
+  int img_chunk;
+  int precision;
+  int topk;
+  int cache_points;
+  int64_t point_budget_bytes;
+  int host_image_type;
+  int device;
+} spf_mtip_config;
+/* The driver's renumbering of an orientation set (host; no device work):
+ * order_host[i] = the caller's index of driver index i, the permutation that
+ * sorts the Morton codes of the quaternions' (x, y, z), each quantised to 10
+ * bits over [-1, 1] (stable for equal codes). quats_host: M x 4 floats. */
+int spf_morton_order(const float* quats_host, int M, int32_t* order_host);
+int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg);
+int spf_mtip_destroy(spf_mtip* h);
+int spf_mtip_info(const spf_mtip* h, int* cache_points, int* orient_chunk, int* img_chunk);
+spf_plan* spf_mtip_plan(spf_mtip* h);
+spf_matcher* spf_mtip_matcher(spf_mtip* h);
+int spf_mtip_status(spf_mtip* h);
+int spf_mtip_set_orientations(spf_mtip* h, const float* quats, const float* q_lab, void* stream);
+int spf_mtip_set_mask(spf_mtip* h, const float* D, void* stream);
+int spf_mtip_match(spf_mtip* h, const float* A, const void* images, int image_type, int n_img, float img_scale,
+                   int32_t* best, float* best_d, float* second_d, int32_t* topk_idx, float* topk_d, void* stream);
+int spf_mtip_merge(spf_mtip* h, const void* images, int image_type, int n_img, float img_scale, const int32_t* best,
+                   float* rhs, float* kernel_hat, void* stream);
+int spf_mtip_solve(spf_mtip* h, const float* rhs, const float* kernel_hat, const float* x0, double lam_rel,
+                   int64_t n_img_total, int cg_iters, float* x, double* lambda_out, double* res_hist, void* stream);
+int spf_mtip_iteration(spf_mtip* h, const float* A, const void* images, int image_type, int n_img, float img_scale,
+                       int cg_iters, double lam_rel, int32_t* best, float* x, double* lambda_out, void* stream);
+int spf_mtip_iteration_host(spf_mtip* h, const float* A_host, const void* images_host, int image_type, int n_img,
+                            float img_scale, int cg_iters, double lam_rel, int32_t* best_host, float* x_host,
+                            double* lambda_out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Photon-count images (no counterpart in the paper's equations; its images
@@ -262,23 +448,27 @@ int spf_counts_to_f32(const uint16_t* counts, int64_t n, float* out, void* strea
 
 /* ---------------------------------------------------------------------------
  * Matching without device allocation. The paper has no counterpart: this is
- * for callers that cannot call cudaMalloc when they match -- code running
- * while its stream is being captured into a CUDA graph, code inside a host
- * framework that owns the device memory pool, or a real-time loop that must
- * not touch the allocator. It computes what spf_match_orientations computes
- * with precision SPF_FP32 and topk 8 (fused FP32 distance + top-8, exact FP32
- * re-rank), but every intermediate buffer lives in one static device array of
- * 4,526,080 bytes (about 4.5 MB) that each GPU loading this library holds
- * until the process exits.
+ * for callers that cannot call cudaMalloc when they match -- code inside a
+ * host framework that owns the device memory pool and forbids allocations
+ * beside it (its allocator must account for every byte), or a real-time
+ * acquisition loop that must not touch the allocator, whose calls can block
+ * and synchronise the device. It computes what spf_match_orientations
+ * computes with precision SPF_FP32 and topk 8 (fused FP32 distance + top-8,
+ * exact FP32 re-rank), but every intermediate buffer lives in one static
+ * device array of 4,526,080 bytes (about 4.5 MB) that each GPU loading this
+ * library holds until the process exits.
  *   images: n_img x P2, slices: n_orient x P2, outputs: n_img each (device).
  *   n_img <= SPF_STATIC_MATCH_MAX_IMAGES, n_orient <= SPF_STATIC_MATCH_MAX_ORIENT;
  *   larger sizes return SPF_ERR_ARG with a message.
  * The first call on a device, with that device current, looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture. It allocates nothing, then or later. All calls on a device
- * share the one array: calls whose work overlaps on the GPU (different
- * streams, or different host threads) race and give wrong results --
- * serialise them. Runs on the calling thread's current device.
+ * device address (cudaGetSymbolAddress); it is looked up again when the
+ * calling thread's current CUDA context changes (for instance after
+ * cudaDeviceReset). Make that first call before any stream capture. It
+ * allocates nothing, then or later. Every call resets the part of the array
+ * it reads before use. All calls on a device share the one array: calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and give wrong results -- serialise them. Runs on the calling thread's
+ * current device.
  * ------------------------------------------------------------------------- */
 #define SPF_STATIC_MATCH_MAX_IMAGES 1024
 #define SPF_STATIC_MATCH_MAX_ORIENT 65536
@@ -298,11 +488,17 @@ int spf_match_orientations_static(const float* images, int n_img, float img_scal
  *   comma-separated list `names` (NULL or "" selects every kernel); the
  *   other launches are still counted by spf_launch_count. Lets a caller time
  *   one kernel inside a timed region without an event pair on every launch.
+ * spf_profile_bytes: for kernel number `index`, the algorithmic global-memory
+ *   bytes of its traced launches since the last enable (each input element
+ *   read once and each output element written once, as the launch site
+ *   states it; 0 for kernels that state none). The bandwidth-bound kernels
+ *   (FFT passes, padding and cropping, CG vectors) state theirs.
  * spf_launch_count: kernels launched by this library since the process began.
  * ------------------------------------------------------------------------- */
 int spf_profile_enable(int on);
 int spf_profile_select(const char* names);
 int spf_profile_read(int index, char* name, int name_len, long long* launches, double* total_ms);
+int spf_profile_bytes(int index, double* bytes);
 long long spf_launch_count(void);
 
 #ifdef __cplusplus

@@ -100,8 +100,9 @@ class Plan:
         return max(1, (1 << 22) // self.w ** 3)
 
     # -- type 2 ----------------------------------------------------------------
-    def type2(self, f, t):
-        """c_j = sum_n f_n exp(-i n.t_j) (approximately); f (M,M,M), t (npts, 3)."""
+    def fine_grid(self, f):
+        """Steps 1-2 of type 2: the deconvolved, zero-padded modes and their
+        FFT, G_l = sum_k g_k exp(-2 pi i k.l / n_f), flattened (n_f^3,)."""
         nf = self.nf
         f = np.asarray(f)
         assert f.shape == (self.n_modes,) * 3
@@ -109,7 +110,11 @@ class Plan:
         ix = self._mode_index()
         pz, py, px = np.meshgrid(self.p, self.p, self.p, indexing="ij")
         g[np.ix_(ix, ix, ix)] = f * (pz * py * px)
-        G = np.fft.fftn(g).ravel()
+        return np.fft.fftn(g).ravel()
+
+    def interp(self, G, t):
+        """Step 3 of type 2: c_j = sum over the w^3 nearest cells of G_l times
+        the three kernel weights, for points t (npts, 3)."""
         t = np.asarray(t, dtype=np.float64).reshape(-1, 3)
         out = np.empty(t.shape[0], dtype=np.complex128)
         cs = self._chunk()
@@ -117,6 +122,10 @@ class Plan:
             flat, wprod = self._taps(t[s:s + cs])
             out[s:s + cs] = np.sum(G[flat] * wprod, axis=(1, 2, 3))
         return out
+
+    def type2(self, f, t):
+        """c_j = sum_n f_n exp(-i n.t_j) (approximately); f (M,M,M), t (npts, 3)."""
+        return self.interp(self.fine_grid(f), t)
 
     # -- type 1 ----------------------------------------------------------------
     def spread(self, v, t):
@@ -134,14 +143,18 @@ class Plan:
             bim += np.bincount(flat.ravel(), weights=(vv.imag * wprod).ravel(), minlength=nf ** 3)
         return (bre + 1j * bim).reshape(nf, nf, nf)
 
-    def type1(self, v, t):
-        """f_n = sum_j v_j exp(+i n.t_j) (approximately) for the n_modes^3 modes."""
+    def modes_of(self, b):
+        """Last steps of type 1: F_k = sum_l b_l exp(+2 pi i k.l / n_f) of the
+        spread grid b, kept for the n_modes^3 modes and deconvolved."""
         nf = self.nf
-        b = self.spread(v, t)
         F = np.fft.ifftn(b) * float(nf) ** 3          # sum_l b_l exp(+2 pi i k.l / nf)
         ix = self._mode_index()
         pz, py, px = np.meshgrid(self.p, self.p, self.p, indexing="ij")
         return F[np.ix_(ix, ix, ix)] * (pz * py * px)
+
+    def type1(self, v, t):
+        """f_n = sum_j v_j exp(+i n.t_j) (approximately) for the n_modes^3 modes."""
+        return self.modes_of(self.spread(v, t))
 
 
 _PLANS = {}

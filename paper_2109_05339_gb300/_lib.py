@@ -18,6 +18,7 @@ SPF_ERR_CUDA = -3
 SPF_ERR_TIMEOUT = -4
 SPF_ERR_UNSUPPORTED = -5
 SPF_FP32, SPF_BF16, SPF_FP8 = 0, 1, 2
+SPF_IMAGES_F32, SPF_IMAGES_U16 = 0, 1
 
 _CODES = {SPF_ERR_ARG: "SPF_ERR_ARG", SPF_ERR_OOM: "SPF_ERR_OOM", SPF_ERR_CUDA: "SPF_ERR_CUDA",
           SPF_ERR_TIMEOUT: "SPF_ERR_TIMEOUT", SPF_ERR_UNSUPPORTED: "SPF_ERR_UNSUPPORTED"}
@@ -34,6 +35,14 @@ I = C.c_int
 I64 = C.c_int64
 F = C.c_float
 D = C.c_double
+
+class MtipConfig(C.Structure):
+    """spf_mtip_config (include/spf.h)."""
+    _fields_ = [("N", C.c_int), ("qmax", C.c_double), ("eps", C.c_double), ("P2", C.c_int),
+                ("max_images", C.c_int), ("n_orient", C.c_int), ("orient_chunk", C.c_int),
+                ("img_chunk", C.c_int), ("precision", C.c_int), ("topk", C.c_int), ("cache_points", C.c_int),
+                ("point_budget_bytes", C.c_int64), ("host_image_type", C.c_int), ("device", C.c_int)]
+
 
 # name: (restype, argtypes)
 PROTOTYPES = {
@@ -52,24 +61,48 @@ PROTOTYPES = {
     "spf_points_destroy": (I, [P]),
     "spf_slice_points": (I, [P, P, P, P, P]),
     "spf_merge_points": (I, [P, P, P, P, I, I, P, F, P, P, I, P]),
+    "spf_merge_begin": (I, [P, P]),
+    "spf_merge_points_add": (I, [P, P, P, P, I, I, P, F, I, I, P]),
+    "spf_merge_images_add": (I, [P, P, P, I, P, I, P, I, P, F, I, I, P]),
+    "spf_merge_finish": (I, [P, P, P, I, P]),
     "spf_cg_begin": (I, [P, P, D, P, P, P, P, P]),
     "spf_cg_merge_step": (I, [P, P, D, P, P, P]),
     "spf_toeplitz_apply": (I, [P, P, D, P, P, P]),
+    "spf_slice_loss_grad": (I, [P, P, P, P, I, P, I, P, F, P, D, I, P, P, P, P]),
+    "spf_slice_normal_apply": (I, [P, P, P, I, P, I, P, D, I, P, P, P]),
+    "spf_gradient_step": (I, [P, P, P, P, I, P, I, P, F, P, D, I, P, P, P, P, P]),
     "spf_cg_objective": (I, [P, P, P, P, P, P, P, P]),
     "spf_weighted_sumsq": (I, [P, P, I, I, P, F, P, I, P]),
+    "spf_lcurve_corner": (I, [P, P, P, I, C.POINTER(I), P]),
     "spf_matcher_create": (I, [C.POINTER(P), I, I, I, I, I, I]),
     "spf_matcher_destroy": (I, [P]),
     "spf_matcher_status": (I, [P]),
     "spf_matcher_set_images": (I, [P, P, I, F, P]),
     "spf_matcher_set_mask": (I, [P, P, P]),
     "spf_matcher_add_slices": (I, [P, P, I, I, P]),
+    "spf_matcher_set_schedule": (I, [P, I]),
     "spf_matcher_results": (I, [P, P, P, P, P, P, P]),
     "spf_match_orientations": (I, [P, P, I, F, P, I, P, P, P, P]),
     "spf_match_orientations_static": (I, [P, I, F, P, I, I, P, P, P, P]),
     "spf_counts_to_f32": (I, [P, I64, P, P]),
+    "spf_morton_order": (I, [P, I, P]),
+    "spf_mtip_create": (I, [C.POINTER(P), C.POINTER(MtipConfig)]),
+    "spf_mtip_destroy": (I, [P]),
+    "spf_mtip_info": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+    "spf_mtip_plan": (P, [P]),
+    "spf_mtip_matcher": (P, [P]),
+    "spf_mtip_status": (I, [P]),
+    "spf_mtip_set_orientations": (I, [P, P, P, P]),
+    "spf_mtip_set_mask": (I, [P, P, P]),
+    "spf_mtip_match": (I, [P, P, P, I, I, F, P, P, P, P, P, P]),
+    "spf_mtip_merge": (I, [P, P, I, I, F, P, P, P, P]),
+    "spf_mtip_solve": (I, [P, P, P, P, D, I64, I, P, C.POINTER(D), P, P]),
+    "spf_mtip_iteration": (I, [P, P, P, I, I, F, I, D, P, P, C.POINTER(D), P]),
+    "spf_mtip_iteration_host": (I, [P, P, P, I, I, F, I, D, P, P, C.POINTER(D), P]),
     "spf_profile_enable": (I, [I]),
     "spf_profile_select": (I, [C.c_char_p]),
     "spf_profile_read": (I, [I, C.c_char_p, I, C.POINTER(C.c_longlong), C.POINTER(D)]),
+    "spf_profile_bytes": (I, [I, C.POINTER(D)]),
     "spf_launch_count": (C.c_longlong, []),
 }
 
@@ -114,6 +147,20 @@ def profile_read():
     n, ms = C.c_longlong(), C.c_double()
     while lib.spf_profile_read(i, buf, 128, C.byref(n), C.byref(ms)) == SPF_OK:
         out[buf.value.decode()] = (n.value, ms.value)
+        i += 1
+    return out
+
+
+def profile_bytes():
+    """{kernel name: algorithmic bytes of its traced launches} since the last
+    profile_enable() (0 for kernels that state none)."""
+    out = {}
+    i = 0
+    buf = C.create_string_buffer(128)
+    n, ms, b = C.c_longlong(), C.c_double(), C.c_double()
+    while lib.spf_profile_read(i, buf, 128, C.byref(n), C.byref(ms)) == SPF_OK:
+        if lib.spf_profile_bytes(i, C.byref(b)) == SPF_OK:
+            out[buf.value.decode()] = b.value
         i += 1
     return out
 

@@ -62,9 +62,24 @@ class Plan:
         check(lib.spf_plan_sizes(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         self.nf, self.nfT, self.PT, self.w = a.value, b.value, c.value, d.value
 
+    @classmethod
+    def view(cls, handle, N, qmax=1.0, eps=1e-6, device=None):
+        """A non-owning Plan over a plan that another object (the M-TIP
+        driver) created and destroys."""
+        p = cls.__new__(cls)
+        p.device = _dev_index(device)
+        p._h = C.c_void_p(handle)
+        p._owned = False
+        p.N, p.qmax, p.eps, p.max_points = int(N), float(qmax), float(eps), 0
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(lib.spf_plan_sizes(p._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        p.nf, p.nfT, p.PT, p.w = a.value, b.value, c.value, d.value
+        return p
+
     def close(self):
         if getattr(self, "_h", None):
-            lib.spf_plan_destroy(self._h)
+            if getattr(self, "_owned", True):
+                lib.spf_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -175,6 +190,41 @@ class Plan:
                                    int(bool(accumulate)), _stream(d)))
         return rhs, kernel_hat
 
+    # -- deferred merge over many chunks (one transform of the summed grids) ---
+    def merge_begin(self):
+        check(lib.spf_merge_begin(self._h, _stream(self.device)))
+
+    def merge_images_add(self, images, quats, q_lab, D=None, b_scale=1.0, orient_idx=None, want_rhs=True,
+                         want_kernel=True):
+        """Spread one image chunk onto the open merge (see merge_images)."""
+        d = self.device
+        _f32(quats, "quats", d)
+        _f32(q_lab, "q_lab", d)
+        P2 = q_lab.shape[0]
+        if orient_idx is not None:
+            if orient_idx.dtype != torch.int32 or not orient_idx.is_contiguous():
+                raise TypeError("orient_idx must be a contiguous int32 tensor")
+            n_img = orient_idx.shape[0]
+        else:
+            n_img = quats.shape[0]
+        if want_rhs:
+            _f32(images, "images", d, (n_img, P2))
+        if D is not None:
+            _f32(D, "D", d, (P2,))
+        check(lib.spf_merge_images_add(self._h, _ptr(images) if want_rhs else None, _ptr(quats), quats.shape[0],
+                                       _ptr(orient_idx), n_img, _ptr(q_lab), P2, _ptr(D), float(b_scale),
+                                       int(bool(want_rhs)), int(bool(want_kernel)), _stream(d)))
+
+    def merge_finish(self, rhs=None, kernel_hat=None, accumulate=False):
+        """Transform the open merge's sums into rhs (N^3) and kernel_hat (P_T^3)."""
+        d = self.device
+        if rhs is not None:
+            self._grid(rhs, "rhs")
+        if kernel_hat is not None:
+            _f32(kernel_hat, "kernel_hat", d, (self.PT,) * 3)
+        check(lib.spf_merge_finish(self._h, _ptr(rhs), _ptr(kernel_hat), int(bool(accumulate)), _stream(d)))
+        return rhs, kernel_hat
+
     def toeplitz_apply(self, kernel_hat, lam, x, out=None):
         d = self.device
         _f32(kernel_hat, "kernel_hat", d, (self.PT,) * 3)
@@ -256,6 +306,23 @@ class PointSet:
         check(lib.spf_slice_points(p._h, self._h, _ptr(A), _ptr(out), _stream(d)))
         return out
 
+    def merge_add(self, images, orient_idx, orient_offset=0, D=None, b_scale=1.0, want_rhs=True,
+                  want_kernel=True):
+        """Class sums of this set's orientations spread onto the plan's open
+        merge (Plan.merge_begin ... Plan.merge_finish)."""
+        p, d = self.plan, self.plan.device
+        _f32(images, "images", d)
+        if orient_idx.dtype != torch.int32 or not orient_idx.is_contiguous():
+            raise TypeError("orient_idx must be a contiguous int32 tensor")
+        n_img = images.shape[0]
+        if images.dim() != 2 or images.shape[1] != self.P2 or orient_idx.shape[0] != n_img:
+            raise ValueError("images must be (n, P2) with one orient_idx per image")
+        if D is not None:
+            _f32(D, "D", d, (self.P2,))
+        check(lib.spf_merge_points_add(p._h, self._h, _ptr(images), _ptr(orient_idx), n_img, int(orient_offset),
+                                       _ptr(D), float(b_scale), int(bool(want_rhs)), int(bool(want_kernel)),
+                                       _stream(d)))
+
     def merge(self, images, orient_idx, orient_offset=0, D=None, b_scale=1.0, rhs=None, kernel_hat=None,
               accumulate=False, want_rhs=True, want_kernel=True):
         """Sec. II-C right-hand side and Toeplitz kernel from class sums of the
@@ -300,9 +367,24 @@ class Matcher:
         self._images = None
         self.n_img = 0
 
+    @classmethod
+    def view(cls, handle, max_images, max_orient_chunk, P2, precision="bf16", topk=8, device=None):
+        """A non-owning Matcher over a matcher the M-TIP driver owns."""
+        m = cls.__new__(cls)
+        m.device = _dev_index(device)
+        m.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        m._h = C.c_void_p(handle)
+        m._owned = False
+        m.P2, m.topk = int(P2), int(topk)
+        m.max_images, m.max_orient = int(max_images), int(max_orient_chunk)
+        m._images = None
+        m.n_img = 0
+        return m
+
     def close(self):
         if getattr(self, "_h", None):
-            lib.spf_matcher_destroy(self._h)
+            if getattr(self, "_owned", True):
+                lib.spf_matcher_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -320,6 +402,10 @@ class Matcher:
             _f32(D, "D", self.device, (self.P2,))
         self._mask = D
         check(lib.spf_matcher_set_mask(self._h, _ptr(D), _stream(self.device)))
+
+    def set_schedule(self, schedule="auto"):
+        """Tile schedule of the tensor-core cross term: "auto", "contiguous" or "grid"."""
+        check(lib.spf_matcher_set_schedule(self._h, {"auto": 0, "contiguous": 1, "grid": 2}[schedule]))
 
     def set_images(self, images, img_scale=1.0):
         _f32(images, "images", self.device)

@@ -66,14 +66,17 @@ int type1_explicit(spf_plan* P, const float* v, const float* t, int64_t npts, fl
                    int accumulate, int* err, cudaStream_t s);
 int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats,
               const int* oidx, int n_img, const float* qlab, int P2, const float* D, float b_scale,
-              float* rhs, float* kernel_hat, int accumulate, int* err, cudaStream_t s);
+              float* rhs, float* kernel_hat, int accumulate, int* err, cudaStream_t s, int mode,
+              bool want_rhs, bool want_kernel);
+int merge_begin(spf_plan* P, cudaStream_t s);
+int merge_finish(spf_plan* P, float* rhs, float* kernel_hat, int accumulate, cudaStream_t s);
 int grid_init(Grid* g, int n_modes, int nf, double cells_per_q, int w, double beta,
               int64_t max_points, bool interp_source);
 int points_build(spf_plan* P, spf_points* S, cudaStream_t s);
 int slice_points(spf_plan* P, spf_points* S, const float* A, float* out, cudaStream_t s);
 int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oidx, int n_img, int off,
                  const float* D, float b_scale, float* rhs, float* kernel_hat, int accumulate,
-                 cudaStream_t s);
+                 cudaStream_t s, int mode, bool want_rhs, bool want_kernel);
 void grid_free(Grid* g);
 // cg.cu
 int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x, float* out,
@@ -82,6 +85,16 @@ int cg_begin(spf_plan* P, const float* khat, double lambda, const float* rhs, co
              float* x, double* res, cudaStream_t s);
 int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res, cudaStream_t s);
 int cg_alloc(spf_plan* P);
+// grad.cu
+int grad_alloc(spf_plan* P);
+int slice_loss_grad(spf_plan* P, const float* x, const float* x0, const float* quats, int n_img, const float* qlab,
+                    int P2, const float* img, float b_scale, const float* D, double lambda, int chunk, float* work,
+                    double* loss, float* grad, cudaStream_t s);
+int slice_normal_apply(spf_plan* P, const float* v, const float* quats, int n_img, const float* qlab, int P2,
+                       const float* D, double lambda, int chunk, float* work, float* out, cudaStream_t s);
+int gradient_step(spf_plan* P, float* x, const float* x0, const float* quats, int n_img, const float* qlab, int P2,
+                  const float* img, float b_scale, const float* D, double lambda, int chunk, float* work,
+                  float* grad, float* Hg, double* loss, cudaStream_t s);
 int cg_objective(spf_plan* P, const float* khat, const float* rhs, const float* x, const float* x0,
                  const double* b2, double* out, cudaStream_t s);
 int weighted_sumsq(spf_plan* P, const float* img, int64_t n, int P2, const float* D, float scale,
@@ -118,6 +131,9 @@ static void plan_free(spf_plan* P) {
   cudaFree(P->cg_sc);
   cudaFree(P->cg_part);
   cudaFree(P->cg_count);
+  cudaFree(P->grad_part);
+  cudaFree(P->grad_count);
+  cudaFree(P->grad_sc);
   cudaFree(P->err);
   delete P;
 }
@@ -142,6 +158,7 @@ static int plan_init(spf_plan* P) {
   SPF_TRY(dev_alloc((void**)&P->sorted, sizeof(uint32_t) * (size_t)std::max<int64_t>(1, P->max_points),
                     "sorted point ids"));
   SPF_TRY(cg_alloc(P));
+  SPF_TRY(grad_alloc(P));
   SPF_TRY(dev_alloc((void**)&P->err, sizeof(int), "error word"));
   SPF_CUDA(cudaMemset(P->err, 0, sizeof(int)));
   SPF_CUDA(cudaDeviceSynchronize());
@@ -150,6 +167,15 @@ static int plan_init(spf_plan* P) {
 
 static int check_plan(const spf_plan* P) {
   SPF_CHECK_ARG(P != nullptr, "plan is NULL");
+  return SPF_OK;
+}
+
+// Calls that write the plan's fine grids are refused while a deferred merge
+// keeps its partial sums there.
+static int check_grids_free(const spf_plan* P) {
+  SPF_CHECK_ARG(!P->merge_open,
+                "a deferred merge is open on this plan (spf_merge_begin without spf_merge_finish): "
+                "its partial sums occupy the fine grids this call would overwrite");
   return SPF_OK;
 }
 
@@ -227,6 +253,7 @@ int spf_slice_model(spf_plan* plan, const float* A, const float* quats, int M, c
                     int P2, float* slices, void* stream) {
   clear_error();
   SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
   SPF_CHECK_ARG(M >= 0 && P2 > 0, "M >= 0 and P2 > 0 required");
   SPF_CHECK_ARG((int64_t)M * P2 <= 0xffffffffLL, "M*P2 must be < 2^32");
   SPF_CHECK_ARG(A && q_lab && (M == 0 || (quats && slices)), "NULL pointer");
@@ -243,6 +270,7 @@ int spf_slice_adjoint(spf_plan* plan, const float* g, const float* quats, int M,
                       int P2, float* gradA, int accumulate, void* stream) {
   clear_error();
   SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
   SPF_CHECK_ARG(M >= 0 && P2 > 0, "M >= 0 and P2 > 0 required");
   SPF_CHECK_ARG((int64_t)M * P2 <= plan->max_points, "M*P2 = %lld exceeds max_points %lld",
                 (long long)M * P2, (long long)plan->max_points);
@@ -257,6 +285,7 @@ int spf_nufft_type2(spf_plan* plan, const float* A, const float* pts, int64_t np
                     void* stream) {
   clear_error();
   SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
   SPF_CHECK_ARG(npts >= 0 && npts <= 0xffffffffLL, "npts must be in [0, 2^32)");
   SPF_CHECK_ARG(A && (npts == 0 || (pts && out)), "NULL pointer");
   if (npts == 0) return SPF_OK;
@@ -271,6 +300,7 @@ int spf_nufft_type1(spf_plan* plan, const float* v, const float* pts, int64_t np
                     int accumulate, void* stream) {
   clear_error();
   SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
   SPF_CHECK_ARG(npts >= 0 && npts <= plan->max_points, "npts %lld exceeds max_points %lld",
                 (long long)npts, (long long)plan->max_points);
   SPF_CHECK_ARG(out && (npts == 0 || (pts && v)), "NULL pointer");
@@ -285,6 +315,7 @@ int spf_merge_images(spf_plan* plan, const float* images, const float* quats, in
                      void* stream) {
   clear_error();
   SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
   SPF_CHECK_ARG(n_img >= 0 && P2 > 0, "n_img >= 0 and P2 > 0 required");
   SPF_CHECK_ARG((int64_t)n_img * P2 <= plan->max_points, "n_img*P2 = %lld exceeds max_points %lld",
                 (long long)n_img * P2, (long long)plan->max_points);
@@ -296,7 +327,8 @@ int spf_merge_images(spf_plan* plan, const float* images, const float* quats, in
   DeviceScope dev(plan->device);
   if (dev.rc != SPF_OK) return dev.rc;
   return merge_run(plan, images, quats, n_quats, orient_idx, n_img, q_lab, P2, D, b_scale, rhs,
-                   kernel_hat, accumulate, plan->err, as_stream(stream));
+                   kernel_hat, accumulate, plan->err, as_stream(stream), kMergeClear | kMergeFinish,
+                   rhs != nullptr, kernel_hat != nullptr);
 }
 
 int spf_cg_begin(spf_plan* plan, const float* kernel_hat, double lambda, const float* rhs,
@@ -340,6 +372,59 @@ int spf_weighted_sumsq(spf_plan* plan, const float* images, int n_img, int P2, c
   if (dev.rc != SPF_OK) return dev.rc;
   return weighted_sumsq(plan, images, (int64_t)n_img * P2, P2, D, scale, out, accumulate,
                         as_stream(stream));
+}
+
+static int check_grad_args(const spf_plan* P, const float* quats, int n_img, const float* q_lab, int P2,
+                           double lambda, int chunk, const float* work) {
+  SPF_CHECK_ARG(n_img >= 0 && P2 > 0 && chunk >= 1, "n_img >= 0, P2 > 0 and chunk >= 1 required");
+  SPF_CHECK_ARG((int64_t)chunk * P2 <= P->max_points, "chunk*P2 = %lld exceeds max_points %lld",
+                (long long)chunk * P2, (long long)P->max_points);
+  SPF_CHECK_ARG(lambda >= 0.0, "lambda must be >= 0");
+  SPF_CHECK_ARG(q_lab && work && (n_img == 0 || quats), "NULL pointer");
+  SPF_CHECK_ARG(n_img == 0 || aligned16(quats), "quats must be 16-byte aligned");
+  return SPF_OK;
+}
+
+int spf_slice_loss_grad(spf_plan* plan, const float* x, const float* x0, const float* quats, int n_img,
+                        const float* q_lab, int P2, const float* images, float b_scale, const float* D,
+                        double lambda, int chunk, float* work, double* loss, float* grad, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
+  SPF_TRY(check_grad_args(plan, quats, n_img, q_lab, P2, lambda, chunk, work));
+  SPF_CHECK_ARG(x && loss && grad && (n_img == 0 || images) && (lambda == 0.0 || x0), "NULL pointer");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return slice_loss_grad(plan, x, x0, quats, n_img, q_lab, P2, images, b_scale, D, lambda, chunk, work, loss, grad,
+                         as_stream(stream));
+}
+
+int spf_slice_normal_apply(spf_plan* plan, const float* v, const float* quats, int n_img, const float* q_lab,
+                           int P2, const float* D, double lambda, int chunk, float* work, float* out,
+                           void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
+  SPF_TRY(check_grad_args(plan, quats, n_img, q_lab, P2, lambda, chunk, work));
+  SPF_CHECK_ARG(v && out, "NULL pointer");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return slice_normal_apply(plan, v, quats, n_img, q_lab, P2, D, lambda, chunk, work, out, as_stream(stream));
+}
+
+int spf_gradient_step(spf_plan* plan, float* x, const float* x0, const float* quats, int n_img,
+                      const float* q_lab, int P2, const float* images, float b_scale, const float* D,
+                      double lambda, int chunk, float* work, float* grad, float* Hg, double* loss,
+                      void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
+  SPF_TRY(check_grad_args(plan, quats, n_img, q_lab, P2, lambda, chunk, work));
+  SPF_CHECK_ARG(x && grad && Hg && loss && (n_img == 0 || images) && (lambda == 0.0 || x0), "NULL pointer");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return gradient_step(plan, x, x0, quats, n_img, q_lab, P2, images, b_scale, D, lambda, chunk, work, grad, Hg,
+                       loss, as_stream(stream));
 }
 
 int spf_toeplitz_apply(spf_plan* plan, const float* kernel_hat, double lambda, const float* x,
@@ -476,6 +561,14 @@ int spf_matcher_set_mask(spf_matcher* m, const float* D, void* stream) {
   return set_mask_weights(m, D, as_stream(stream));
 }
 
+int spf_matcher_set_schedule(spf_matcher* m, int schedule) {
+  clear_error();
+  SPF_CHECK_ARG(m != nullptr, "matcher is NULL");
+  SPF_CHECK_ARG(schedule >= 0 && schedule <= 2, "schedule must be 0 (model), 1 (contiguous) or 2 (grid)");
+  m->tc_force = schedule;
+  return SPF_OK;
+}
+
 int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float img_scale,
                            void* stream) {
   clear_error();
@@ -523,8 +616,7 @@ int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient, in
     SPF_TRY(simt_launch(m, slices, n_orient, orient_offset, nsplit, s));
   } else {
     SPF_TRY(quantize_rows(m, slices, n_orient, 1.f, m->yq, m->ys, m->y2, s));
-    int grid;
-    tc_geometry(m->n_img, n_orient, m->n_sms, &grid, &nsplit);
+    nsplit = tc_schedule(m->n_img, n_orient, m->n_sms, m->Kpad, m->precision == SPF_FP8, m->tc_force).nsplit;
     SPF_TRY(match_tc_launch(m, n_orient, orient_offset, nsplit, s));
   }
   return rerank_launch(m, slices, n_orient, orient_offset, nsplit, s);
@@ -645,6 +737,7 @@ int spf_points_destroy(spf_points* pts) {
 int spf_slice_points(spf_plan* plan, spf_points* pts, const float* A, float* slices, void* stream) {
   clear_error();
   SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
   SPF_CHECK_ARG(pts && pts->plan == plan, "point set is NULL or belongs to another plan");
   SPF_CHECK_ARG(A && (pts->M == 0 || slices), "NULL pointer");
   DeviceScope dev(plan->device);
@@ -657,6 +750,7 @@ int spf_merge_points(spf_plan* plan, spf_points* pts, const float* images, const
                      float* kernel_hat, int accumulate, void* stream) {
   clear_error();
   SPF_TRY(check_plan(plan));
+  SPF_TRY(check_grids_free(plan));
   SPF_CHECK_ARG(pts && pts->plan == plan, "point set is NULL or belongs to another plan");
   SPF_CHECK_ARG(pts->flags == 0, "the point set was created for slicing only");
   SPF_CHECK_ARG(n_img >= 0 && (n_img == 0 || (images && orient_idx)), "NULL pointer");
@@ -664,7 +758,68 @@ int spf_merge_points(spf_plan* plan, spf_points* pts, const float* images, const
   DeviceScope dev(plan->device);
   if (dev.rc != SPF_OK) return dev.rc;
   return merge_points(plan, pts, images, orient_idx, n_img, orient_offset, D, b_scale, rhs, kernel_hat,
-                      accumulate, as_stream(stream));
+                      accumulate, as_stream(stream), kMergeClear | kMergeFinish, rhs != nullptr,
+                      kernel_hat != nullptr);
+}
+
+int spf_merge_begin(spf_plan* plan, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  SPF_TRY(merge_begin(plan, as_stream(stream)));
+  plan->merge_open = true;
+  return SPF_OK;
+}
+
+static int check_merge_open(const spf_plan* P) {
+  SPF_CHECK_ARG(P->merge_open, "no deferred merge is open on this plan (call spf_merge_begin first)");
+  return SPF_OK;
+}
+
+int spf_merge_points_add(spf_plan* plan, spf_points* pts, const float* images, const int32_t* orient_idx,
+                         int n_img, int orient_offset, const float* D, float b_scale, int want_rhs,
+                         int want_kernel, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_TRY(check_merge_open(plan));
+  SPF_CHECK_ARG(pts && pts->plan == plan, "point set is NULL or belongs to another plan");
+  SPF_CHECK_ARG(pts->flags == 0, "the point set was created for slicing only");
+  SPF_CHECK_ARG(n_img >= 0 && (n_img == 0 || (images && orient_idx)), "NULL pointer");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return merge_points(plan, pts, images, orient_idx, n_img, orient_offset, D, b_scale, nullptr, nullptr, 0,
+                      as_stream(stream), 0, want_rhs != 0, want_kernel != 0);
+}
+
+int spf_merge_images_add(spf_plan* plan, const float* images, const float* quats, int n_quats,
+                         const int32_t* orient_idx, int n_img, const float* q_lab, int P2, const float* D,
+                         float b_scale, int want_rhs, int want_kernel, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_TRY(check_merge_open(plan));
+  SPF_CHECK_ARG(n_img >= 0 && P2 > 0, "n_img >= 0 and P2 > 0 required");
+  SPF_CHECK_ARG((int64_t)n_img * P2 <= plan->max_points, "n_img*P2 = %lld exceeds max_points %lld",
+                (long long)n_img * P2, (long long)plan->max_points);
+  SPF_CHECK_ARG(q_lab != nullptr, "NULL pointer");
+  SPF_CHECK_ARG(n_img == 0 || (quats && aligned16(quats)), "quats must be 16-byte aligned");
+  SPF_CHECK_ARG(n_img == 0 || !want_rhs || images, "images is NULL");
+  SPF_CHECK_ARG(orient_idx ? n_quats > 0 : n_quats >= n_img,
+                "quats must hold n_img rows, or n_quats > 0 rows with orient_idx");
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  return merge_run(plan, images, quats, n_quats, orient_idx, n_img, q_lab, P2, D, b_scale, nullptr, nullptr,
+                   0, plan->err, as_stream(stream), 0, want_rhs != 0, want_kernel != 0);
+}
+
+int spf_merge_finish(spf_plan* plan, float* rhs, float* kernel_hat, int accumulate, void* stream) {
+  clear_error();
+  SPF_TRY(check_plan(plan));
+  SPF_TRY(check_merge_open(plan));
+  DeviceScope dev(plan->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  plan->merge_open = false;
+  return merge_finish(plan, rhs, kernel_hat, accumulate, as_stream(stream));
 }
 
 }  // extern "C"

@@ -211,10 +211,13 @@ int toeplitz_apply(spf_plan* P, const float* khat, double lambda, const float* x
     ep.part = part;
     return fft3_convolve_real(&P->fftP, N, x, nullptr, nullptr, nullptr, khat, P->cubeP, out, ep, s);
   }
-  SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for((int64_t)N * N * N), 256, 0, s>>>(x, N, PT, P->cubeP); }));
+  const double n3 = (double)N * N * N;
+  SPF_TRY(launch("pad_kernel", s, [&] { pad_kernel<<<grid_for((int64_t)N * N * N), 256, 0, s>>>(x, N, PT, P->cubeP); },
+                 12.0 * n3));
   SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
   SPF_TRY(launch("crop_apply_kernel", s, [&] { crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3),
-                                                       (float)lambda, x, out, part, nullptr, nullptr); }));
+                                                       (float)lambda, x, out, part, nullptr, nullptr); },
+                 16.0 * n3));
   return SPF_OK;
 }
 
@@ -223,7 +226,7 @@ int cg_begin(spf_plan* P, const float* khat, double lambda, const float* rhs, co
   int64_t n3 = (int64_t)P->N * P->N * P->N;
   SPF_TRY(toeplitz_apply(P, khat, lambda, x0, P->cg_Ap, nullptr, s));
   SPF_TRY(launch("cg_init_kernel", s, [&] { cg_init_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(rhs, x0, P->cg_Ap, (float)lambda, n3, x,
-                                                    P->cg_r, P->cg_p, P->cg_part); }));
+                                                    P->cg_r, P->cg_p, P->cg_part); }, 24.0 * n3));
   SPF_TRY(launch("finalize_kernel", s, [&] { finalize_kernel<<<1, kRedThreads, 0, s>>>(P->cg_part, kRedBlocks, P->cg_sc, 0, res); }));
   return SPF_OK;
 }
@@ -246,17 +249,18 @@ int cg_step(spf_plan* P, const float* khat, double lambda, float* x, double* res
     SPF_TRY(fft3_convolve_real(&P->fftP, N, P->cg_p, P->cg_r, P->cg_sc + 3, P->cg_p, khat, P->cubeP, P->cg_Ap, ep,
                                s));
   } else {
-    SPF_TRY(launch("pad_kernel", s, [&] { pad_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, N, PT, P->cubeP); }));
+    SPF_TRY(launch("pad_kernel", s, [&] { pad_dir_kernel<<<grid_for(n3), 256, 0, s>>>(P->cg_r, P->cg_p, P->cg_sc, N, PT, P->cubeP); },
+                   20.0 * n3));
     SPF_TRY(fft3_convolve(&P->fftP, P->cubeP, khat, P->Mh + 1, P->Mh + 1, s));
     SPF_TRY(launch("crop_apply_kernel", s, [&] {
       crop_apply_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(P->cubeP, N, PT, (float)(1.0 / (double)PT3), (float)lambda,
                                                            P->cg_p, P->cg_Ap, P->cg_part, P->cg_sc, P->cg_count);
-    }));
+    }, 16.0 * n3));
   }
   return launch("cg_update_kernel", s, [&] {
     cg_update_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, P->cg_r, P->cg_p, P->cg_Ap, P->cg_sc, n3, P->cg_part,
                                                         res, P->cg_count);
-  });
+  }, 24.0 * n3);
 }
 
 int cg_alloc(spf_plan* P) {
@@ -299,3 +303,45 @@ int weighted_sumsq(spf_plan* P, const float* img, int64_t n, int P2, const float
   });
 }
 }  // namespace spf
+
+// ------------------------------------------------------------ L-curve ----
+// Corner of the L-curve (Sec. II-C: the regularisation parameter is chosen on
+// the L-curve): with s = log lambda, rho = log |A x - b|_D and eta =
+// log |x - x0| (half the logs of the squared norms), the curvature of
+// (rho(s), eta(s)) is kappa = (rho' eta'' - rho'' eta') / (rho'^2 + eta'^2)^(3/2),
+// derivatives by three-point finite differences on the uneven grid s, at the
+// interior points. Host arithmetic on the n scalars of a sweep.
+extern "C" int spf_lcurve_corner(const double* lams, const double* res2, const double* reg2, int n, int* index,
+                                 double* kappa) {
+  using namespace spf;
+  clear_error();
+  SPF_CHECK_ARG(n >= 3 && lams && res2 && reg2 && index, "need n >= 3 points and non-NULL arrays");
+  for (int i = 0; i < n; ++i) {
+    SPF_CHECK_ARG(lams[i] > 0.0 && res2[i] > 0.0 && reg2[i] > 0.0, "lambda and both norms must be positive");
+    SPF_CHECK_ARG(i == 0 || lams[i] > lams[i - 1], "lambdas must increase");
+  }
+  int best = -1;
+  double kbest = 0.0;
+  for (int i = 1; i + 1 < n; ++i) {
+    const double s0 = std::log(lams[i - 1]), s1 = std::log(lams[i]), s2 = std::log(lams[i + 1]);
+    const double h0 = s1 - s0, h1 = s2 - s1;
+    auto d1 = [&](double y0, double y1, double y2) {
+      return -h1 / (h0 * (h0 + h1)) * y0 + (h1 - h0) / (h0 * h1) * y1 + h0 / (h1 * (h0 + h1)) * y2;
+    };
+    auto d2 = [&](double y0, double y1, double y2) {
+      return 2.0 * (y0 / (h0 * (h0 + h1)) - y1 / (h0 * h1) + y2 / (h1 * (h0 + h1)));
+    };
+    const double r0 = 0.5 * std::log(res2[i - 1]), r1 = 0.5 * std::log(res2[i]), r2 = 0.5 * std::log(res2[i + 1]);
+    const double e0 = 0.5 * std::log(reg2[i - 1]), e1 = 0.5 * std::log(reg2[i]), e2 = 0.5 * std::log(reg2[i + 1]);
+    const double rp = d1(r0, r1, r2), rpp = d2(r0, r1, r2), ep = d1(e0, e1, e2), epp = d2(e0, e1, e2);
+    const double k = (rp * epp - rpp * ep) / std::pow(rp * rp + ep * ep, 1.5);
+    if (kappa) kappa[i - 1] = k;
+    if (best < 0 || k > kbest) {
+      best = i;
+      kbest = k;
+    }
+  }
+  *index = best;
+  return SPF_OK;
+}
+

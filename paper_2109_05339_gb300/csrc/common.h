@@ -58,15 +58,17 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Launch tracing (profile.cu): every kernel launch goes through launch(),
 // which counts it and, while profiling is on, brackets it with CUDA events
-// on its stream.
+// on its stream and adds `bytes` -- the algorithmic global-memory bytes the
+// launch must move (each input element read once, each output written once;
+// 0 where not stated) -- to the kernel's total.
 extern std::atomic<long long> g_launches;
 bool prof_on();
-int prof_begin(const char* name, cudaStream_t s);
+int prof_begin(const char* name, cudaStream_t s, double bytes);
 void prof_end(int slot, cudaStream_t s);
 
 template <class F>
-inline int launch(const char* name, cudaStream_t s, F&& f) {
-  int slot = prof_on() ? prof_begin(name, s) : -1;
+inline int launch(const char* name, cudaStream_t s, F&& f, double bytes = 0.0) {
+  int slot = prof_on() ? prof_begin(name, s, bytes) : -1;
   f();
   cudaError_t e = cudaGetLastError();
   if (slot >= 0) prof_end(slot, s);

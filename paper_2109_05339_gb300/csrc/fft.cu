@@ -743,8 +743,9 @@ int launch_r2c_cube_ct(const FFT3* p, const float* in, int sign, int h, float2* 
   const unsigned grid = (unsigned)ceil_div((int64_t)N * (N / 2), L);
   const size_t smem = (size_t)(L + 1) * N * sizeof(float2);
   const float2* tw = p->ax[0].twiddle;
+  const double bytes = (double)N * N * N * 4.0 + (double)N * N * h * 8.0;
   return launch("fft_r2c_cube_kernel", s,
-                [&] { r2c_cube_ct<N><<<grid, kThreads, smem, s>>>(in, tw, (float)sign, h, out); });
+                [&] { r2c_cube_ct<N><<<grid, kThreads, smem, s>>>(in, tw, (float)sign, h, out); }, bytes);
 }
 
 template <int N>
@@ -760,20 +761,25 @@ int launch_rows_ct(bool forward, const FFT3* p, int Nm, const float* x, const fl
   const unsigned grid = rows_grid<N>(Nm);
   const size_t smem = (size_t)(L + 1) * N * sizeof(float2);   // lines and the twiddle table
   const float2* tw = p->ax[0].twiddle;
+  // rows of the Nm^3 vector (and of `add`, with x_new written) against the
+  // Nm x Nm half-spectrum rows of H = N/2 + 1 columns that hold data
+  const double vec = (double)Nm * Nm * Nm * 4.0, half = (double)Nm * Nm * (N / 2 + 1) * 8.0;
   if (forward)
     return launch("fft_r2c_rows_kernel", s,
-                  [&] { r2c_rows_ct<N><<<grid, kThreads, smem, s>>>(x, add, beta, x_new, tw, Nm, work); });
+                  [&] { r2c_rows_ct<N><<<grid, kThreads, smem, s>>>(x, add, beta, x_new, tw, Nm, work); },
+                  vec * (add ? 3.0 : 1.0) + half);
   return launch("fft_c2r_rows_kernel", s,
-                [&] { c2r_rows_ct<N><<<grid, kThreads, smem, s>>>(work, tw, Nm, y, ep); });
+                [&] { c2r_rows_ct<N><<<grid, kThreads, smem, s>>>(work, tw, Nm, y, ep); },
+                half + vec * (ep.xin ? 2.0 : 1.0));
 }
 
 template <int N>
-int launch_ct(PassArgs& A, bool contiguous, int na, int nb, cudaStream_t s) {
+int launch_ct(PassArgs& A, bool contiguous, int na, int nb, double bytes, cudaStream_t s) {
   if (contiguous) {
     constexpr int L = ct_lines<N>();
     const int grid = (int)ceil_div((int64_t)na * nb, L);
     const size_t smem = (size_t)(L + 1) * N * sizeof(float2);   // lines and the twiddle table
-    return launch("fft_contig_kernel", s, [&] { fft_contig_ct<N><<<grid, kThreads, smem, s>>>(A); });
+    return launch("fft_contig_kernel", s, [&] { fft_contig_ct<N><<<grid, kThreads, smem, s>>>(A); }, bytes);
   }
   constexpr int T = ct_tile<N>();
   const int64_t grid = ceil_div(nb, T) * (int64_t)na;
@@ -782,7 +788,7 @@ int launch_ct(PassArgs& A, bool contiguous, int na, int nb, cudaStream_t s) {
   if (smem > 48 * 1024)
     SPF_CUDA(cudaFuncSetAttribute(fft_strided_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return launch("fft_strided_kernel", s,
-                [&] { fft_strided_ct<N><<<(unsigned)grid, kThreads, smem, s>>>(A); });
+                [&] { fft_strided_ct<N><<<(unsigned)grid, kThreads, smem, s>>>(A); }, bytes);
 }
 
 int factorize(int n, int* radix) {
@@ -808,18 +814,30 @@ int count(const int* lo, const int* hi) {
   return std::max(0, hi[0] - lo[0]) + std::max(0, hi[1] - lo[1]);
 }
 
+// Algorithmic bytes of one pass: every line reads its positions inside the
+// read range (4 bytes real, 8 complex), writes all n outputs (4 or 8 bytes)
+// and reads n real factors when it multiplies by post_mul.
+double pass_bytes(const PassArgs& A, int na, int nb) {
+  const double lines = (double)na * nb;
+  const double rd = count(A.in_lo, A.in_hi);
+  const double ein = A.in_real ? 4.0 : 8.0, eout = A.out_real ? 4.0 : 8.0;
+  const double pm = A.post_mul ? 4.0 * A.n : 0.0;
+  return lines * (rd * ein + A.n * eout + pm);
+}
+
 int launch_pass(PassArgs A, bool contiguous, cudaStream_t s) {
   int na = count(A.ls.a_lo, A.ls.a_hi), nb = count(A.ls.b_lo, A.ls.b_hi);
   if (na == 0 || nb == 0) return SPF_OK;
+  const double bytes = pass_bytes(A, na, nb);
   switch (A.n) {
-    case 36: return launch_ct<36>(A, contiguous, na, nb, s);
-    case 72: return launch_ct<72>(A, contiguous, na, nb, s);
-    case 162: return launch_ct<162>(A, contiguous, na, nb, s);
-    case 216: return launch_ct<216>(A, contiguous, na, nb, s);
-    case 320: return launch_ct<320>(A, contiguous, na, nb, s);
-    case 324: return launch_ct<324>(A, contiguous, na, nb, s);
-    case 432: return launch_ct<432>(A, contiguous, na, nb, s);
-    case 640: return launch_ct<640>(A, contiguous, na, nb, s);
+    case 36: return launch_ct<36>(A, contiguous, na, nb, bytes, s);
+    case 72: return launch_ct<72>(A, contiguous, na, nb, bytes, s);
+    case 162: return launch_ct<162>(A, contiguous, na, nb, bytes, s);
+    case 216: return launch_ct<216>(A, contiguous, na, nb, bytes, s);
+    case 320: return launch_ct<320>(A, contiguous, na, nb, bytes, s);
+    case 324: return launch_ct<324>(A, contiguous, na, nb, bytes, s);
+    case 432: return launch_ct<432>(A, contiguous, na, nb, bytes, s);
+    case 640: return launch_ct<640>(A, contiguous, na, nb, bytes, s);
     default: break;
   }
   if (contiguous) {
@@ -828,14 +846,14 @@ int launch_pass(PassArgs A, bool contiguous, cudaStream_t s) {
     int grid = (int)ceil_div(total, A.lines_per_cta);
     size_t smem = (size_t)A.lines_per_cta * A.n * sizeof(float2);
     return launch("fft_contig_kernel", s,
-                  [&] { fft_contig_kernel<<<grid, kThreads, smem, s>>>(A); });
+                  [&] { fft_contig_kernel<<<grid, kThreads, smem, s>>>(A); }, bytes);
   } else {
     A.lines_per_cta = std::max(1, std::min(16, kMaxElems / A.n));
     int tiles_b = (int)ceil_div(nb, A.lines_per_cta);
     int64_t grid = (int64_t)tiles_b * na;
     size_t smem = (size_t)A.lines_per_cta * A.n * sizeof(float2);
     return launch("fft_strided_kernel", s,
-                  [&] { fft_strided_kernel<<<(unsigned)grid, kThreads, smem, s>>>(A); });
+                  [&] { fft_strided_kernel<<<(unsigned)grid, kThreads, smem, s>>>(A); }, bytes);
   }
 }
 

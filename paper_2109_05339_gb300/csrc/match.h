@@ -34,6 +34,7 @@ struct spf_matcher {
   int* rr_start = nullptr;        // max_orient + 1 bucket starts / cursors
   int* rr_order = nullptr;        // max_images
   int n_sms = 152;
+  int tc_force = 0;               // tensor-core schedule: 0 by the model, 1 contiguous, 2 grid
 };
 
 namespace spf {
@@ -41,5 +42,13 @@ int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit,
 int match_tc_supported(int device);
 // out[i] = (float)counts[i], i < n (device buffers).
 int counts_to_f32(const uint16_t* counts, int64_t n, float* out, cudaStream_t s);
-void tc_geometry(int n_img, int n_orient, int n_sms, int* grid, int* nsplit);
+// Launch schedule of the tensor-core matching kernel (match_tc.cu).
+struct TcSched {
+  int mode = 0;       // 0: contiguous tile ranges, 1: gi x go grid of image x orientation tile ranges
+  int grid = 1;       // CTAs
+  int nsplit = 1;     // candidate slots per image the launch writes
+  int gi = 0, go = 0;
+  double cost = 0.0;  // modelled seconds
+};
+TcSched tc_schedule(int n_img, int n_orient, int n_sms, int kpad, bool fp8, int force = 0);
 }  // namespace spf

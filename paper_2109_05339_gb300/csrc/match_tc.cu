@@ -151,9 +151,18 @@ constexpr uint32_t kTcHalf = 32 * 1024;      // one operand tile per stage (256 
 constexpr uint32_t kTcStage = 2 * kTcHalf;
 constexpr int kTcThreads = 384;
 
+// Which tiles each CTA computes. mode 0: contiguous ranges of the row-major
+// (image tile, orientation tile) order -- consecutive CTAs share image
+// tiles when there are few of them. mode 1: a gi x go grid of CTAs; CTA
+// (a, b) takes the image tiles of range a and the orientation tiles of range
+// b, image tile by image tile. The go CTAs of a row then work on the same
+// image tile and the gi CTAs of a column on the same orientation tile at the
+// same time, so each operand tile is read from HBM about once per row or
+// column instead of once per tile when the image tiles outnumber the CTAs.
 struct TcParams {
   int n_img, n_orient, orient_offset, nkb;
   int n_it, n_ot, total, grid;
+  int mode, gi, go;
   const float* y2;
   const float* xs;   // FP8 image scales (nullptr for BF16)
   const float* ys;   // FP8 slice scales
@@ -216,6 +225,44 @@ __host__ __device__ inline int work_start(int c, int total, int grid) {
   return (int)((long long)c * total / grid);
 }
 
+// The tiles of one CTA, in the order it computes them (image tile major).
+struct TcWork {
+  int mode, n_ot;
+  int q0, q1;          // mode 0: [q0, q1) of the row-major tile order
+  int i0, o0, ni, no;  // mode 1: image tiles [i0, i0 + ni) x orientation tiles [o0, o0 + no)
+  __device__ __forceinline__ int count() const { return mode == 0 ? q1 - q0 : ni * no; }
+  __device__ __forceinline__ void tile(int t, int& it, int& ot) const {
+    if (mode == 0) {
+      const int q = q0 + t;
+      it = q / n_ot;
+      ot = q - it * n_ot;
+    } else {
+      const int a = t / no;
+      it = i0 + a;
+      ot = o0 + (t - a * no);
+    }
+  }
+};
+
+__device__ __forceinline__ TcWork tc_work(const TcParams& p, int c) {
+  TcWork w;
+  w.mode = p.mode;
+  w.n_ot = p.n_ot;
+  if (p.mode == 0) {
+    w.q0 = work_start(c, p.total, p.grid);
+    w.q1 = work_start(c + 1, p.total, p.grid);
+    w.i0 = w.o0 = w.ni = w.no = 0;
+  } else {
+    const int a = c / p.go, b = c - a * p.go;
+    w.i0 = work_start(a, p.n_it, p.gi);
+    w.ni = work_start(a + 1, p.n_it, p.gi) - w.i0;
+    w.o0 = work_start(b, p.n_ot, p.go);
+    w.no = work_start(b + 1, p.n_ot, p.go) - w.o0;
+    w.q0 = w.q1 = 0;
+  }
+  return w;
+}
+
 // First CTA whose contiguous work range contains item q.
 __host__ __device__ inline int owner_cta(int q, int total, int grid) {
   int c = (int)(((long long)q * grid) / total);
@@ -241,7 +288,8 @@ tc_match_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x;
-  const int q0 = work_start(c, p.total, p.grid), q1 = work_start(c + 1, p.total, p.grid);
+  const TcWork work = tc_work(p, c);
+  const int n_tiles = work.count();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; ++s) {
@@ -273,8 +321,9 @@ tc_match_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       for (int s = 0; s < kTcStages; ++s) used[s] = false;
       uint32_t it = 0;
       bool ok = true;
-      for (int q = q0; q < q1 && ok; ++q) {
-        const int ti_ = q / p.n_ot, to_ = q - ti_ * p.n_ot;
+      for (int q = 0; q < n_tiles && ok; ++q) {
+        int ti_, to_;
+        work.tile(q, ti_, to_);
         for (int kb = 0; kb < p.nkb; ++kb, ++it) {
           const int s = it % kTcStages;
           const uint32_t ph = (it / kTcStages) & 1u;
@@ -297,7 +346,7 @@ tc_match_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     if (lane == 0) {
       uint32_t it = 0, t = 0;
       bool ok = true;
-      for (int q = q0; q < q1 && ok; ++q, ++t) {
+      for (int q = 0; q < n_tiles && ok; ++q, ++t) {
         if (!mbar_wait(tempty, (t & 1u) ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
         for (int kb = 0; kb < p.nkb; ++kb, ++it) {
@@ -335,7 +384,7 @@ tc_match_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     auto flush = [&](int it_) {
       const int i = it_ * kTcTile + row;
       if (i < p.n_img) {
-        const int slot = c - owner_cta(it_ * p.n_ot, p.total, p.grid);
+        const int slot = p.mode == 0 ? c - owner_cta(it_ * p.n_ot, p.total, p.grid) : c % p.go;
         const size_t o = ((size_t)i * kMaxSplits + slot) * kCand;
 #pragma unroll
         for (int k = 0; k < kCand; ++k) {
@@ -344,8 +393,9 @@ tc_match_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         }
       }
     };
-    for (int q = q0; q < q1; ++q, ++t) {
-      const int it_ = q / p.n_ot, to_ = q - it_ * p.n_ot;
+    for (int q = 0; q < n_tiles; ++q, ++t) {
+      int it_, to_;
+      work.tile(q, it_, to_);
       if (it_ != cur_it) {
         if (cur_it >= 0) flush(cur_it);
 #pragma unroll
@@ -423,19 +473,54 @@ int make_map(CUtensorMap* map, void* base, int rows, int Kpad, bool fp8) {
 
 }  // namespace
 
-// Grid and the number of candidate slots per image that one launch writes.
-void tc_geometry(int n_img, int n_orient, int n_sms, int* grid, int* nsplit) {
+// Schedule of one launch: the contiguous order (mode 0) or the gi x go grid
+// (mode 1), whichever a simple model predicts faster. Per CTA tile the model
+// charges the tensor-core time of 2 x 256 x 256 x K multiply-adds and, for the
+// whole launch, the HBM time of the operand tiles that concurrent CTAs do
+// not share (an operand that fits half the L2 is read once).
+TcSched tc_schedule(int n_img, int n_orient, int n_sms, int kpad, bool fp8, int force) {
   const int n_it = (int)ceil_div(n_img, kTcTile), n_ot = (int)ceil_div(n_orient, kTcTile);
-  const int total = n_it * n_ot;
-  int G = std::min({n_sms, total, n_it * (kMaxSplits - 1)});
-  G = std::max(G, 1);
-  int ns = 1;
-  for (int it = 0; it < n_it; ++it) {
-    int a = owner_cta(it * n_ot, total, G), b = owner_cta(it * n_ot + n_ot - 1, total, G);
-    ns = std::max(ns, b - a + 1);
+  const int64_t total = (int64_t)n_it * n_ot;
+  const double tile_bytes = (double)kTcTile * kpad * (fp8 ? 1.0 : 2.0);
+  const double t_tile = 2.0 * kTcTile * kTcTile * kpad / (fp8 ? 22.6e12 : 11.3e12);   // s per tile per SM
+  const double bw = 6.0e12, l2_half = 64.0e6;
+  auto traffic = [&](double share_a, double share_b) {
+    const double a_all = n_it * tile_bytes, b_all = n_ot * tile_bytes;
+    const double a = a_all <= l2_half ? a_all : total * tile_bytes / std::max(1.0, share_a);
+    const double b = b_all <= l2_half ? b_all : total * tile_bytes / std::max(1.0, share_b);
+    return (a + b) / bw;
+  };
+  TcSched best;
+  {
+    int G = (int)std::min<int64_t>({(int64_t)n_sms, total, (int64_t)n_it * (kMaxSplits - 1)});
+    G = std::max(G, 1);
+    int ns = 1;
+    for (int it = 0; it < n_it; ++it) {
+      int a = owner_cta(it * n_ot, (int)total, G), b = owner_cta(it * n_ot + n_ot - 1, (int)total, G);
+      ns = std::max(ns, b - a + 1);
+    }
+    best.mode = 0;
+    best.grid = G;
+    best.nsplit = ns;
+    best.gi = best.go = 0;
+    best.cost = std::max(ceil_div(total, G) * t_tile, traffic((double)G / n_it, (double)G / n_ot));
   }
-  *grid = G;
-  *nsplit = ns;
+  if (force == 1) return best;
+  if (force == 2) best.cost = 1e30;   // the best grid, whatever the contiguous order costs
+  for (int go = 1; go <= std::min(n_ot, kMaxSplits); ++go) {
+    const int gi = std::min(n_it, n_sms / go);
+    if (gi < 1) break;
+    const double cost = std::max((double)ceil_div(n_it, gi) * ceil_div(n_ot, go) * t_tile, traffic(go, gi));
+    if (cost < 0.97 * best.cost) {
+      best.mode = 1;
+      best.grid = gi * go;
+      best.nsplit = go;
+      best.gi = gi;
+      best.go = go;
+      best.cost = cost;
+    }
+  }
+  return best;
 }
 
 int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit, cudaStream_t s) {
@@ -443,10 +528,10 @@ int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit,
   CUtensorMap ta, tb;
   SPF_TRY(make_map(&ta, m->xq, m->n_img, m->Kpad, fp8));
   SPF_TRY(make_map(&tb, m->yq, n_orient, m->Kpad, fp8));
-  int G, ns;
-  tc_geometry(m->n_img, n_orient, m->n_sms, &G, &ns);
-  if (ns != nsplit) {
-    set_error("internal: split count %d != %d", ns, nsplit);
+  const TcSched sch = tc_schedule(m->n_img, n_orient, m->n_sms, m->Kpad, fp8, m->tc_force);
+  const int G = sch.grid;
+  if (sch.nsplit != nsplit) {
+    set_error("internal: split count %d != %d", sch.nsplit, nsplit);
     return SPF_ERR_ARG;
   }
   TcParams p;
@@ -458,6 +543,9 @@ int match_tc_launch(spf_matcher* m, int n_orient, int orient_offset, int nsplit,
   p.n_ot = (int)ceil_div(n_orient, kTcTile);
   p.total = p.n_it * p.n_ot;
   p.grid = G;
+  p.mode = sch.mode;
+  p.gi = sch.gi;
+  p.go = sch.go;
   p.y2 = m->y2;
   p.xs = fp8 ? m->xs : nullptr;
   p.ys = fp8 ? m->ys : nullptr;

@@ -1,13 +1,17 @@
 // Orientation matching without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they match:
-// code running while a CUDA stream is being captured into a graph, code
-// embedded in a host framework that owns the device memory pool and forbids
-// cudaMalloc, or real-time loops that must not touch the allocator. This entry
-// point runs the same FP32 matching kernels as spf_matcher_* (fused distance +
-// running top-8, exact FP32 re-rank of the 8 candidates), but its scratch --
-// row norms, candidate lists and running lists -- lives in one statically
-// sized device array that every GPU loading this library holds until exit.
+// code embedded in a host framework that owns the device memory pool and
+// forbids cudaMalloc next to it (the framework's allocator must see every
+// byte), or real-time acquisition loops that must not touch the allocator,
+// whose calls can block and synchronise the device. This entry point runs the
+// same FP32 matching kernels as spf_matcher_* (fused distance + running
+// top-8, exact FP32 re-rank of the 8 candidates), but its scratch -- row
+// norms, candidate lists and running lists -- lives in one statically sized
+// device array that every GPU loading this library holds until exit.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -45,19 +49,42 @@ constexpr size_t kScratchBytes = kOffStI + align256(sizeof(int) * (size_t)kStati
 static_assert(kScratchBytes == 4526080, "scratch size stated in include/spf.h");
 static __device__ __align__(256) unsigned char g_match_scratch[kScratchBytes];
 
-// Device address of g_match_scratch per device ordinal. In host code the
-// symbol's name is only a host-side stand-in, so its address is looked up
-// once per device with that device current.
+// Device address of g_match_scratch per device ordinal, with the CUDA
+// context it was looked up in. In host code the symbol's name is only a
+// host-side stand-in, so its address is looked up with the device current:
+// once per device, and again whenever the current context is another one
+// (after cudaDeviceReset, or a context the caller made current through the
+// driver API), where the module -- and the array -- live elsewhere.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+  CUcontext ctx = nullptr;
+  void* ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 int scratch_for_current_device(unsigned char** out) {
   int dev = -1;
   SPF_CUDA(cudaGetDevice(&dev));
   SPF_CHECK_ARG(dev >= 0 && dev < kMaxDevices, "device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchAddr& a = g_scratch[dev];
+  CUcontext ctx = current_context();
+  if (!a.ptr || !ctx || ctx != a.ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
     if (e != cudaSuccess || !p) {
@@ -65,9 +92,10 @@ int scratch_for_current_device(unsigned char** out) {
                      dev, cudaGetErrorString(e));
       return SPF_ERR_CUDA;
     }
-    g_scratch_ptr[dev] = p;
+    a.ptr = p;
+    a.ctx = current_context();   // the look-up made the runtime's context current
   }
-  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  *out = static_cast<unsigned char*>(a.ptr);
   return SPF_OK;
 }
 

@@ -1244,12 +1244,13 @@ int sort_and_cut(spf_plan* P, Grid& g, Pts pts, int64_t npts, SortedSet& set, in
   });
 }
 
-// Spread onto g.real (cleared first) the points of an already sorted set.
+// Spread onto g.real the points of an already sorted set (the grid cleared
+// first unless `clear` is false: then the spread adds to what it holds).
 template <int W, class Pts, class Str>
 int spread_sorted(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, const SortedSet& set, int* err,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool clear = true) {
   BinSort& b = g.bins;
-  SPF_CUDA(cudaMemsetAsync(g.real, 0, sizeof(float) * (size_t)g.nf * g.nf * g.nf, s));
+  if (clear) SPF_CUDA(cudaMemsetAsync(g.real, 0, sizeof(float) * (size_t)g.nf * g.nf * g.nf, s));
   if (npts == 0) return SPF_OK;
   SPF_CUDA(cudaMemsetAsync(set.nsubs + 1, 0, sizeof(int), s));   // work cursor
   using C = SpreadCfg<W>;
@@ -1266,10 +1267,11 @@ int spread_sorted(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, const So
 }
 
 template <int W, class Pts, class Str>
-int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cudaStream_t s) {
+int spread_w(spf_plan* P, Grid& g, Pts pts, Str str, int64_t npts, int* err, cudaStream_t s,
+             bool clear = true) {
   SortedSet set{P->sorted, g.bins.subs, g.bins.nsubs, g.bins.max_subs};
   if (npts > 0) SPF_TRY((sort_and_cut<W, Pts>(P, g, pts, npts, set, err, s)));
-  return spread_sorted<W, Pts, Str>(P, g, pts, str, npts, set, err, s);
+  return spread_sorted<W, Pts, Str>(P, g, pts, str, npts, set, err, s, clear);
 }
 
 }  // namespace
@@ -1289,14 +1291,15 @@ int type2_setup(spf_plan* P, const float* A, cudaStream_t s, bool halo) {
   Grid& g = P->g;
   const int64_t nm3 = (int64_t)P->N * P->N * P->N;
   SPF_TRY(launch("deconv_pad_kernel", s,
-                 [&] { deconv_pad_kernel<<<grid_for(nm3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); }));
+                 [&] { deconv_pad_kernel<<<grid_for(nm3), 256, 0, s>>>(A, P->N, g.deconv, g.nf, g.cube); },
+                 12.0 * nm3));
   SPF_TRY(fft3_exec_ex(&g.fft, g.cube, nullptr, g.real, nullptr, -1, P->Mh + 1, 0, s));
   if (!halo) return SPF_OK;
   const int np = g.nf + P->w, npx = halo_npx(g.nf, P->w);
   const int64_t tot = 4 * (int64_t)np * np * npx;
   return launch("halo_kernel", s, [&] {
     halo_kernel<<<grid_for(tot), 256, 0, s>>>(g.real, g.nf, np, npx, P->w / 2, g.halo);
-  });
+  }, 4.0 * tot + 4.0 * g.nf * (double)g.nf * g.nf);
 }
 
 // Slices of M orientations; sorted in chunks of whole orientations that fit
@@ -1366,7 +1369,7 @@ static int type1_finish(spf_plan* P, Grid& g, float* out, int accumulate, cudaSt
   int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
   return launch("crop_deconv_kernel", s, [&] {
     crop_deconv_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, hx, g.n_modes, g.deconv, out, accumulate);
-  });
+  }, (accumulate ? 16.0 : 12.0) * m3);
 }
 
 // Toeplitz kernel from the spread T-grid: FFT, K(d) = Re, circulant
@@ -1380,31 +1383,49 @@ static int kernel_finish(spf_plan* P, float* kernel_hat, int accumulate, cudaStr
   int64_t m3 = (int64_t)g.n_modes * g.n_modes * g.n_modes;
   SPF_TRY(launch("crop_embed_kernel", s, [&] {
     crop_embed_kernel<<<grid_for(m3), 256, 0, s>>>(g.cube, g.nf, hx, g.n_modes, g.deconv, P->PT, P->cubeP);
-  }));
+  }, 16.0 * m3));
   SPF_TRY(fft3_exec_ex(&P->fftP, P->cubeP, nullptr, P->realP, nullptr, -1, P->N, 0, s));
   return launch("accumulate_kernel", s, [&] {
     accumulate_kernel<<<grid_for(PT3), 256, 0, s>>>(P->realP, kernel_hat, PT3, accumulate);
-  });
+  }, (accumulate ? 12.0 : 8.0) * PT3);
 }
 
 // Merge: RHS onto the N-mode grid, Toeplitz kernel onto the (2N-1)-mode grid.
+// mode: kMergeClear clears a grid before spreading onto it, kMergeFinish
+// transforms it into the output afterwards; a deferred merge spreads several
+// chunks with neither and finishes once (merge_finish).
 int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats, const int* oidx,
               int n_img, const float* qlab, int P2, const float* D, float b_scale, float* rhs,
-              float* kernel_hat, int accumulate, int* err, cudaStream_t s) {
+              float* kernel_hat, int accumulate, int* err, cudaStream_t s, int mode, bool want_rhs,
+              bool want_kernel) {
   const float4* q4 = reinterpret_cast<const float4*>(quats);
   int64_t npts = (int64_t)n_img * P2;
-  if (rhs) {
+  const bool clear = (mode & kMergeClear) != 0, finish = (mode & kMergeFinish) != 0;
+  if (want_rhs) {
     QuatPts pts{q4, qlab, FastDiv((uint32_t)P2), P->g.cells_per_q, oidx, n_quats, err, (float)P->g.nf, 1.f / (float)P->g.nf};
     StrImage str{images, D, FastDiv((uint32_t)P2), b_scale};
-    SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, QuatPts, StrImage>(P, P->g, pts, str, npts, err, s))));
-    SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
+    SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, QuatPts, StrImage>(P, P->g, pts, str, npts, err, s, clear))));
+    if (finish) SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
   }
-  if (kernel_hat) {
+  if (want_kernel) {
     QuatPts pts{q4, qlab, FastDiv((uint32_t)P2), P->gT.cells_per_q, oidx, n_quats, err, (float)P->gT.nf, 1.f / (float)P->gT.nf};
     StrWeights str{D, FastDiv((uint32_t)P2)};
-    SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, QuatPts, StrWeights>(P, P->gT, pts, str, npts, err, s))));
-    SPF_TRY(kernel_finish(P, kernel_hat, accumulate, s));
+    SPF_W_SWITCH(P->w, SPF_TRY((spread_w<W, QuatPts, StrWeights>(P, P->gT, pts, str, npts, err, s, clear))));
+    if (finish) SPF_TRY(kernel_finish(P, kernel_hat, accumulate, s));
   }
+  return SPF_OK;
+}
+
+// Deferred merge: clear both fine grids / transform what they hold.
+int merge_begin(spf_plan* P, cudaStream_t s) {
+  SPF_CUDA(cudaMemsetAsync(P->g.real, 0, sizeof(float) * (size_t)P->g.nf * P->g.nf * P->g.nf, s));
+  SPF_CUDA(cudaMemsetAsync(P->gT.real, 0, sizeof(float) * (size_t)P->gT.nf * P->gT.nf * P->gT.nf, s));
+  return SPF_OK;
+}
+
+int merge_finish(spf_plan* P, float* rhs, float* kernel_hat, int accumulate, cudaStream_t s) {
+  if (rhs) SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
+  if (kernel_hat) SPF_TRY(kernel_finish(P, kernel_hat, accumulate, s));
   return SPF_OK;
 }
 
@@ -1435,7 +1456,7 @@ int slice_points(spf_plan* P, spf_points* S, const float* A, float* out, cudaStr
 
 int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oidx, int n_img, int off,
                  const float* D, float b_scale, float* rhs, float* kernel_hat, int accumulate,
-                 cudaStream_t s) {
+                 cudaStream_t s, int mode, bool want_rhs, bool want_kernel) {
   const int64_t npts = (int64_t)S->M * S->P2;
   SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)npts, s));
   SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
@@ -1448,19 +1469,20 @@ int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oid
     }));
   }
   const float4* q4 = reinterpret_cast<const float4*>(S->quats);
-  if (rhs) {
+  const bool clear = (mode & kMergeClear) != 0, finish = (mode & kMergeFinish) != 0;
+  if (want_rhs) {
     QuatPts pts{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
     StrSorted str{S->cls};
     SPF_W_SWITCH(P->w, SPF_TRY((spread_sorted<W, QuatPts, StrSorted>(P, P->g, pts, str, npts, S->setN,
-                                                                    P->err, s))));
-    SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
+                                                                    P->err, s, clear))));
+    if (finish) SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
   }
-  if (kernel_hat) {
+  if (want_kernel) {
     QuatPts pts{q4, S->qlab, FastDiv((uint32_t)S->P2), P->gT.cells_per_q, nullptr, 0, P->err, (float)P->gT.nf, 1.f / (float)P->gT.nf};
     StrCount str{S->cnt, D, FastDiv((uint32_t)S->P2)};
     SPF_W_SWITCH(P->w, SPF_TRY((spread_sorted<W, QuatPts, StrCount>(P, P->gT, pts, str, npts, S->setT,
-                                                                   P->err, s))));
-    SPF_TRY(kernel_finish(P, kernel_hat, accumulate, s));
+                                                                   P->err, s, clear))));
+    if (finish) SPF_TRY(kernel_finish(P, kernel_hat, accumulate, s));
   }
   return SPF_OK;
 }

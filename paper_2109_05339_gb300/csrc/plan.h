@@ -89,6 +89,10 @@ struct spf_plan {
   double* cg_part = nullptr;  // per-block partial sums
   unsigned* cg_count = nullptr;  // blocks done with a fused reduction (last one finalises)
   int* err = nullptr;         // device error word (bit 1: point outside its bin)
+  double* grad_part = nullptr;   // gradient merge: per-block partials (2 per block)
+  unsigned* grad_count = nullptr;
+  double* grad_sc = nullptr;     // [g.g, g.Hg]
+  bool merge_open = false;    // a deferred merge holds partial sums in the fine grids
 };
 
 // Orientations x pixels of a fixed orientation set, sorted once for both grids.
@@ -107,6 +111,10 @@ struct spf_points {
 };
 
 namespace spf {
+// Merge modes (nufft.cu): clear the fine grid before spreading, transform it
+// into the output after.
+constexpr int kMergeClear = 1;
+constexpr int kMergeFinish = 2;
 // Host side of the ES kernel set-up (es.cu).
 void es_params(double eps, int* w, double* beta);
 void es_poly(int w, double beta, EsPoly* out);

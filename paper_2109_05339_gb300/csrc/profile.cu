@@ -30,6 +30,7 @@ struct Prof {
   std::vector<std::string> names;
   std::vector<long long> count;
   std::vector<double> ms;
+  std::vector<double> bytes;
   std::vector<Pending> pending;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
   size_t pool_used = 0;
@@ -48,6 +49,7 @@ int kernel_id(Prof& P, const char* name) {
   P.names.emplace_back(name);
   P.count.push_back(0);
   P.ms.push_back(0.0);
+  P.bytes.push_back(0.0);
   return (int)P.names.size() - 1;
 }
 
@@ -66,7 +68,7 @@ void drain(Prof& P) {
 
 bool prof_on() { return prof().on; }
 
-int prof_begin(const char* name, cudaStream_t s) {
+int prof_begin(const char* name, cudaStream_t s, double bytes) {
   Prof& P = prof();
   std::lock_guard<std::mutex> g(P.mu);
   if (!P.on) return -1;
@@ -90,7 +92,9 @@ int prof_begin(const char* name, cudaStream_t s) {
   }
   auto ev = P.pool[P.pool_used++];
   cudaEventRecord(ev.first, s);
-  P.pending.push_back({kernel_id(P, name), ev.first, ev.second});
+  const int id = kernel_id(P, name);
+  P.bytes[id] += bytes;
+  P.pending.push_back({id, ev.first, ev.second});
   return (int)P.pending.size() - 1;
 }
 
@@ -114,6 +118,7 @@ int spf_profile_enable(int on) {
     for (size_t i = 0; i < P.count.size(); ++i) {
       P.count[i] = 0;
       P.ms[i] = 0.0;
+      P.bytes[i] = 0.0;
     }
     P.dropped = 0;
   }
@@ -154,6 +159,18 @@ int spf_profile_read(int index, char* name, int name_len, long long* launches, d
   }
   if (launches) *launches = P.count[index];
   if (total_ms) *total_ms = P.ms[index];
+  return SPF_OK;
+}
+
+int spf_profile_bytes(int index, double* bytes) {
+  clear_error();
+  Prof& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  if (index < 0 || index >= (int)P.names.size()) {
+    set_error("no profiled kernel at index %d", index);
+    return SPF_ERR_ARG;
+  }
+  if (bytes) *bytes = P.bytes[index];
   return SPF_OK;
 }
 

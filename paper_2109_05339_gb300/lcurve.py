@@ -2,10 +2,10 @@
 
 For each lambda of a sweep, CG solves Eq. 2 on the device; the library then
 computes |A x - b|_D^2 (from the Toeplitz product and the right-hand side, no
-pass over the points) and |x - x0|^2 with FP64 reductions. The chosen lambda
-maximises the curvature of (log |A x - b|, log |x - x0|) as a function of
-log lambda (three-point derivatives on the possibly uneven grid). Only the
-few scalars of the curve are read back to the host.
+pass over the points) and |x - x0|^2 with FP64 reductions, and picks the
+lambda of maximum curvature of (log |A x - b|_D, log |x - x0|) over
+log lambda (spf_lcurve_corner). This module only marshals: the few scalars of
+the curve are read back and passed to the library's corner search.
 """
 from __future__ import annotations
 
@@ -18,24 +18,19 @@ from ._lib import check, lib
 from .api import Plan, _f32, _ptr, _stream
 
 
-def _deriv(y, s):
-    h0 = s[1:-1] - s[:-2]
-    h1 = s[2:] - s[1:-1]
-    d1 = (-h1 / (h0 * (h0 + h1)) * y[:-2] + (h1 - h0) / (h0 * h1) * y[1:-1]
-          + h0 / (h1 * (h0 + h1)) * y[2:])
-    d2 = 2.0 * (y[:-2] / (h0 * (h0 + h1)) - y[1:-1] / (h0 * h1) + y[2:] / (h1 * (h0 + h1)))
-    return d1, d2
-
-
 def corner(lams, res2, reg2):
-    """Index of the maximum-curvature point of the L-curve (interior points)."""
-    s = np.log(np.asarray(lams, dtype=np.float64))
-    rho = 0.5 * np.log(np.asarray(res2, dtype=np.float64))
-    eta = 0.5 * np.log(np.asarray(reg2, dtype=np.float64))
-    r1, r2 = _deriv(rho, s)
-    e1, e2 = _deriv(eta, s)
-    kappa = (r1 * e2 - r2 * e1) / (r1 * r1 + e1 * e1) ** 1.5
-    return int(np.argmax(kappa)) + 1, kappa
+    """Index of the maximum-curvature point of the L-curve, and the curvature
+    at the interior points (computed by the library)."""
+    lams = np.ascontiguousarray(lams, dtype=np.float64)
+    res2 = np.ascontiguousarray(res2, dtype=np.float64)
+    reg2 = np.ascontiguousarray(reg2, dtype=np.float64)
+    n = lams.shape[0]
+    kappa = np.zeros(max(n - 2, 0), dtype=np.float64)
+    idx = C.c_int()
+    check(lib.spf_lcurve_corner(lams.ctypes.data_as(C.c_void_p), res2.ctypes.data_as(C.c_void_p),
+                                reg2.ctypes.data_as(C.c_void_p), n, C.byref(idx),
+                                kappa.ctypes.data_as(C.c_void_p)))
+    return idx.value, kappa
 
 
 def weighted_sumsq(plan: Plan, images, D=None, scale=1.0, out=None, accumulate=False):
@@ -50,7 +45,7 @@ def weighted_sumsq(plan: Plan, images, D=None, scale=1.0, out=None, accumulate=F
 
 
 def sweep(plan: Plan, kernel_hat, rhs, x0, lams, iters, b_norm2):
-    """CG solve for every lambda; returns dict(lams, res2, reg2, index, x)."""
+    """CG solve for every lambda; returns dict(lams, res2, reg2, index, kappa, x, xs)."""
     d = plan.device
     vals = torch.zeros((len(lams), 2), dtype=torch.float64, device=x0.device)
     xs = []

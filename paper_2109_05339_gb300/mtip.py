@@ -1,210 +1,259 @@
 """One slice -> match -> merge -> CG iteration of M-TIP on one GPU (Fig. 3
-without phasing), as a sequence of C-ABI calls.
+without phasing): a thin binding of the library's native driver
+(spf_mtip_* in include/spf.h), which orchestrates the kernels.
 
-The reference orientations are fixed across iterations (Sec. II-A), so their
-rotated detector points are sorted once per orientation chunk (PointSet) and
-reused by every iteration's slicing and merge. A point set costs 16 bytes per
-(orientation, pixel); when the whole set would not fit the memory budget
-(e.g. the paper's 1.2 million orientations of 128 x 128 pixels, 315 GB) the
-driver streams instead: each chunk's points are sorted (for slicing only,
-4 bytes per point), sliced and matched, then released, and the merge spreads
-the images at their matched orientations (image chunks accumulate).
-
-The driver numbers the reference orientations along a space-filling (Morton)
-curve of their quaternions, so that orientations close in index are close on
-SO(3): images re-ranked together then share candidate model images, which
-stay in L2. Indices returned to the caller are in the caller's numbering
-(an exact distance tie resolves to the lower index in the driver's numbering).
+The reference orientations are fixed across iterations (Sec. II-A), so the
+driver takes the orientation set once: it renumbers it along a Morton curve of
+the quaternions and sorts the rotated points of every orientation chunk once
+(kept, 16 bytes per orientation x pixel) or, beyond the memory budget (e.g.
+the paper's 1.2 million orientations of 128 x 128 pixels, 315 GB), re-sorts
+them per chunk for slicing on every iteration and merges image chunks at their
+matched orientations. The binding re-sends the set when the caller passes
+other tensors, or the same tensors written in place through torch (their
+version counter moved); the driver keeps its own copies.
 
 1. Slicing (Sec. II-A) and matching (Sec. II-B), streamed in orientation
-   chunks: each chunk of model images is sliced into one reusable buffer and
-   matched against every image; the running top-k survives across chunks, so
-   no more than one chunk of slices is resident.
-2. Merging (Sec. II-C): images are summed per matched orientation (class
-   sums) and the sums and class counts are spread at the fixed points; chunks
-   accumulate (linearity, the paper's per-node type-1 sums and reduction).
+   chunks; the running top-k survives across chunks.
+2. Merging (Sec. II-C): every chunk is spread onto the plan's fine grids,
+   transformed once into the right-hand side and the Toeplitz kernel
+   (linearity, the paper's per-node type-1 sums and reduction).
 3. ``cg_iters`` conjugate-gradient steps on Eq. 2 from x0 = current model,
    lambda = lam_rel * sum of the weights D over all merged pixels.
+
+With a process group the images are one shard: the right-hand side and the
+kernel are summed over the ranks between merge and solve, and lambda takes
+the global image count.
 """
 from __future__ import annotations
+
+import ctypes as C
 
 import numpy as np
 import torch
 
-from .api import COUNT_DTYPES, Matcher, Plan, PointSet, counts_to_f32
+from ._lib import SPF_IMAGES_F32, SPF_IMAGES_U16, MtipConfig, check, lib
+from .api import COUNT_DTYPES, PRECISIONS, Matcher, Plan, _dev_index, _f32, _ptr, _stream
 from .dist import allreduce_sum_, global_count
 
 
 def morton_order(quats_host):
-    """Permutation sorting unit quaternions (w, x, y, z; w >= 0) by the Morton
-    code of (x, y, z) quantised to 10 bits per axis."""
-    q = np.asarray(quats_host, dtype=np.float64)
-    c = np.clip(((q[:, 1:4] + 1.0) * 0.5 * 1023.0).round(), 0, 1023).astype(np.uint64)
-    key = np.zeros(q.shape[0], dtype=np.uint64)
-    for bit in range(10):
-        for a in range(3):
-            key |= ((c[:, a] >> np.uint64(bit)) & np.uint64(1)) << np.uint64(3 * bit + a)
-    return np.argsort(key, kind="stable")
+    """The driver's renumbering: permutation sorting unit quaternions (w, x, y,
+    z) by the Morton code of (x, y, z) quantised to 10 bits per axis."""
+    q = np.ascontiguousarray(np.asarray(quats_host, dtype=np.float32))
+    M = q.shape[0]
+    out = np.empty(M, dtype=np.int32)
+    check(lib.spf_morton_order(q.ctypes.data_as(C.c_void_p), M, out.ctypes.data_as(C.c_void_p)))
+    return out.astype(np.int64)
 
 
-POINT_SET_BYTES = 16   # per (orientation, pixel): two sort orders, inverse order, class sum
+def _tensor_key(t):
+    """Identity of a tensor's contents as far as torch can tell without reading
+    them: storage, shape, and the version counter that every in-place write
+    through torch increments."""
+    return (t.data_ptr(), tuple(t.shape), t._version)
 
 
 class MTIP:
     def __init__(self, N, qmax, P2, n_img, n_orient, orient_chunk=None, img_chunk=None,
                  eps=1e-6, precision="bf16", topk=8, device=None, cache_points=None,
-                 point_budget_bytes=None, process_group=None):
-        """cache_points: keep every chunk's sorted points across iterations
-        (True), stream them (False), or decide from point_budget_bytes (None;
-        default budget: half of the device's free memory at construction).
-        process_group: the images are one shard of a torch.distributed group;
-        the merge's sums and the image count are added over its ranks."""
+                 point_budget_bytes=None, process_group=None, host_images=None):
+        """cache_points: keep every chunk's sorted points (True), stream them
+        (False), or decide from point_budget_bytes (None; default budget: half
+        of the device's free memory). process_group: the images are one shard
+        of a torch.distributed group. host_images: None, "f32" or "u16" --
+        the image type of iteration_host (allocates its two device slots)."""
         self.group = process_group
-        self._n_total = {}   # local image count -> count over the group
-        self.orient_chunk = min(n_orient, orient_chunk or n_orient)
-        if device is None:
-            dev = torch.device("cuda", torch.cuda.current_device())
-        else:
-            dev = device if isinstance(device, torch.device) else torch.device("cuda", int(device))
-        if cache_points is None:
-            if point_budget_bytes is None:
-                free, _ = torch.cuda.mem_get_info(dev)
-                point_budget_bytes = free // 2
-            cache_points = POINT_SET_BYTES * n_orient * P2 <= point_budget_bytes
-        self.cache_points = bool(cache_points)
-        # the plan's own sort buffers serve per-call slicing of one orientation
-        # chunk and, when streaming, the merge of one image chunk (< 2^31 points)
-        self.img_chunk = min(n_img, img_chunk or n_img, (2 ** 31 - 1) // P2)
-        max_pts = self.orient_chunk * P2
-        if not self.cache_points:
-            max_pts = max(max_pts, self.img_chunk * P2)
-        self.plan = Plan(N, qmax, eps, max_points=max_pts, device=device)
-        self.device = self.plan.device
-        self.matcher = Matcher(n_img, self.orient_chunk, P2, precision, topk, device=self.device)
-        dev = torch.device("cuda", self.device)
-        self.slices = torch.empty((self.orient_chunk, P2), dtype=torch.float32, device=dev)
-        self.rhs = torch.empty((N,) * 3, dtype=torch.float32, device=dev)
-        self.khat = torch.empty((self.plan.PT,) * 3, dtype=torch.float32, device=dev)
-        self.x = torch.empty((N,) * 3, dtype=torch.float32, device=dev)
-        self.N, self.P2, self.n_img, self.n_orient = N, P2, n_img, n_orient
-        self.sets = None
+        self._n_total = {}
+        dev = _dev_index(device)
+        cfg = MtipConfig(N=int(N), qmax=float(qmax), eps=float(eps), P2=int(P2), max_images=int(n_img),
+                         n_orient=int(n_orient), orient_chunk=int(orient_chunk or 0),
+                         img_chunk=int(img_chunk or 0),
+                         precision=PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                         topk=int(topk), cache_points=-1 if cache_points is None else int(bool(cache_points)),
+                         point_budget_bytes=int(point_budget_bytes or 0),
+                         host_image_type={None: -1, "f32": SPF_IMAGES_F32, "u16": SPF_IMAGES_U16}[host_images],
+                         device=dev)
+        h = C.c_void_p()
+        check(lib.spf_mtip_create(C.byref(h), C.byref(cfg)))
+        self._h = h
+        cp, oc, ic = C.c_int(), C.c_int(), C.c_int()
+        check(lib.spf_mtip_info(h, C.byref(cp), C.byref(oc), C.byref(ic)))
+        self.cache_points, self.orient_chunk, self.img_chunk = bool(cp.value), oc.value, ic.value
+        self.device = dev
+        self.N, self.P2, self.n_img, self.n_orient, self.topk = int(N), int(P2), int(n_img), int(n_orient), int(topk)
+        self.host_images = host_images
+        self.plan = Plan.view(lib.spf_mtip_plan(h), N, qmax, eps, device=dev)
+        self.matcher = Matcher.view(lib.spf_mtip_matcher(h), n_img, self.orient_chunk, P2, precision, topk,
+                                    device=dev)
+        d = torch.device("cuda", dev)
+        self.rhs = torch.empty((N,) * 3, dtype=torch.float32, device=d)
+        self.khat = torch.empty((self.plan.PT,) * 3, dtype=torch.float32, device=d)
+        self.x = torch.empty((N,) * 3, dtype=torch.float32, device=d)
+        self._best = torch.empty(n_img, dtype=torch.int32, device=d)
         self._key = None
-        self._okey = None
-        self.order = None   # sorted index -> caller's orientation index (int64, device)
-        self.quats_sorted = None
-        self._img32 = None   # FP32 images converted from 16-bit counts
+        self._mask = None
 
-    def _order_orientations(self, quats):
-        """Renumber the orientation set along the Morton curve (once per set)."""
-        okey = (quats.data_ptr(), tuple(quats.shape))
-        if self._okey == okey:
+    # -- configuration --------------------------------------------------------
+    def set_orientations(self, quats, q_lab, force=False):
+        """Give the driver the orientation set and detector (sorted once);
+        repeated calls with unchanged tensors do nothing unless force is set."""
+        _f32(quats, "quats", self.device, (self.n_orient, 4))
+        _f32(q_lab, "q_lab", self.device, (self.P2, 3))
+        key = (_tensor_key(quats), _tensor_key(q_lab))
+        if key == self._key and not force:
             return
-        order = morton_order(quats.detach().cpu().numpy())
-        self.order = torch.as_tensor(order, dtype=torch.int64, device=quats.device)
-        self.quats_sorted = quats.index_select(0, self.order).contiguous()
-        self._okey = okey
-
-    def set_orientations(self, quats, q_lab):
-        """Sort the points of every orientation chunk once (reused by later calls)."""
-        self._order_orientations(quats)
-        key = (quats.data_ptr(), tuple(quats.shape), q_lab.data_ptr(), tuple(q_lab.shape))
-        if self._key == key:
-            return
-        if self.sets:
-            for _, s in self.sets:
-                s.close()
-        self.sets = []
-        qs = self.quats_sorted
-        M = qs.shape[0]
-        for c0 in range(0, M, self.orient_chunk):
-            c1 = min(M, c0 + self.orient_chunk)
-            self.sets.append((c0, PointSet(self.plan, qs[c0:c1].contiguous(), q_lab)))
+        self._key = None
+        check(lib.spf_mtip_set_orientations(self._h, _ptr(quats), _ptr(q_lab), _stream(self.device)))
         self._key = key
 
-    def _to_caller(self, res):
-        """Match results with orientation indices in the caller's numbering;
-        the sorted-numbering best index is kept under 'best_sorted'."""
-        out = dict(res)
-        out["best_sorted"] = res["best"]
-        out["best"] = self.order.index_select(0, res["best"].long()).to(torch.int32)
-        if "topk_idx" in res:
-            ti = res["topk_idx"].long()
-            out["topk_idx"] = self.order.index_select(0, ti.clamp(min=0).reshape(-1)).reshape(ti.shape) \
-                .to(torch.int32).masked_fill(ti < 0, -1)
+    def set_mask(self, D):
+        """Pixel weights D (P2,) for matching, merging and lambda; None: ones."""
+        key = None if D is None else _tensor_key(D)
+        if key == self._mask:
+            return
+        if D is not None:
+            _f32(D, "D", self.device, (self.P2,))
+        self._D = D                       # the driver keeps the pointer
+        check(lib.spf_mtip_set_mask(self._h, _ptr(D), _stream(self.device)))
+        self._mask = key
+
+    def _images(self, images):
+        if images.dtype in COUNT_DTYPES:
+            t = SPF_IMAGES_U16
+        elif images.dtype == torch.float32:
+            t = SPF_IMAGES_F32
+        else:
+            raise TypeError("images must be float32, or 16-bit photon counts (int16 read as unsigned, uint16)")
+        if images.device.type != "cuda" or images.device.index != self.device or not images.is_contiguous():
+            raise ValueError(f"images must be contiguous on cuda:{self.device}")
+        if images.dim() != 2 or images.shape[1] != self.P2 or not 1 <= images.shape[0] <= self.n_img:
+            raise ValueError(f"images must be (n, {self.P2}) with 1 <= n <= {self.n_img}")
+        return t
+
+    # -- the three steps --------------------------------------------------------
+    def match(self, A, quats, q_lab, images, img_scale, with_topk=False):
+        """Per image the best orientation (caller's numbering), best and
+        second distances, optionally the re-ranked top-k."""
+        self.set_orientations(quats, q_lab)
+        self.plan._grid(A, "A")
+        t = self._images(images)
+        n, d = images.shape[0], images.device
+        best = torch.empty(n, dtype=torch.int32, device=d)
+        d1 = torch.empty(n, dtype=torch.float32, device=d)
+        d2 = torch.empty(n, dtype=torch.float32, device=d)
+        ti = td = None
+        if with_topk:
+            ti = torch.empty((n, self.topk), dtype=torch.int32, device=d)
+            td = torch.empty((n, self.topk), dtype=torch.float32, device=d)
+        check(lib.spf_mtip_match(self._h, _ptr(A), _ptr(images), t, n, C.c_float(img_scale), _ptr(best), _ptr(d1),
+                                 _ptr(d2), _ptr(ti), _ptr(td), _stream(self.device)))
+        out = {"best": best, "d1": d1, "d2": d2}
+        if with_topk:
+            out["topk_idx"], out["topk_d"] = ti, td
         return out
 
-    def match(self, A, quats, q_lab, images, img_scale, with_topk=False):
-        """Match every image against the orientation set; indices in the
-        caller's numbering ('best_sorted': the driver's own numbering)."""
-        m = self.matcher
-        m.set_images(images, img_scale)
-        if self.cache_points:
-            self.set_orientations(quats, q_lab)
-            for c0, ps in self.sets:
-                sl = self.slices[: ps.M]
-                ps.slice(A, out=sl)
-                m.add_slices(sl, orient_offset=c0)
-            return self._to_caller(m.results(with_topk))
-        self._order_orientations(quats)
-        qs = self.quats_sorted
-        M = qs.shape[0]
-        for c0 in range(0, M, self.orient_chunk):
-            c1 = min(M, c0 + self.orient_chunk)
-            ps = PointSet(self.plan, qs[c0:c1].contiguous(), q_lab, slice_only=True)
-            sl = self.slices[: c1 - c0]
-            ps.slice(A, out=sl)
-            m.add_slices(sl, orient_offset=c0)
-            ps.close()
-        return self._to_caller(m.results(with_topk))
+    def merge(self, images, quats, q_lab, best, img_scale, rhs=None, kernel_hat=None):
+        """Right-hand side and Toeplitz-kernel spectrum of the images at
+        orientations best (caller's numbering, int32)."""
+        self.set_orientations(quats, q_lab)
+        t = self._images(images)
+        if best.dtype != torch.int32 or not best.is_contiguous() or best.shape != (images.shape[0],):
+            raise ValueError("best must be a contiguous int32 tensor, one per image")
+        rhs = self.rhs if rhs is None else self.plan._grid(rhs, "rhs")
+        kernel_hat = self.khat if kernel_hat is None else _f32(kernel_hat, "kernel_hat", self.device,
+                                                               (self.plan.PT,) * 3)
+        check(lib.spf_mtip_merge(self._h, _ptr(images), t, images.shape[0], C.c_float(img_scale), _ptr(best),
+                                 _ptr(rhs), _ptr(kernel_hat), _stream(self.device)))
+        return rhs, kernel_hat
 
-    def merge(self, images, quats, best_sorted, q_lab, img_scale, D=None):
-        """Merge at the matched orientations, given in the driver's numbering
-        (the 'best_sorted' of match)."""
-        if self.cache_points:
-            self.set_orientations(quats, q_lab)
-            for k, (c0, ps) in enumerate(self.sets):
-                ps.merge(images, best_sorted, orient_offset=c0, D=D, b_scale=img_scale, rhs=self.rhs,
-                         kernel_hat=self.khat, accumulate=k > 0)
-            return self.rhs, self.khat
-        self._order_orientations(quats)
-        n = images.shape[0]
-        for i0 in range(0, n, self.img_chunk):
-            i1 = min(n, i0 + self.img_chunk)
-            self.plan.merge_images(images[i0:i1], self.quats_sorted, q_lab, D=D, b_scale=img_scale,
-                                   rhs=self.rhs, kernel_hat=self.khat, accumulate=i0 > 0,
-                                   orient_idx=best_sorted[i0:i1].contiguous())
-        return self.rhs, self.khat
+    def solve_system(self, rhs, kernel_hat, x0, lam_rel, n_img_total, cg_iters, x=None, res_hist=None):
+        """CG on Eq. 2 from x0; returns (x, lambda)."""
+        x = self.x if x is None else self.plan._grid(x, "x")
+        if res_hist is not None and (res_hist.dtype != torch.float64 or res_hist.numel() < cg_iters + 1):
+            raise ValueError("res_hist must be a float64 device tensor of cg_iters + 1 values")
+        lam = C.c_double()
+        check(lib.spf_mtip_solve(self._h, _ptr(rhs), _ptr(kernel_hat), _ptr(self.plan._grid(x0, "x0")),
+                                 float(lam_rel), int(n_img_total), int(cg_iters), _ptr(x), C.byref(lam),
+                                 _ptr(res_hist), _stream(self.device)))
+        return x, lam.value
 
-    def _images_f32(self, images):
-        """The images as FP32: 16-bit photon counts are converted on the
-        device into a buffer kept by the driver."""
-        if images.dtype not in COUNT_DTYPES:
-            return images
-        if self._img32 is None or self._img32.shape != images.shape or self._img32.device != images.device:
-            self._img32 = torch.empty(images.shape, dtype=torch.float32, device=images.device)
-        return counts_to_f32(images, out=self._img32)
+    def _global_count(self, n):
+        if self.group is None:
+            return n
+        if n not in self._n_total:
+            self._n_total[n] = global_count(n, torch.device("cuda", self.device), self.group)
+        return self._n_total[n]
 
-    def iteration(self, A, quats, q_lab, images, img_scale, cg_iters, lam_rel=1e-3, D=None,
-                  d_sum=None, res_hist=None):
-        """Returns (match results, merged model x, lambda); d_sum = sum of D over one image.
-        images: FP32, or 16-bit photon counts (int16 read as unsigned, or uint16)."""
-        images = self._images_f32(images)
-        res = self.match(A, quats, q_lab, images, img_scale)
-        self.merge(images, quats, res["best_sorted"], q_lab, img_scale, D)
-        n_img = images.shape[0]
+    def solve(self, A, quats, q_lab, images, img_scale, best, cg_iters, lam_rel=1e-3, D=None, res_hist=None):
+        """The merge and solve half of an iteration at given orientations:
+        image i merged at orientation best[i] (caller's numbering), then
+        cg_iters CG steps from x0 = A. Returns (x, lambda)."""
+        self.set_mask(D)
+        rhs, kh = self.merge(images, quats, q_lab, best, img_scale)
         if self.group is not None:
-            allreduce_sum_([self.rhs, self.khat], self.group)
-            if n_img not in self._n_total:
-                self._n_total[n_img] = global_count(n_img, images.device, self.group)
-            n_img = self._n_total[n_img]
-        per_img = float(self.P2) if D is None else float(d_sum)
-        lam = lam_rel * per_img * n_img
-        x = self.plan.cg_solve(self.khat, lam, self.rhs, A, cg_iters, x=self.x, res_hist=res_hist)
+            allreduce_sum_([rhs, kh], self.group)
+        return self.solve_system(rhs, kh, A, lam_rel, self._global_count(images.shape[0]), cg_iters,
+                                 res_hist=res_hist)
+
+    def iteration(self, A, quats, q_lab, images, img_scale, cg_iters, lam_rel=1e-3, D=None, res_hist=None):
+        """Returns (match results, merged model x, lambda). images: FP32, or
+        16-bit photon counts (int16 read as unsigned, or uint16)."""
+        self.set_mask(D)
+        if self.group is None and res_hist is None:
+            self.set_orientations(quats, q_lab)
+            self.plan._grid(A, "A")
+            t = self._images(images)
+            n = images.shape[0]
+            best = self._best[:n]
+            lam = C.c_double()
+            check(lib.spf_mtip_iteration(self._h, _ptr(A), _ptr(images), t, n, C.c_float(img_scale), int(cg_iters),
+                                         float(lam_rel), _ptr(best), _ptr(self.x), C.byref(lam),
+                                         _stream(self.device)))
+            return {"best": best}, self.x, lam.value
+        res = self.match(A, quats, q_lab, images, img_scale)
+        x, lam = self.solve(A, quats, q_lab, images, img_scale, res["best"], cg_iters, lam_rel, D, res_hist)
         return res, x, lam
 
+    def iteration_host(self, A_host, images_host, img_scale, cg_iters, lam_rel=1e-3, best_out=None, x_out=None):
+        """The iteration from host buffers (page-locked for overlap): the
+        inputs are copied on the driver's copy stream while the previous call
+        computes; best_out (int32, n) and x_out (float32, N^3) are host tensors
+        written when the current stream reaches the end of this call's work.
+        Returns (best_out, x_out, lambda)."""
+        if self.host_images is None:
+            raise ValueError("construct the driver with host_images='f32' or 'u16' for host-buffer iterations")
+        want = torch.float32 if self.host_images == "f32" else None
+        if A_host.device.type != "cpu" or images_host.device.type != "cpu":
+            raise ValueError("iteration_host takes host tensors")
+        if (want is not None and images_host.dtype != want) or \
+                (want is None and images_host.dtype not in COUNT_DTYPES):
+            raise TypeError(f"images_host must be {self.host_images}")
+        if A_host.dtype != torch.float32 or tuple(A_host.shape) != (self.N,) * 3 or not A_host.is_contiguous():
+            raise ValueError(f"A_host must be a contiguous float32 ({self.N},)*3 host tensor")
+        if not images_host.is_contiguous() or images_host.dim() != 2 or images_host.shape[1] != self.P2:
+            raise ValueError(f"images_host must be a contiguous (n, {self.P2}) host tensor")
+        n = images_host.shape[0]
+        if best_out is None:
+            best_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        if x_out is None:
+            x_out = torch.empty((self.N,) * 3, dtype=torch.float32, pin_memory=True)
+        lam = C.c_double()
+        t = SPF_IMAGES_F32 if self.host_images == "f32" else SPF_IMAGES_U16
+        check(lib.spf_mtip_iteration_host(self._h, _ptr(A_host), _ptr(images_host), t, n, C.c_float(img_scale),
+                                          int(cg_iters), float(lam_rel), _ptr(best_out), _ptr(x_out),
+                                          C.byref(lam), _stream(self.device)))
+        return best_out, x_out, lam.value
+
+    def status(self):
+        check(lib.spf_mtip_status(self._h))
+
     def close(self):
-        if self.sets:
-            for _, s in self.sets:
-                s.close()
-        self.matcher.close()
-        self.plan.close()
+        if getattr(self, "_h", None):
+            lib.spf_mtip_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

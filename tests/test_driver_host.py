@@ -35,3 +35,25 @@ def test_counts_binding_rejects_wrong_inputs(pkg):
         pkg.counts_to_f32(torch.zeros(8, dtype=torch.float32))
     with pytest.raises(ValueError):
         pkg.counts_to_f32(torch.zeros(8, dtype=torch.int16))   # host tensor
+
+
+def test_lcurve_corner_matches_the_oracle(pkg):
+    """The library's L-curve corner (host arithmetic behind the C ABI) picks
+    the oracle's maximum-curvature point on uneven lambda grids, and its
+    curvature values agree with the oracle's formula."""
+    from oracle import lcurve as olc
+    from paper_2109_05339_gb300.lcurve import corner
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        n = int(rng.integers(3, 15))
+        lams = np.sort(rng.uniform(-4, 2, n))
+        lams = 10.0 ** np.unique(lams)
+        if lams.shape[0] < 3:
+            continue
+        t = np.log(lams)
+        res2 = np.exp(2 * (0.3 * t + 0.2 * np.tanh(t) + 0.05 * rng.standard_normal(t.shape[0])))
+        reg2 = np.exp(2 * (-0.8 * t - 0.3 * np.tanh(2 * t)))
+        idx, kappa = corner(lams, res2, reg2)
+        assert idx == olc.corner(lams, res2, reg2)
+        np.testing.assert_allclose(kappa, olc.curvature(lams, res2, reg2), rtol=1e-10, atol=1e-12)
+

@@ -57,6 +57,30 @@ def test_chunks_accumulate_to_whole(c1_merge):
     assert rel_l2(kh.cpu().numpy(), c["khat"].cpu().numpy()) < 1e-6
 
 
+def test_deferred_merge_over_chunks_equals_one_call(c1_merge):
+    """Chunks spread onto one open merge and transformed once give the
+    single-call merge of all images; calls that would overwrite the fine
+    grids are refused while the merge is open."""
+    import torch
+    from paper_2109_05339_gb300 import SpfError
+    c = c1_merge
+    plan = c["plan"]
+    plan.merge_begin()
+    for c0, c1 in [(0, 33), (33, 34), (34, 100)]:
+        plan.merge_images_add(to_dev(c["images"][c0:c1]), to_dev(c["quats"]), to_dev(c["qlab"]), D=to_dev(c["D"]),
+                              b_scale=float(c["b_scale"]), orient_idx=to_dev(c["best"][c0:c1], torch.int32))
+    with pytest.raises(SpfError, match="deferred merge is open"):
+        plan.slice_model(to_dev(np.zeros((c["N"],) * 3, np.float32)), to_dev(c["quats"]), to_dev(c["qlab"]))
+    rhs = torch.empty_like(c["rhs"])
+    kh = torch.empty_like(c["khat"])
+    plan.merge_finish(rhs, kh)
+    plan.status()
+    assert rel_l2(rhs.cpu().numpy(), c["rhs"].cpu().numpy()) < 1e-6
+    assert rel_l2(kh.cpu().numpy(), c["khat"].cpu().numpy()) < 1e-6
+    with pytest.raises(SpfError, match="no deferred merge"):
+        plan.merge_finish(rhs, kh)
+
+
 def test_toeplitz_operator(c1_merge):
     c = c1_merge
     N = c["N"]
@@ -125,11 +149,13 @@ def test_toeplitz_and_cg_at_generic_fft_sides():
 
 @pytest.mark.parametrize("N,PT", [(35, 72), (101, 216)])
 def test_real_input_toeplitz_apply_and_cg(N, PT):
-    """Precompiled cube sides: the Toeplitz apply runs as real-input row
-    transforms (two rows per complex line), half-spectrum y and z passes with
-    the kernel product inside the z pass, and the inverse row transforms.
-    Checked against the oracle's complex convolution with the same kernel,
-    then three CG steps against the oracle's CG."""
+    """Precompiled cube sides: the right-hand side and the kernel spectrum
+    (real-input type-1 transforms) against the oracle's merge; the Toeplitz
+    apply -- real-input row transforms (two rows per complex line),
+    half-spectrum y and z passes with the kernel product inside the z pass,
+    and the inverse row transforms -- against the oracle's complex
+    convolution with the oracle's kernel; three CG steps on the oracle's
+    right-hand side and kernel against the oracle's CG."""
     import torch
     from paper_2109_05339_gb300 import Plan
     pb = problem("c1")
@@ -144,15 +170,21 @@ def test_real_input_toeplitz_apply_and_cg(N, PT):
     images = rng.poisson(20.0, (quats.shape[0], qlab.shape[0])).astype(np.float32)
     rhs, khat = plan.merge_images(to_dev(images), to_dev(quats), to_dev(qlab), b_scale=0.01)
     plan.status()
-    kh = khat.cpu().numpy().astype(np.float64)
+    t = rotation.nufft_points(f32(quats), f32(qlab), N, 1.0).reshape(-1, 3)
+    ones = np.ones(t.shape[0])
+    ref_rhs = merge.rhs(f32(images).reshape(-1) * 0.01, t, ones, N)
+    ref_khat = merge.kernel_hat(merge.toeplitz_kernel(t, ones, N), N)
+    assert rel_l2(rhs.cpu().numpy(), ref_rhs) < 1e-5
+    assert rel_l2(khat.cpu().numpy(), ref_khat) < 1e-5
     lam = 1e-3 * float(images.size)
     x0 = (rng.standard_normal((N, N, N)) * 0.01).astype(np.float32)
-    y = plan.toeplitz_apply(khat, lam, to_dev(x0)).cpu().numpy()
-    assert rel_l2(y, merge.apply_toeplitz(f32(x0), kh, N, lam)) < 1e-5
+    kh32 = f32(ref_khat.astype(np.float32))
+    y = plan.toeplitz_apply(to_dev(kh32), lam, to_dev(x0)).cpu().numpy()
+    assert rel_l2(y, merge.apply_toeplitz(f32(x0), kh32, N, lam)) < 1e-5
     hist = torch.zeros(4, dtype=torch.float64, device="cuda")
-    x = plan.cg_solve(khat, lam, rhs, to_dev(x0), 3, res_hist=hist).cpu().numpy()
-    b = f32(rhs.cpu().numpy()) + lam * f32(x0)
-    xr, hr = merge.cg(lambda v: merge.apply_toeplitz(v, kh, N, lam), b, f32(x0), 3)
+    rhs32 = f32(ref_rhs.astype(np.float32))
+    x = plan.cg_solve(to_dev(kh32), lam, to_dev(rhs32), to_dev(x0), 3, res_hist=hist).cpu().numpy()
+    xr, hr = merge.cg(lambda v: merge.apply_toeplitz(v, kh32, N, lam), rhs32 + lam * f32(x0), f32(x0), 3)
     assert rel_l2(x, xr) < 1e-4
     np.testing.assert_allclose(hist.cpu().numpy(), hr, rtol=1e-4)
     plan.close()

@@ -43,9 +43,43 @@ def test_iteration_matches_oracle(c1, cache, chunk):
     assert ok.sum() >= n // 2
     np.testing.assert_array_equal(res["best"].cpu().numpy()[ok], m["best"][ok])
     assert abs(lam - ref["lam"]) <= 1e-9 * ref["lam"]
+    # the merged volume, always compared: merge and solve at the oracle's
+    # argmins (images below the margin may legitimately match elsewhere)
+    x2, lam2 = drv.solve(to_dev(pb.A.astype(np.float32)), to_dev(pb.quats.astype(np.float32)),
+                         to_dev(pb.q_lab.astype(np.float32)), to_dev(counts.astype(np.float32)), 1.0 / s,
+                         torch.as_tensor(m["best"], dtype=torch.int32, device="cuda"), cg_iters=3)
+    torch.cuda.synchronize()
+    drv.plan.status()
+    assert lam2 == lam
+    assert rel_l2(x2.cpu().numpy(), ref["x"]) < 1e-5
     if np.all(res["best"].cpu().numpy() == m["best"]):
         assert rel_l2(x.cpu().numpy(), ref["x"]) < 1e-5
     drv.close()
+
+
+def test_orientation_set_rewritten_in_place_is_taken_again(c1):
+    """A caller who rewrites the quaternion tensor in place gets slices of the
+    new orientations: the driver keys its sorted point sets on the tensor's
+    in-place version, not only on its address."""
+    import torch
+    from paper_2109_05339_gb300 import MTIP
+    pb, counts, s, ref = c1
+    N, P2, M, n = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0], counts.shape[0]
+    drv = MTIP(N, 1.0, P2, n, M, cache_points=True)
+    A = to_dev(pb.A.astype(np.float32))
+    q = to_dev(pb.quats.astype(np.float32))
+    ql = to_dev(pb.q_lab.astype(np.float32))
+    imgs = to_dev(counts.astype(np.float32))
+    drv.iteration(A, q, ql, imgs, 1.0 / s, cg_iters=1)
+    q.copy_(q.flip(0))                                  # same storage, new contents
+    res, _, _ = drv.iteration(A, q, ql, imgs, 1.0 / s, cg_iters=1)
+    torch.cuda.synchronize()
+    fresh = MTIP(N, 1.0, P2, n, M, cache_points=True)
+    res2, _, _ = fresh.iteration(A, q.clone(), ql, imgs, 1.0 / s, cg_iters=1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(res["best"].cpu().numpy(), res2["best"].cpu().numpy())
+    drv.close()
+    fresh.close()
 
 
 def test_iteration_with_a_process_group_equals_without(c1):

@@ -1,8 +1,9 @@
 """The allocation-free matching entry point gives the regular matcher's results.
 
-Some callers cannot allocate device memory when they match: code running while
-its stream is captured into a CUDA graph, or code inside a framework that owns
-the device memory pool. For them the library offers
+Some callers cannot allocate device memory when they match: code inside a host
+framework that owns the device memory pool and forbids allocations beside it,
+or a real-time acquisition loop that must not touch the allocator (its calls
+can block and synchronise the device). For them the library offers
 spf_match_orientations_static, whose scratch is a static device array instead
 of cudaMalloc'd buffers. This test calls it through the C ABI twice in a row
 (different sizes, so leftovers of the first call would show in the second)
@@ -49,11 +50,15 @@ def test_static_scratch_matching_equals_matcher():
 
 
 def test_static_scratch_rejects_sizes_beyond_its_limit():
+    """Sizes above the array's limit are refused with a message naming the
+    limit. The buffers are NULL: the call must fail on the size, and were the
+    size check ever lost, the NULL-pointer check would still refuse the call
+    (with another message, failing this test) before any kernel could run."""
     from paper_2109_05339_gb300 import _lib
     L = _lib.lib
-    z = C.c_void_p(16)  # never dereferenced: the size check comes first
-    assert L.spf_match_orientations_static(z, 1025, C.c_float(1.0), z, 10, 64, z, z, z, None) \
-        == _lib.SPF_ERR_ARG
-    assert b"1024" in L.spf_last_error_string()
-    assert L.spf_match_orientations_static(z, 10, C.c_float(1.0), z, 65537, 64, z, z, z, None) \
-        == _lib.SPF_ERR_ARG
+    assert L.spf_match_orientations_static(None, 1025, C.c_float(1.0), None, 10, 64, None, None, None,
+                                           None) == _lib.SPF_ERR_ARG
+    assert b"limit of 1024" in L.spf_last_error_string()
+    assert L.spf_match_orientations_static(None, 10, C.c_float(1.0), None, 65537, 64, None, None, None,
+                                           None) == _lib.SPF_ERR_ARG
+    assert b"limit of 65536" in L.spf_last_error_string()
