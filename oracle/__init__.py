@@ -23,6 +23,8 @@ What it computes (arXiv 2109.05339, Sec. II):
                    A*DA (Sec. II-C, the "type-1 with ones" kernel) and the direct
                    form, and a textbook conjugate gradient.
 * ``mtip``      -- one slice -> match -> merge -> CG iteration on a sample.
+* ``phasing``   -- error reduction, hybrid input-output and shrinkwrap on the
+                   model's grid (Sec. II-D), with exact DFTs.
 
 Parity status of each function is stated in its module header.
 """
