@@ -435,6 +435,51 @@ int spf_mtip_iteration_host(spf_mtip* h, const float* A_host, const void* images
                             double* lambda_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Phasing, Sec. II-D: from the merged diffraction volume to a density by
+ * error reduction (ER), hybrid input-output (HIO) and shrinkwrap, the
+ * published methods the paper combines, on the model's N^3 grid (N odd,
+ * 3..401; layout as the model). Transforms are exact DFTs:
+ *   forward rho^_m = sum_n rho_n exp(-2 pi i m.n / N),
+ *   inverse rho_n  = N^-3 sum_m rho^_m exp(+2 pi i m.n / N).
+ * Data: magnitudes amp_m (amp < 0: a mode without data, left free).
+ *   P_M rho: rho^ -> amp rho^ / |rho^| on modes with data (amp where
+ *            rho^ = 0), back to real space (real part).
+ *   ER:  rho' = P_M rho where (support and, with positivity, P_M rho > 0),
+ *        else 0.
+ *   HIO: the same where kept, else rho - beta P_M rho.
+ *   Fourier error of an iterate: sqrt(sum_data (|rho^| - amp)^2 / sum_data amp^2).
+ *   Shrinkwrap: support = blur > threshold * max(blur), blur = |rho|
+ *        circularly convolved with the normalised Gaussian of width sigma
+ *        voxels over the minimal periodic offsets {-M..M}^3.
+ * spf_phaser_create allocates the iterate, support (initially all ones),
+ *   magnitudes, work cube and scratch (about 30 bytes per voxel).
+ * spf_phaser_set_amplitudes copies amp (N^3 floats, device);
+ * spf_phaser_amplitudes_from_model sets amp = sqrt(max(Re forward(x), 0))
+ *   from a merged autocorrelation x (N^3 floats, device): every mode has data.
+ * spf_phaser_set_state copies the iterate rho (N^3 floats) and / or the
+ *   support (N^3 bytes, nonzero = inside); either may be NULL.
+ * spf_phaser_iterate: `iters` steps of SPF_PHASE_ER or SPF_PHASE_HIO (beta
+ *   used by HIO), positivity 0 / 1; errors (device, iters doubles, may be
+ *   NULL) receives the Fourier error of each iterate before its step.
+ * spf_phaser_shrinkwrap updates the support from the current iterate.
+ * spf_phaser_get copies the iterate, support and magnitudes out (each
+ *   device pointer may be NULL).
+ * All stream-ordered; FP32 transforms, FP64 error sums.
+ * ------------------------------------------------------------------------- */
+#define SPF_PHASE_ER 0
+#define SPF_PHASE_HIO 1
+typedef struct spf_phaser spf_phaser;
+int spf_phaser_create(spf_phaser** out, int N, int device);
+int spf_phaser_destroy(spf_phaser* ph);
+int spf_phaser_set_amplitudes(spf_phaser* ph, const float* amp, void* stream);
+int spf_phaser_amplitudes_from_model(spf_phaser* ph, const float* x, void* stream);
+int spf_phaser_set_state(spf_phaser* ph, const float* rho, const uint8_t* support, void* stream);
+int spf_phaser_iterate(spf_phaser* ph, int method, int iters, float beta, int positivity, double* errors,
+                       void* stream);
+int spf_phaser_shrinkwrap(spf_phaser* ph, float sigma, float threshold, void* stream);
+int spf_phaser_get(spf_phaser* ph, float* rho, uint8_t* support, float* amp, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Photon-count images (no counterpart in the paper's equations; its images
  * are photon counts). Moving frames as 16-bit counts halves the
  * host-to-device bytes of FP32 images; the FP32 copy the other calls take is

@@ -12,7 +12,7 @@ import importlib
 
 _EXPORTS = {
     "Plan": "api", "PointSet": "api", "Matcher": "api", "SliceModel": "api", "slice_model": "api",
-    "SpfError": "api", "PRECISIONS": "api", "counts_to_f32": "api", "MTIP": "mtip",
+    "SpfError": "api", "PRECISIONS": "api", "counts_to_f32": "api", "MTIP": "mtip", "Phaser": "phasing",
 }
 
 

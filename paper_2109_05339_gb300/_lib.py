@@ -19,6 +19,7 @@ SPF_ERR_TIMEOUT = -4
 SPF_ERR_UNSUPPORTED = -5
 SPF_FP32, SPF_BF16, SPF_FP8 = 0, 1, 2
 SPF_IMAGES_F32, SPF_IMAGES_U16 = 0, 1
+SPF_PHASE_ER, SPF_PHASE_HIO = 0, 1
 
 _CODES = {SPF_ERR_ARG: "SPF_ERR_ARG", SPF_ERR_OOM: "SPF_ERR_OOM", SPF_ERR_CUDA: "SPF_ERR_CUDA",
           SPF_ERR_TIMEOUT: "SPF_ERR_TIMEOUT", SPF_ERR_UNSUPPORTED: "SPF_ERR_UNSUPPORTED"}
@@ -86,6 +87,14 @@ PROTOTYPES = {
     "spf_match_orientations_static": (I, [P, I, F, P, I, I, P, P, P, P]),
     "spf_counts_to_f32": (I, [P, I64, P, P]),
     "spf_morton_order": (I, [P, I, P]),
+    "spf_phaser_create": (I, [C.POINTER(P), I, I]),
+    "spf_phaser_destroy": (I, [P]),
+    "spf_phaser_set_amplitudes": (I, [P, P, P]),
+    "spf_phaser_amplitudes_from_model": (I, [P, P, P]),
+    "spf_phaser_set_state": (I, [P, P, P, P]),
+    "spf_phaser_iterate": (I, [P, I, I, F, I, P, P]),
+    "spf_phaser_shrinkwrap": (I, [P, F, F, P]),
+    "spf_phaser_get": (I, [P, P, P, P, P]),
     "spf_mtip_create": (I, [C.POINTER(P), C.POINTER(MtipConfig)]),
     "spf_mtip_destroy": (I, [P]),
     "spf_mtip_info": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
