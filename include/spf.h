@@ -311,6 +311,19 @@ int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient,
  * (concurrent CTAs share operand tiles; the model's choice for many image
  * tiles). The results differ only in which approximate candidates tie. */
 int spf_matcher_set_schedule(spf_matcher* m, int schedule);
+/* When the exact re-rank runs (host; set before spf_matcher_set_images).
+ * deferred = 0 (default): each add_slices call re-ranks its own best
+ * candidates, so its slices are needed only until its work completes.
+ * deferred = 1: every call merges its candidates into a running approximate
+ * top-8 per image, and the exact FP32 re-rank of that list runs once, in
+ * spf_matcher_results, reading each image once. The slices of every
+ * add_slices call since set_images must then stay valid and unchanged until
+ * spf_matcher_results; calls must cover increasing, non-overlapping
+ * orientation ranges (at most 1024 of them). The re-ranked candidates are
+ * the best 8 by approximate distance over all chunks, instead of the best 8
+ * of each chunk. spf_matcher_results synchronises the stream once (the
+ * chunk table is uploaded from the host). */
+int spf_matcher_set_rerank(spf_matcher* m, int deferred);
 int spf_matcher_results(spf_matcher* m, int32_t* best_idx, float* best_d, float* second_d,
                         int32_t* topk_idx, float* topk_d, void* stream);
 
@@ -388,7 +401,8 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
  * spf_mtip_status: the plan's, the matcher's and the driver's error words
  *   (waits for the device). spf_mtip_plan / spf_mtip_matcher: the driver's
  *   plan and matcher (owned by the driver) for the other calls of this header.
- * spf_mtip_info: whether point sets are kept, and the chunk sizes in use.
+ * spf_mtip_info: whether point sets are kept, the chunk sizes in use, and
+ *   whether all slices are kept (one deferred re-rank per iteration).
  * ------------------------------------------------------------------------- */
 #define SPF_IMAGES_F32 0
 #define SPF_IMAGES_U16 1
@@ -408,6 +422,7 @@ typedef struct spf_mtip_config {
   int64_t point_budget_bytes;
   int host_image_type;
   int device;
+  int keep_slices;
 } spf_mtip_config;
 /* The driver's renumbering of an orientation set (host; no device work):
  * order_host[i] = the caller's index of driver index i, the permutation that
@@ -416,7 +431,7 @@ typedef struct spf_mtip_config {
 int spf_morton_order(const float* quats_host, int M, int32_t* order_host);
 int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg);
 int spf_mtip_destroy(spf_mtip* h);
-int spf_mtip_info(const spf_mtip* h, int* cache_points, int* orient_chunk, int* img_chunk);
+int spf_mtip_info(const spf_mtip* h, int* cache_points, int* orient_chunk, int* img_chunk, int* keep_slices);
 spf_plan* spf_mtip_plan(spf_mtip* h);
 spf_matcher* spf_mtip_matcher(spf_mtip* h);
 int spf_mtip_status(spf_mtip* h);

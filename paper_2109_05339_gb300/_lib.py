@@ -42,7 +42,8 @@ class MtipConfig(C.Structure):
     _fields_ = [("N", C.c_int), ("qmax", C.c_double), ("eps", C.c_double), ("P2", C.c_int),
                 ("max_images", C.c_int), ("n_orient", C.c_int), ("orient_chunk", C.c_int),
                 ("img_chunk", C.c_int), ("precision", C.c_int), ("topk", C.c_int), ("cache_points", C.c_int),
-                ("point_budget_bytes", C.c_int64), ("host_image_type", C.c_int), ("device", C.c_int)]
+                ("point_budget_bytes", C.c_int64), ("host_image_type", C.c_int), ("device", C.c_int),
+                ("keep_slices", C.c_int)]
 
 
 # name: (restype, argtypes)
@@ -82,6 +83,7 @@ PROTOTYPES = {
     "spf_matcher_set_mask": (I, [P, P, P]),
     "spf_matcher_add_slices": (I, [P, P, I, I, P]),
     "spf_matcher_set_schedule": (I, [P, I]),
+    "spf_matcher_set_rerank": (I, [P, I]),
     "spf_matcher_results": (I, [P, P, P, P, P, P, P]),
     "spf_match_orientations": (I, [P, P, I, F, P, I, P, P, P, P]),
     "spf_match_orientations_static": (I, [P, I, F, P, I, I, P, P, P, P]),
@@ -97,7 +99,7 @@ PROTOTYPES = {
     "spf_phaser_get": (I, [P, P, P, P, P]),
     "spf_mtip_create": (I, [C.POINTER(P), C.POINTER(MtipConfig)]),
     "spf_mtip_destroy": (I, [P]),
-    "spf_mtip_info": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+    "spf_mtip_info": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
     "spf_mtip_plan": (P, [P]),
     "spf_mtip_matcher": (P, [P]),
     "spf_mtip_status": (I, [P]),

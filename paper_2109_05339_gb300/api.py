@@ -407,6 +407,12 @@ class Matcher:
         """Tile schedule of the tensor-core cross term: "auto", "contiguous" or "grid"."""
         check(lib.spf_matcher_set_schedule(self._h, {"auto": 0, "contiguous": 1, "grid": 2}[schedule]))
 
+    def set_rerank(self, deferred=False):
+        """Re-rank per add_slices call (False) or once, at results, over the
+        running approximate top-8 of all chunks (True: every chunk's slices must
+        stay valid until results)."""
+        check(lib.spf_matcher_set_rerank(self._h, int(bool(deferred))))
+
     def set_images(self, images, img_scale=1.0):
         _f32(images, "images", self.device)
         if images.dim() != 2 or images.shape[1] != self.P2:

@@ -455,6 +455,10 @@ static void matcher_free(spf_matcher* m) {
   cudaFree(m->rr_key);
   cudaFree(m->rr_start);
   cudaFree(m->rr_order);
+  cudaFree(m->ap_v);
+  cudaFree(m->ap_i);
+  cudaFree(m->ch_off_d);
+  cudaFree(m->ch_ptr_d);
   delete m;
 }
 
@@ -492,6 +496,10 @@ int spf_matcher_create(spf_matcher** out, int max_images, int max_orient_chunk, 
   A((void**)&m->rr_key, sizeof(int) * std::max(max_images, 1), "re-rank keys");
   A((void**)&m->rr_start, sizeof(int) * ((size_t)max_orient_chunk + 1), "re-rank buckets");
   A((void**)&m->rr_order, sizeof(int) * std::max(max_images, 1), "re-rank order");
+  A((void**)&m->ap_v, sizeof(float) * (size_t)std::max(max_images, 1) * kCand, "approximate candidates");
+  A((void**)&m->ap_i, sizeof(int) * (size_t)std::max(max_images, 1) * kCand, "approximate candidates");
+  A((void**)&m->ch_off_d, sizeof(int) * (kMaxChunks + 1), "re-rank chunk offsets");
+  A((void**)&m->ch_ptr_d, sizeof(float*) * kMaxChunks, "re-rank chunk rows");
   if (rc == SPF_OK && precision != SPF_FP32) {
     if (!match_tc_supported(device)) {
       set_error("tensor-core matching needs an sm_103 device");
@@ -559,6 +567,15 @@ int spf_matcher_set_mask(spf_matcher* m, const float* D, void* stream) {
   DeviceScope dev(m->device);
   if (dev.rc != SPF_OK) return dev.rc;
   return set_mask_weights(m, D, as_stream(stream));
+}
+
+int spf_matcher_set_rerank(spf_matcher* m, int deferred) {
+  clear_error();
+  SPF_CHECK_ARG(m != nullptr, "matcher is NULL");
+  SPF_CHECK_ARG(deferred == 0 || deferred == 1, "deferred must be 0 or 1");
+  SPF_CHECK_ARG(!m->pending, "a deferred re-rank is pending: read the results first");
+  m->defer = deferred;
+  return SPF_OK;
 }
 
 int spf_matcher_set_schedule(spf_matcher* m, int schedule) {

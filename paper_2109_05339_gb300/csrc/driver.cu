@@ -101,6 +101,7 @@ struct spf_mtip {
   spf_plan* plan = nullptr;
   spf_matcher* matcher = nullptr;
   bool cache_points = false;
+  bool keep_slices = false;        // slices of all chunks kept: one deferred re-rank
   int orient_chunk = 0, img_chunk = 0;
   // orientation set in the driver's numbering
   bool have_set = false;
@@ -110,7 +111,7 @@ struct spf_mtip {
   int* inv = nullptr;              // caller index -> driver index
   std::vector<spf_points*> sets;   // kept point sets, one per orientation chunk
   spf_points stream_set;           // streaming: one slice-only set, re-sorted per chunk
-  float* slices = nullptr;         // orient_chunk x P2
+  float* slices = nullptr;         // orient_chunk x P2, or n_orient x P2 when kept
   float* img32 = nullptr;          // max_images x P2: 16-bit counts converted to FP32
   int* best_sorted = nullptr;      // max_images
   int* best = nullptr;             // max_images (caller numbering)
@@ -206,16 +207,17 @@ int match_core(spf_mtip* h, const float* A, const float* img, int n_img, float i
   SPF_TRY(spf_matcher_set_images(h->matcher, img, n_img, img_scale, s));
   for (int c = 0, c0 = 0; c0 < M; ++c, c0 += h->orient_chunk) {
     const int m = std::min(h->orient_chunk, M - c0);
+    float* out = h->keep_slices ? h->slices + (size_t)c0 * P2 : h->slices;
     if (h->cache_points) {
-      SPF_TRY(slice_points(P, h->sets[c], A, h->slices, s));
+      SPF_TRY(slice_points(P, h->sets[c], A, out, s));
     } else {
       spf_points& S = h->stream_set;
       S.M = m;
       S.quats = h->quats_sorted + 4 * (size_t)c0;
       SPF_TRY(points_build(P, &S, s));
-      SPF_TRY(slice_points(P, &S, A, h->slices, s));
+      SPF_TRY(slice_points(P, &S, A, out, s));
     }
-    SPF_TRY(spf_matcher_add_slices(h->matcher, h->slices, m, c0, s));
+    SPF_TRY(spf_matcher_add_slices(h->matcher, out, m, c0, s));
   }
   return SPF_OK;
 }
@@ -280,6 +282,7 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
   SPF_CHECK_ARG(c.orient_chunk >= 0 && c.img_chunk >= 0, "chunk sizes must be >= 0 (0: all at once)");
   SPF_CHECK_ARG(c.cache_points >= -1 && c.cache_points <= 1, "cache_points must be -1, 0 or 1");
   SPF_CHECK_ARG(c.host_image_type >= -1 && c.host_image_type <= SPF_IMAGES_U16, "unknown host image type");
+  SPF_CHECK_ARG(c.keep_slices >= -1 && c.keep_slices <= 1, "keep_slices must be -1, 0 or 1");
   const int chunk = std::min(c.n_orient, c.orient_chunk > 0 ? c.orient_chunk : c.n_orient);
   SPF_CHECK_ARG((int64_t)chunk * c.P2 < 0x7fffffffLL, "orient_chunk x P2 must be < 2^31");
   DevScope dev(c.device);
@@ -299,6 +302,13 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
     }
     h->cache_points = kPointSetBytes * (int64_t)c.n_orient * P2 <= budget;
   }
+  if (c.keep_slices >= 0) {
+    h->keep_slices = c.keep_slices == 1;
+  } else {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+    h->keep_slices = (double)c.n_orient * P2 * sizeof(float) <= 0.25 * (double)fr;
+  }
   const int64_t cap = (0x7fffffffLL) / P2;
   h->img_chunk = (int)std::min<int64_t>({(int64_t)c.max_images, c.img_chunk > 0 ? c.img_chunk : c.max_images, cap});
   int64_t max_pts = (int64_t)h->orient_chunk * P2;
@@ -315,7 +325,9 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
   A((void**)&h->qlab, sizeof(float) * 3 * (size_t)P2, "driver detector");
   A((void**)&h->order, sizeof(int) * (size_t)c.n_orient, "orientation order");
   A((void**)&h->inv, sizeof(int) * (size_t)c.n_orient, "inverse orientation order");
-  A((void**)&h->slices, sizeof(float) * (size_t)h->orient_chunk * P2, "slice chunk");
+  A((void**)&h->slices, sizeof(float) * (size_t)(h->keep_slices ? c.n_orient : h->orient_chunk) * P2,
+    h->keep_slices ? "slices of all chunks" : "slice chunk");
+  if (rc == SPF_OK) rc = spf_matcher_set_rerank(h->matcher, h->keep_slices ? 1 : 0);
   A((void**)&h->img32, sizeof(float) * (size_t)c.max_images * P2, "FP32 images");
   A((void**)&h->best_sorted, sizeof(int) * (size_t)c.max_images, "matches (driver numbering)");
   A((void**)&h->best, sizeof(int) * (size_t)c.max_images, "matches");
@@ -379,9 +391,10 @@ int spf_mtip_destroy(spf_mtip* h) {
   return SPF_OK;
 }
 
-int spf_mtip_info(const spf_mtip* h, int* cache_points, int* orient_chunk, int* img_chunk) {
+int spf_mtip_info(const spf_mtip* h, int* cache_points, int* orient_chunk, int* img_chunk, int* keep_slices) {
   clear_error();
   SPF_TRY(check_handle(h, false));
+  if (keep_slices) *keep_slices = h->keep_slices ? 1 : 0;
   if (cache_points) *cache_points = h->cache_points ? 1 : 0;
   if (orient_chunk) *orient_chunk = h->orient_chunk;
   if (img_chunk) *img_chunk = h->img_chunk;

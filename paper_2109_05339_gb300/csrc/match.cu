@@ -269,15 +269,17 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
 // ------------------------------------------------------------ rerank -----
 // Re-rank order: images bucketed by the orientation of their best
 // approximate candidate (counting sort; bucket n_orient: no candidate).
+// Candidates of image i: `ncand` entries from i * stride; key = (best index -
+// key_off) / key_div, bucket nkeys when there is none.
 __global__ void rr_key_kernel(const float* __restrict__ cand_v, const int* __restrict__ cand_i, int n_img,
-                              int nsplit, int orient_offset, int n_orient, int* __restrict__ key,
-                              int* __restrict__ count) {
+                              int stride, int ncand, int key_off, int key_div, int n_orient,
+                              int* __restrict__ key, int* __restrict__ count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_img) return;
-  const size_t base = (size_t)i * kMaxSplits * kCand;
+  const size_t base = (size_t)i * stride;
   float bv = FLT_MAX;
   int bj = -1;
-  for (int q = 0; q < nsplit * kCand; ++q) {
+  for (int q = 0; q < ncand; ++q) {
     const int j = __ldg(cand_i + base + q);
     const float v = __ldg(cand_v + base + q);
     if (j >= 0 && (v < bv || (v == bv && j < bj))) {
@@ -285,7 +287,7 @@ __global__ void rr_key_kernel(const float* __restrict__ cand_v, const int* __res
       bj = j;
     }
   }
-  int k = bj >= 0 ? bj - orient_offset : n_orient;
+  int k = bj >= 0 ? (bj - key_off) / key_div : n_orient;
   if (k < 0 || k > n_orient) k = n_orient;
   key[i] = k;
   atomicAdd(count + k, 1);
@@ -336,15 +338,35 @@ __global__ void rr_scatter_kernel(const int* __restrict__ key, int n_img, int* _
 
 // One CTA per image: merge nsplit candidate lists, take the best topk by
 // approximate score, recompute them exactly, merge into the running list.
+// Rows of model images: one block Y of rows [orient_offset, ...) or, with
+// nch > 0, the blocks ch_ptr[c] holding rows [ch_off[c], ch_off[c + 1]).
+struct RowTable {
+  const float* Y;
+  int orient_offset;
+  const int* ch_off;
+  const float* const* ch_ptr;
+  int nch;
+  __device__ __forceinline__ const float* row(int j, int P2) const {
+    if (nch == 0) return Y + (size_t)(j - orient_offset) * P2;
+    int lo = 0, hi = nch - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(ch_off + mid) <= j) lo = mid;
+      else hi = mid - 1;
+    }
+    return ch_ptr[lo] + (size_t)(j - __ldg(ch_off + lo)) * P2;
+  }
+};
+
 template <int K>
 __global__ void __launch_bounds__(256)
-rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict__ Y, int P2,
-              int orient_offset, int n_orient, int nsplit, const float* __restrict__ cand_v,
-              const int* __restrict__ cand_i, const float* __restrict__ wsq, float* __restrict__ st_d,
-              int* __restrict__ st_i, const int* __restrict__ order) {
+rerank_kernel(const float* __restrict__ X, float xscale, RowTable rows, int P2, int stride, int ncand,
+              const float* __restrict__ cand_v, const int* __restrict__ cand_i, const float* __restrict__ wsq,
+              float* __restrict__ st_d, int* __restrict__ st_i, const int* __restrict__ order) {
   const int img = order ? __ldg(order + blockIdx.x) : blockIdx.x;
   __shared__ float s_v[K];
   __shared__ int s_i[K];
+  __shared__ const float* s_row[K];
   if (threadIdx.x == 0) {
     float tv[K];
     int ti[K];
@@ -353,12 +375,11 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
       tv[q] = FLT_MAX;
       ti[q] = -1;
     }
-    const size_t base = (size_t)img * kMaxSplits * kCand;
-    for (int s = 0; s < nsplit; ++s)
-      for (int q = 0; q < kCand; ++q) {
-        int j = cand_i[base + s * kCand + q];
-        if (j >= 0) list_insert_ordered<K>(tv, ti, cand_v[base + s * kCand + q], j);
-      }
+    const size_t base = (size_t)img * stride;
+    for (int q = 0; q < ncand; ++q) {
+      int j = cand_i[base + q];
+      if (j >= 0) list_insert_ordered<K>(tv, ti, cand_v[base + q], j);
+    }
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       s_v[q] = tv[q];
@@ -366,15 +387,19 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
     }
   }
   __syncthreads();
+  if (threadIdx.x < K) s_row[threadIdx.x] = s_i[threadIdx.x] >= 0 ? rows.row(s_i[threadIdx.x], P2) : nullptr;
+  __syncthreads();
   // exact FP32 distances of all candidates in one sweep over the pixels
   const float* x = X + (size_t)img * P2;
   const float* y[K];
 #pragma unroll
-  for (int q = 0; q < K; ++q) y[q] = s_i[q] >= 0 ? Y + (size_t)(s_i[q] - orient_offset) * P2 : x;
+  for (int q = 0; q < K; ++q) y[q] = s_row[q] ? s_row[q] : x;
   float acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.f;
-  bool vec = !wsq && (P2 % 4) == 0 && (((uintptr_t)x) & 15) == 0 && (((uintptr_t)Y) & 15) == 0;
+  bool vec = !wsq && (P2 % 4) == 0 && (((uintptr_t)x) & 15) == 0;
+#pragma unroll
+  for (int q = 0; q < K; ++q) vec = vec && (((uintptr_t)y[q]) & 15) == 0;
   if (vec) {
 #pragma unroll 2
     for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
@@ -429,6 +454,31 @@ rerank_kernel(const float* __restrict__ X, float xscale, const float* __restrict
       st_d[(size_t)img * K + q] = tv[q];
       st_i[(size_t)img * K + q] = ti[q];
     }
+  }
+}
+
+// Running approximate top-kCand per image across orientation chunks (deferred
+// re-rank): the nsplit * kCand candidates of this launch merged into ap.
+__global__ void cand_merge_kernel(const float* __restrict__ cand_v, const int* __restrict__ cand_i, int n_img,
+                                  int nsplit, float* __restrict__ ap_v, int* __restrict__ ap_i) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_img) return;
+  float tv[kCand];
+  int ti[kCand];
+#pragma unroll
+  for (int q = 0; q < kCand; ++q) {
+    tv[q] = ap_v[(size_t)i * kCand + q];
+    ti[q] = ap_i[(size_t)i * kCand + q];
+  }
+  const size_t base = (size_t)i * kMaxSplits * kCand;
+  for (int q = 0; q < nsplit * kCand; ++q) {
+    const int j = __ldg(cand_i + base + q);
+    if (j >= 0) list_insert_ordered<kCand>(tv, ti, __ldg(cand_v + base + q), j);
+  }
+#pragma unroll
+  for (int q = 0; q < kCand; ++q) {
+    ap_v[(size_t)i * kCand + q] = tv[q];
+    ap_i[(size_t)i * kCand + q] = ti[q];
   }
 }
 
@@ -489,24 +539,35 @@ int row_norms(const float* src, int rows, int P2, float scale, float* out, cudaS
 }
 
 int state_reset(spf_matcher* m, cudaStream_t s) {
+  m->n_chunks = 0;
+  m->pending = false;
   int n = m->n_img * m->topk;
   if (n == 0) return SPF_OK;
   SPF_TRY(launch("state_reset_kernel", s, [&] { state_reset_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(m->st_d, m->st_i, n); }));
+  if (m->defer) {
+    const int na = m->n_img * kCand;
+    SPF_TRY(launch("state_reset_kernel", s, [&] {
+      state_reset_kernel<<<(unsigned)ceil_div(na, 256), 256, 0, s>>>(m->ap_v, m->ap_i, na);
+    }));
+  }
   return SPF_OK;
 }
 
-int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
-                  cudaStream_t s) {
+// Exact FP32 re-rank of candidate lists (stride and count per image) with
+// model-image rows from `rows`; images visited grouped by their best
+// candidate (bucket = (index - key_off) / key_div, at most max_orient + 1).
+static int rerank_core(spf_matcher* m, const RowTable& rows, const float* cv, const int* ci, int stride,
+                       int ncand, int key_off, int key_div, int nkeys, cudaStream_t s) {
   if (m->n_img == 0) return SPF_OK;
   const int* order = nullptr;
-  if (m->rr_order && n_orient <= m->max_orient) {
+  if (m->rr_order && nkeys <= m->max_orient) {
     const unsigned g = (unsigned)ceil_div(m->n_img, 256);
-    SPF_CUDA(cudaMemsetAsync(m->rr_start, 0, sizeof(int) * ((size_t)n_orient + 1), s));
+    SPF_CUDA(cudaMemsetAsync(m->rr_start, 0, sizeof(int) * ((size_t)nkeys + 1), s));
     SPF_TRY(launch("rr_key_kernel", s, [&] {
-      rr_key_kernel<<<g, 256, 0, s>>>(m->cand_v, m->cand_i, m->n_img, nsplit, orient_offset, n_orient,
-                                      m->rr_key, m->rr_start);
+      rr_key_kernel<<<g, 256, 0, s>>>(cv, ci, m->n_img, stride, ncand, key_off, key_div, nkeys, m->rr_key,
+                                      m->rr_start);
     }));
-    SPF_TRY(launch("rr_scan_kernel", s, [&] { rr_scan_kernel<<<1, 1024, 0, s>>>(m->rr_start, n_orient + 1); }));
+    SPF_TRY(launch("rr_scan_kernel", s, [&] { rr_scan_kernel<<<1, 1024, 0, s>>>(m->rr_start, nkeys + 1); }));
     SPF_TRY(launch("rr_scatter_kernel", s, [&] {
       rr_scatter_kernel<<<g, 256, 0, s>>>(m->rr_key, m->n_img, m->rr_start, m->rr_order);
     }));
@@ -515,9 +576,8 @@ int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_
 #define SPF_RR(K)                                                                               \
   case K:                                                                                       \
     return launch("rerank_kernel", s, [&] {                                                     \
-      rerank_kernel<K><<<m->n_img, 256, 0, s>>>(m->images, m->img_scale, slices, m->P2,         \
-                                                orient_offset, n_orient, nsplit, m->cand_v,     \
-                                                m->cand_i, m->wsq, m->st_d, m->st_i, order);    \
+      rerank_kernel<K><<<m->n_img, 256, 0, s>>>(m->images, m->img_scale, rows, m->P2, stride,   \
+                                                ncand, cv, ci, m->wsq, m->st_d, m->st_i, order); \
     });
   switch (m->topk) {
     SPF_RR(2) SPF_RR(3) SPF_RR(4) SPF_RR(5) SPF_RR(6) SPF_RR(7) SPF_RR(8)
@@ -526,9 +586,47 @@ int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_
 #undef SPF_RR
 }
 
+int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
+                  cudaStream_t s) {
+  if (m->defer) {
+    // keep this launch's best candidates and the rows they point into; the
+    // exact re-rank runs once, when the results are read
+    SPF_CHECK_ARG(m->n_chunks < kMaxChunks, "deferred re-rank: more than %d chunks", kMaxChunks);
+    SPF_CHECK_ARG(m->n_chunks == 0 || orient_offset >= m->ch_off_h[m->n_chunks],
+                  "deferred re-rank: chunks must come in increasing, non-overlapping orientation ranges");
+    m->ch_off_h[m->n_chunks] = orient_offset;
+    m->ch_ptr_h[m->n_chunks] = slices;
+    m->ch_off_h[m->n_chunks + 1] = orient_offset + n_orient;
+    ++m->n_chunks;
+    m->pending = true;
+    return launch("cand_merge_kernel", s, [&] {
+      cand_merge_kernel<<<(unsigned)ceil_div(m->n_img, 256), 256, 0, s>>>(m->cand_v, m->cand_i, m->n_img, nsplit,
+                                                                        m->ap_v, m->ap_i);
+    });
+  }
+  RowTable rows{slices, orient_offset, nullptr, nullptr, 0};
+  return rerank_core(m, rows, m->cand_v, m->cand_i, kMaxSplits * kCand, nsplit * kCand, orient_offset, 1,
+                     n_orient, s);
+}
+
+int rerank_flush(spf_matcher* m, cudaStream_t s) {
+  if (!m->defer || !m->pending) return SPF_OK;
+  m->pending = false;
+  const int n = m->n_chunks;
+  SPF_CUDA(cudaMemcpyAsync(m->ch_off_d, m->ch_off_h, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+  SPF_CUDA(cudaMemcpyAsync(m->ch_ptr_d, m->ch_ptr_h, sizeof(const float*) * n, cudaMemcpyHostToDevice, s));
+  // the host table is read by the copies above: keep it until they are done
+  SPF_CUDA(cudaStreamSynchronize(s));
+  const int lo = m->ch_off_h[0], total = m->ch_off_h[n] - lo;
+  const int div = (int)std::max<int64_t>(1, ceil_div(total, std::max(1, m->max_orient)));
+  RowTable rows{nullptr, 0, m->ch_off_d, m->ch_ptr_d, n};
+  return rerank_core(m, rows, m->ap_v, m->ap_i, kCand, kCand, lo, div, (int)ceil_div(total, div), s);
+}
+
 int results_launch(spf_matcher* m, int32_t* best_idx, float* best_d, float* second_d,
                    int32_t* topk_idx, float* topk_d, cudaStream_t s) {
   if (m->n_img == 0) return SPF_OK;
+  SPF_TRY(rerank_flush(m, s));
   SPF_TRY(launch("results_kernel", s, [&] { results_kernel<<<(unsigned)ceil_div(m->n_img, 256), 256, 0, s>>>(
       m->st_d, m->st_i, m->n_img, m->topk, best_idx, best_d, second_d, topk_idx, topk_d); }));
   return SPF_OK;

@@ -5,6 +5,7 @@
 
 constexpr int kCand = 8;          // approximate candidates kept per (image, split)
 constexpr int kMaxSplits = 64;    // orientation splits of one GEMM launch
+constexpr int kMaxChunks = 1024;  // orientation chunks of one deferred re-rank
 
 struct spf_matcher {
   int device = 0;
@@ -35,6 +36,17 @@ struct spf_matcher {
   int* rr_order = nullptr;        // max_images
   int n_sms = 152;
   int tc_force = 0;               // tensor-core schedule: 0 by the model, 1 contiguous, 2 grid
+  // deferred re-rank: the approximate top-kCand per image is carried across
+  // orientation chunks and re-ranked once, reading rows from every chunk
+  int defer = 0;
+  bool pending = false;
+  float* ap_v = nullptr;          // max_images x kCand running approximate list
+  int* ap_i = nullptr;
+  int n_chunks = 0;
+  int ch_off_h[kMaxChunks + 1];   // chunk c holds orientations [ch_off[c], ch_off[c + 1])
+  const float* ch_ptr_h[kMaxChunks];
+  int* ch_off_d = nullptr;
+  const float** ch_ptr_d = nullptr;
 };
 
 namespace spf {

@@ -56,12 +56,14 @@ def _tensor_key(t):
 class MTIP:
     def __init__(self, N, qmax, P2, n_img, n_orient, orient_chunk=None, img_chunk=None,
                  eps=1e-6, precision="bf16", topk=8, device=None, cache_points=None,
-                 point_budget_bytes=None, process_group=None, host_images=None):
+                 point_budget_bytes=None, process_group=None, host_images=None, keep_slices=None):
         """cache_points: keep every chunk's sorted points (True), stream them
         (False), or decide from point_budget_bytes (None; default budget: half
         of the device's free memory). process_group: the images are one shard
         of a torch.distributed group. host_images: None, "f32" or "u16" --
-        the image type of iteration_host (allocates its two device slots)."""
+        the image type of iteration_host (allocates its two device slots).
+        keep_slices: keep every chunk's slices and re-rank once per iteration
+        (True), re-rank per chunk (False), or decide from free memory (None)."""
         self.group = process_group
         self._n_total = {}
         dev = _dev_index(device)
@@ -72,13 +74,14 @@ class MTIP:
                          topk=int(topk), cache_points=-1 if cache_points is None else int(bool(cache_points)),
                          point_budget_bytes=int(point_budget_bytes or 0),
                          host_image_type={None: -1, "f32": SPF_IMAGES_F32, "u16": SPF_IMAGES_U16}[host_images],
-                         device=dev)
+                         device=dev, keep_slices=-1 if keep_slices is None else int(bool(keep_slices)))
         h = C.c_void_p()
         check(lib.spf_mtip_create(C.byref(h), C.byref(cfg)))
         self._h = h
-        cp, oc, ic = C.c_int(), C.c_int(), C.c_int()
-        check(lib.spf_mtip_info(h, C.byref(cp), C.byref(oc), C.byref(ic)))
+        cp, oc, ic, ks = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(lib.spf_mtip_info(h, C.byref(cp), C.byref(oc), C.byref(ic), C.byref(ks)))
         self.cache_points, self.orient_chunk, self.img_chunk = bool(cp.value), oc.value, ic.value
+        self.keep_slices = bool(ks.value)
         self.device = dev
         self.N, self.P2, self.n_img, self.n_orient, self.topk = int(N), int(P2), int(n_img), int(n_orient), int(topk)
         self.host_images = host_images

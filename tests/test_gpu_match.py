@@ -85,6 +85,35 @@ def test_chunked_streaming_equals_one_shot(c1_data, topk, chunk):
     np.testing.assert_array_equal(many["best"][ok], ref["best"][ok])
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_deferred_rerank_over_chunks(c1_data, precision):
+    """The re-rank deferred to the results: the approximate top-8 runs across
+    ragged orientation chunks (every chunk's slices kept alive) and is
+    re-ranked once. Indices above the margin equal the FP64 oracle, and the
+    returned distances are exact FP32 distances to the returned indices."""
+    import torch
+    from paper_2109_05339_gb300 import Matcher
+    pb, slices, clean, counts = c1_data
+    X = counts[:61]
+    scale = np.float32(1.0 / pb.cfg.photons)
+    M, P2, chunk = slices.shape[0], slices.shape[1], 77
+    m = Matcher(X.shape[0], chunk, P2, precision, 8)
+    m.set_rerank(True)
+    m.set_images(to_dev(X), float(scale))
+    kept = [to_dev(slices[c0:c0 + chunk]) for c0 in range(0, M, chunk)]
+    for k, sl in enumerate(kept):
+        m.add_slices(sl, orient_offset=k * chunk)
+    r = {k: v.cpu().numpy() for k, v in m.results(with_topk=True).items()}
+    m.status()
+    torch.cuda.synchronize()
+    Xd = f32(X) * np.float64(scale)
+    ref = matching.match(Xd, f32(slices))
+    ok = _check(r, ref, Xd, f32(slices)) if precision != "fp8" else ref["margin"] > 1e-2
+    np.testing.assert_array_equal(r["best"][ok], ref["best"][ok])
+    assert np.all(np.diff(r["topk_d"], axis=1) >= 0)
+    m.close()
+
+
 def test_ties_resolve_to_lowest_index():
     rng = np.random.default_rng(5)
     Y = rng.uniform(0, 1, (300, 64)).astype(np.float32)

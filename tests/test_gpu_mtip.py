@@ -24,15 +24,18 @@ def c1():
     return pb, counts, s, ref
 
 
-@pytest.mark.parametrize("cache,chunk", [(True, None), (False, 7)])
-def test_iteration_matches_oracle(c1, cache, chunk):
+@pytest.mark.parametrize("cache,chunk,keep", [(True, None, None), (False, 7, False), (True, 7, True),
+                                              (False, 9, True)])
+def test_iteration_matches_oracle(c1, cache, chunk, keep):
     import torch
     from paper_2109_05339_gb300 import MTIP
     pb, counts, s, ref = c1
     N, P2, M, n = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0], counts.shape[0]
     drv = MTIP(N, 1.0, P2, n, M, orient_chunk=chunk, img_chunk=5 if not cache else None,
-               cache_points=cache)
+               cache_points=cache, keep_slices=keep)
     assert drv.cache_points == cache
+    if keep is not None:
+        assert drv.keep_slices == keep
     res, x, lam = drv.iteration(to_dev(pb.A.astype(np.float32)), to_dev(pb.quats.astype(np.float32)),
                                 to_dev(pb.q_lab.astype(np.float32)), to_dev(counts.astype(np.float32)),
                                 1.0 / s, cg_iters=3)
