@@ -39,6 +39,9 @@ int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats,
               float* kernel_hat, int accumulate, int* err, cudaStream_t s, int mode, bool want_rhs,
               bool want_kernel);
 int merge_begin(spf_plan* P, cudaStream_t s);
+int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* inv_tab, float* const* cls_tab,
+                    float* const* cnt_tab, const float* images, const int* oidx, int n_img, int chunk, int n_total,
+                    const float* D, float b_scale, int* err, cudaStream_t s);
 int merge_finish(spf_plan* P, float* rhs, float* kernel_hat, int accumulate, cudaStream_t s);
 int cg_begin(spf_plan* P, const float* khat, double lambda, const float* rhs, const float* x0,
              float* x, double* res, cudaStream_t s);
@@ -110,6 +113,9 @@ struct spf_mtip {
   int* order = nullptr;            // driver index -> caller index
   int* inv = nullptr;              // caller index -> driver index
   std::vector<spf_points*> sets;   // kept point sets, one per orientation chunk
+  uint32_t** inv_tab = nullptr;    // device tables of the sets' inverse orders, class sums, counts
+  float** cls_tab = nullptr;
+  float** cnt_tab = nullptr;
   spf_points stream_set;           // streaming: one slice-only set, re-sorted per chunk
   float* slices = nullptr;         // orient_chunk x P2, or n_orient x P2 when kept
   float* img32 = nullptr;          // max_images x P2: 16-bit counts converted to FP32
@@ -153,6 +159,12 @@ struct DevScope {
 void free_sets(spf_mtip* h) {
   for (auto* p : h->sets) spf_points_destroy(p);
   h->sets.clear();
+  cudaFree(h->inv_tab);
+  cudaFree(h->cls_tab);
+  cudaFree(h->cnt_tab);
+  h->inv_tab = nullptr;
+  h->cls_tab = nullptr;
+  h->cnt_tab = nullptr;
 }
 
 void mtip_free(spf_mtip* h) {
@@ -229,9 +241,13 @@ int merge_core(spf_mtip* h, const float* img, int n_img, float img_scale, const 
   const int P2 = h->cfg.P2, M = h->cfg.n_orient;
   SPF_TRY(merge_begin(P, s));
   if (h->cache_points) {
+    // one pass over the images forms every set's class sums, then each set
+    // spreads its sums and counts
+    SPF_TRY(class_sums_sets(h->sets.data(), (int)h->sets.size(), h->inv_tab, h->cls_tab, h->cnt_tab, img,
+                            best_sorted, n_img, h->orient_chunk, M, h->D, img_scale, h->err, s));
     for (size_t c = 0; c < h->sets.size(); ++c)
       SPF_TRY(merge_points(P, h->sets[c], img, best_sorted, n_img, (int)c * h->orient_chunk, h->D, img_scale,
-                           nullptr, nullptr, 0, s, 0, true, true));
+                           nullptr, nullptr, 0, s, kMergeSumsDone, true, true));
   } else {
     for (int i0 = 0; i0 < n_img; i0 += h->img_chunk) {
       const int ni = std::min(h->img_chunk, n_img - i0);
@@ -460,6 +476,21 @@ int spf_mtip_set_orientations(spf_mtip* h, const float* quats, const float* q_la
       SPF_TRY(spf_points_create(&p, h->plan, h->quats_sorted + 4 * (size_t)c0, m, h->qlab, P2, 0, stream));
       h->sets.push_back(p);
     }
+    const size_t n = h->sets.size();
+    std::vector<uint32_t*> it(n);
+    std::vector<float*> ct(n), nt(n);
+    for (size_t c = 0; c < n; ++c) {
+      it[c] = h->sets[c]->invN;
+      ct[c] = h->sets[c]->cls;
+      nt[c] = h->sets[c]->cnt;
+    }
+    SPF_TRY(dev_alloc((void**)&h->inv_tab, sizeof(uint32_t*) * n, "point-set table"));
+    SPF_TRY(dev_alloc((void**)&h->cls_tab, sizeof(float*) * n, "point-set table"));
+    SPF_TRY(dev_alloc((void**)&h->cnt_tab, sizeof(float*) * n, "point-set table"));
+    SPF_CUDA(cudaMemcpyAsync(h->inv_tab, it.data(), sizeof(uint32_t*) * n, cudaMemcpyHostToDevice, s));
+    SPF_CUDA(cudaMemcpyAsync(h->cls_tab, ct.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, s));
+    SPF_CUDA(cudaMemcpyAsync(h->cnt_tab, nt.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, s));
+    SPF_CUDA(cudaStreamSynchronize(s));
   } else {
     h->stream_set.qlab = h->qlab;
   }

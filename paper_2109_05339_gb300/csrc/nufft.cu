@@ -469,6 +469,43 @@ __global__ void class_sum_kernel(const float* __restrict__ img, const int* __res
   if (c == 0 && threadIdx.x == 0) atomicAdd(cnt + j, 1.f);
 }
 
+// The same for every image at once over a list of point sets holding
+// consecutive orientation chunks of `chunk` orientations (the last may be
+// shorter): image i's orientation o = oidx[i] lies in set c = o / chunk at
+// local index o - c chunk, so one pass over the images fills every set's
+// class sums and counts. An index outside [0, n_total) sets the error word.
+__global__ void class_sum_sets_kernel(const float* __restrict__ img, const int* __restrict__ oidx, int n_img,
+                                      int chunk, int n_total, int P2, const float* __restrict__ D, float b_scale,
+                                      const uint32_t* const* __restrict__ inv_tab, float* const* __restrict__ cls_tab,
+                                      float* const* __restrict__ cnt_tab, int* err) {
+  const int chunks = (P2 + 1023) / 1024;
+  const int i = blockIdx.x / chunks, c = blockIdx.x - i * chunks;
+  if (i >= n_img) return;
+  const int o = __ldg(oidx + i);
+  if (o < 0 || o >= n_total) {
+    if (threadIdx.x == 0 && c == 0) atomicOr(err, 4);
+    return;
+  }
+  const int set = o / chunk, j = o - set * chunk;
+  const float* row = img + (size_t)i * P2;
+  const uint32_t* pos = inv_tab[set] + (size_t)j * P2;
+  float* cls = cls_tab[set];
+  const int p_end = min(P2, (c + 1) * 1024);
+  float v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int p = c * 1024 + threadIdx.x + 256 * k;
+    v[k] = p < p_end ? b_scale * __ldg(row + p) * (D ? __ldg(D + p) : 1.f) : 0.f;
+  }
+  uint32_t at[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) at[k] = v[k] != 0.f ? __ldg(pos + c * 1024 + threadIdx.x + 256 * k) : 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (v[k] != 0.f) atomicAdd(cls + at[k], v[k]);
+  if (c == 0 && threadIdx.x == 0) atomicAdd(cnt_tab[set] + j, 1.f);
+}
+
 // inv[ids[i]] = i: sorted position of every point id.
 __global__ void inverse_order_kernel(const uint32_t* __restrict__ ids, int64_t n, uint32_t* __restrict__ inv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1416,6 +1453,27 @@ int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats,
   return SPF_OK;
 }
 
+// Class sums of all images into consecutive point sets in one pass (the sets'
+// sums and counts cleared first); merge_points then runs with
+// kMergeSumsDone. Tables: device arrays of the sets' inverse orders, class
+// sums and counts.
+int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* inv_tab, float* const* cls_tab,
+                    float* const* cnt_tab, const float* images, const int* oidx, int n_img, int chunk, int n_total,
+                    const float* D, float b_scale, int* err, cudaStream_t s) {
+  for (int c = 0; c < nsets; ++c) {
+    const spf_points* S = sets[c];
+    SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)S->M * S->P2, s));
+    SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
+  }
+  if (n_img == 0 || nsets == 0) return SPF_OK;
+  const int P2 = sets[0]->P2;
+  const int64_t blocks = (int64_t)n_img * ceil_div(P2, 1024);
+  return launch("class_sum_kernel", s, [&] {
+    class_sum_sets_kernel<<<(unsigned)blocks, 256, 0, s>>>(images, oidx, n_img, chunk, n_total, P2, D, b_scale,
+                                                          inv_tab, cls_tab, cnt_tab, err);
+  }, 4.0 * n_img * (double)P2);
+}
+
 // Deferred merge: clear both fine grids / transform what they hold.
 int merge_begin(spf_plan* P, cudaStream_t s) {
   SPF_CUDA(cudaMemsetAsync(P->g.real, 0, sizeof(float) * (size_t)P->g.nf * P->g.nf * P->g.nf, s));
@@ -1458,9 +1516,11 @@ int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oid
                  const float* D, float b_scale, float* rhs, float* kernel_hat, int accumulate,
                  cudaStream_t s, int mode, bool want_rhs, bool want_kernel) {
   const int64_t npts = (int64_t)S->M * S->P2;
+  if (!(mode & kMergeSumsDone)) {
   SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)npts, s));
   SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
-  if (n_img > 0) {
+  }
+  if (n_img > 0 && !(mode & kMergeSumsDone)) {
     const int chunks = (int)ceil_div(S->P2, 1024);
     const int64_t blocks = (int64_t)n_img * chunks;
     SPF_TRY(launch("class_sum_kernel", s, [&] {

@@ -115,6 +115,7 @@ namespace spf {
 // into the output after.
 constexpr int kMergeClear = 1;
 constexpr int kMergeFinish = 2;
+constexpr int kMergeSumsDone = 4;   // point sets: class sums already formed (class_sums_sets)
 // Host side of the ES kernel set-up (es.cu).
 void es_params(double eps, int* w, double* beta);
 void es_poly(int w, double beta, EsPoly* out);
