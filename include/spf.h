@@ -321,8 +321,7 @@ int spf_matcher_set_schedule(spf_matcher* m, int schedule);
  * spf_matcher_results; calls must cover increasing, non-overlapping
  * orientation ranges (at most 1024 of them). The re-ranked candidates are
  * the best 8 by approximate distance over all chunks, instead of the best 8
- * of each chunk. spf_matcher_results synchronises the stream once (the
- * chunk table is uploaded from the host). */
+ * of each chunk. */
 int spf_matcher_set_rerank(spf_matcher* m, int deferred);
 int spf_matcher_results(spf_matcher* m, int32_t* best_idx, float* best_d, float* second_d,
                         int32_t* topk_idx, float* topk_d, void* stream);

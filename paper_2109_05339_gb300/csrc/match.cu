@@ -457,6 +457,16 @@ rerank_kernel(const float* __restrict__ X, float xscale, RowTable rows, int P2, 
   }
 }
 
+// Entry c of the deferred re-rank's chunk table, written in stream order.
+__global__ void chunk_table_kernel(int* __restrict__ off, const float** __restrict__ ptr, int c, int lo, int hi,
+                                   const float* rows) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    off[c] = lo;
+    off[c + 1] = hi;
+    ptr[c] = rows;
+  }
+}
+
 // Running approximate top-kCand per image across orientation chunks (deferred
 // re-rank): the nsplit * kCand candidates of this launch merged into ap.
 __global__ void cand_merge_kernel(const float* __restrict__ cand_v, const int* __restrict__ cand_i, int n_img,
@@ -594,11 +604,16 @@ int rerank_launch(spf_matcher* m, const float* slices, int n_orient, int orient_
     SPF_CHECK_ARG(m->n_chunks < kMaxChunks, "deferred re-rank: more than %d chunks", kMaxChunks);
     SPF_CHECK_ARG(m->n_chunks == 0 || orient_offset >= m->ch_off_h[m->n_chunks],
                   "deferred re-rank: chunks must come in increasing, non-overlapping orientation ranges");
-    m->ch_off_h[m->n_chunks] = orient_offset;
-    m->ch_ptr_h[m->n_chunks] = slices;
-    m->ch_off_h[m->n_chunks + 1] = orient_offset + n_orient;
+    const int c = m->n_chunks;
+    m->ch_off_h[c] = orient_offset;
+    m->ch_ptr_h[c] = slices;
+    m->ch_off_h[c + 1] = orient_offset + n_orient;
     ++m->n_chunks;
     m->pending = true;
+    SPF_TRY(launch("chunk_table_kernel", s, [&] {
+      chunk_table_kernel<<<1, 32, 0, s>>>(m->ch_off_d, m->ch_ptr_d, c, orient_offset, orient_offset + n_orient,
+                                          slices);
+    }));
     return launch("cand_merge_kernel", s, [&] {
       cand_merge_kernel<<<(unsigned)ceil_div(m->n_img, 256), 256, 0, s>>>(m->cand_v, m->cand_i, m->n_img, nsplit,
                                                                         m->ap_v, m->ap_i);
@@ -613,10 +628,6 @@ int rerank_flush(spf_matcher* m, cudaStream_t s) {
   if (!m->defer || !m->pending) return SPF_OK;
   m->pending = false;
   const int n = m->n_chunks;
-  SPF_CUDA(cudaMemcpyAsync(m->ch_off_d, m->ch_off_h, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
-  SPF_CUDA(cudaMemcpyAsync(m->ch_ptr_d, m->ch_ptr_h, sizeof(const float*) * n, cudaMemcpyHostToDevice, s));
-  // the host table is read by the copies above: keep it until they are done
-  SPF_CUDA(cudaStreamSynchronize(s));
   const int lo = m->ch_off_h[0], total = m->ch_off_h[n] - lo;
   const int div = (int)std::max<int64_t>(1, ceil_div(total, std::max(1, m->max_orient)));
   RowTable rows{nullptr, 0, m->ch_off_d, m->ch_ptr_d, n};

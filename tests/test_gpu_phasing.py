@@ -63,17 +63,20 @@ def test_er_and_hio_iterates_match_the_oracle(known):
     every Fourier error). HIO with positivity is left to the recovery test:
     its update jumps between rho - beta P_M rho and P_M rho where P_M rho
     crosses zero, so FP32 and FP64 trajectories part once such a voxel
-    flips."""
+    flips. ER's projections do not expand differences, so its iterates stay
+    within 1e-4; HIO's steps outside the support can, and 40 steps amplify
+    the transforms' FP32 rounding (about 1e-6 relative per step) to about
+    2e-4 (measured), bounded here by 1e-3."""
     import torch
     N, rho_true, support, amp, rho0 = known
-    for sched, pos in (([("er", 20)], True), ([("hio", 30, 0.9), ("er", 10)], False)):
+    for sched, pos, tol in (([("er", 20)], True, 1e-4), ([("hio", 30, 0.9), ("er", 10)], False, 1e-3)):
         ph = _phaser(N, amp, rho0, support)
         errs = ph.run(sched, positivity=pos)
         rho, _, _ = ph.get()
         torch.cuda.synchronize()
         ref_rho, _, ref_errs = oph.run(f32(amp), f32(rho0), support, sched, positivity=pos)
-        assert rel_l2(rho.cpu().numpy(), ref_rho) < 1e-4, (sched, rel_l2(rho.cpu().numpy(), ref_rho))
-        np.testing.assert_allclose(errs.cpu().numpy(), ref_errs, rtol=1e-4)
+        assert rel_l2(rho.cpu().numpy(), ref_rho) < tol, (sched, rel_l2(rho.cpu().numpy(), ref_rho))
+        np.testing.assert_allclose(errs.cpu().numpy(), ref_errs, rtol=tol)
         ph.close()
 
 
