@@ -181,6 +181,7 @@ struct PassArgs {
   int64_t sa, sb;        // strides of the line coordinates a and b
   LineSet ls;
   int in_lo[2], in_hi[2];  // positions along the line that are read; the rest count as zero
+  int out_lo[2], out_hi[2];  // positions along the line that are written (the rest are not needed)
   int convolve;          // transform, multiply by post_mul, transform back (-sign)
   int64_t pm_es, pm_sa, pm_sb;  // strided convolution: post_mul strides (along the line, a, b)
   int lines_per_cta;     // contiguous: lines per CTA; strided: b-lines per CTA
@@ -195,6 +196,11 @@ __device__ __forceinline__ int range_count(int lo, int hi) { return hi > lo ? hi
 // Position i of a line is read (else it counts as zero: pruned input).
 __device__ __forceinline__ bool in_read_range(const PassArgs& A, int i) {
   return (i >= A.in_lo[0] && i < A.in_hi[0]) || (i >= A.in_lo[1] && i < A.in_hi[1]);
+}
+
+// Position i of a line is stored (else the next pass does not read it).
+__device__ __forceinline__ bool in_write_range(const PassArgs& A, int i) {
+  return (i >= A.out_lo[0] && i < A.out_hi[0]) || (i >= A.out_lo[1] && i < A.out_hi[1]);
 }
 
 // Map the i-th selected coordinate to its value, over two ranges.
@@ -240,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) fft_strided_kernel(PassArgs A) {
   run_passes(A, sbuf, nlines);
   for (int e = threadIdx.x; e < nlines * n; e += kThreads) {
     int l = e % nlines, i = e / nlines;
+    if (!in_write_range(A, i)) continue;
     int b = pick(first + l, A.ls.b_lo, A.ls.b_hi);
     int64_t g = base_a + (int64_t)b * A.sb + (int64_t)i * A.es;
     float2 v = sbuf[l * n + i];
@@ -275,6 +282,7 @@ __global__ void __launch_bounds__(kThreads) fft_contig_kernel(PassArgs A) {
   run_passes(A, sbuf, nlines);
   for (int e = threadIdx.x; e < nlines * n; e += kThreads) {
     int l = e / n, i = e - l * n;
+    if (!in_write_range(A, i)) continue;
     int li = first + l;
     int a = pick(li / nbs, A.ls.a_lo, A.ls.a_hi);
     int b = pick(li % nbs, A.ls.b_lo, A.ls.b_hi);
@@ -360,8 +368,6 @@ __device__ __forceinline__ void passes_ct(float2* buf, int nlines, const float2*
 
 template <int N>
 __host__ __device__ constexpr int ct_lines() { return kMaxElems / N; }
-template <int N>
-__host__ __device__ constexpr int ct_tile() { return (kMaxElems / N) < 16 ? (kMaxElems / N) : 16; }
 
 // Element (position i, global offset g) of a line into shared memory: complex
 // input by an asynchronous copy (no register round trip, every copy of the
@@ -433,28 +439,83 @@ __global__ void __launch_bounds__(kThreads) fft_contig_ct(PassArgs A) {
     passes_ct<N, L, 1>(sbuf, nlines, stw, -A.sign, typename RadixPlan<N>::type{});
     for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
       const int l = e / N, i = e - l * N;
-      A.data[lbase[l] + i] = sbuf[e];
+      if (in_write_range(A, i)) A.data[lbase[l] + i] = sbuf[e];
     }
     return;
   }
   for (int e = threadIdx.x; e < nlines * N; e += kThreads) {
     const int l = e / N, i = e - l * N;
-    store_elem(A, lbase[l] + i, sbuf[e]);
+    if (in_write_range(A, i)) store_elem(A, lbase[l] + i, sbuf[e]);
   }
+}
+
+// Strided axes: a CTA takes kStrideTile neighbouring lines (consecutive b,
+// stride 1 in memory) and keeps them column-major in shared memory, element
+// (position i, line l) at i * kStrideTile + l. Sixteen lines make every
+// global row segment 128 contiguous bytes, and a half warp's butterfly
+// operands (one j, sixteen lines) fill one 128-byte shared-memory row, so
+// neither the staging copies nor the passes conflict on banks.
+constexpr int kStrideTile = 16;
+
+template <int N, int R, int Ns>
+__device__ __forceinline__ void pass_col(float2* buf, int nlines, const float2* __restrict__ tw, float sign) {
+  constexpr int T = kStrideTile;
+  constexpr int NB = N / R;
+  constexpr int Q = (T * NB + kThreads - 1) / kThreads;
+  constexpr int TSTEP = N / (Ns * R);
+  float2 v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int b = threadIdx.x + q * kThreads;
+    const int l = b % T, j = b / T;
+    if (b < T * NB && l < nlines) {
+      const float2* src = buf + j * T + l;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = src[r * NB * T];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int b = threadIdx.x + q * kThreads;
+    const int l = b % T, j = b / T;
+    if (b < T * NB && l < nlines) {
+      const int k = j % Ns;
+      if (Ns > 1 && k != 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[k * r * TSTEP];   // shared-memory table
+          w.y *= -sign;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      dft<R>(v[q], sign);
+      float2* dst = buf + ((j / Ns) * Ns * R + k) * T + l;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * Ns * T] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int Ns, int R, int... Rest>
+__device__ __forceinline__ void passes_col(float2* buf, int nlines, const float2* __restrict__ tw, float sign,
+                                           Rad<R, Rest...>) {
+  pass_col<N, R, Ns>(buf, nlines, tw, sign);
+  if constexpr (sizeof...(Rest) > 0) passes_col<N, Ns * R>(buf, nlines, tw, sign, Rad<Rest...>{});
 }
 
 template <int N>
 __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
-  constexpr int T = ct_tile<N>();
+  constexpr int T = kStrideTile;
   extern __shared__ float2 sbuf[];
-  __shared__ int64_t lbase[T];
+  __shared__ int64_t lbase[T], pbase[T];
   const int nb_sel = range_count(A.ls.b_lo[0], A.ls.b_hi[0]) + range_count(A.ls.b_lo[1], A.ls.b_hi[1]);
   const int tiles_b = (nb_sel + T - 1) / T;
   const int tile = blockIdx.x % tiles_b;
   const int a = pick(blockIdx.x / tiles_b, A.ls.a_lo, A.ls.a_hi);
   const int first = tile * T;
   const int nlines = min(T, nb_sel - first);
-  __shared__ int64_t pbase[T];
   if (threadIdx.x < nlines) {
     const int b = pick(first + threadIdx.x, A.ls.b_lo, A.ls.b_hi);
     lbase[threadIdx.x] = (int64_t)a * A.sa + (int64_t)b * A.sb;
@@ -462,11 +523,11 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
   }
   __syncthreads();
   float2* stw = sbuf + T * N;
-  float* skern = reinterpret_cast<float*>(sbuf + (T + 1) * N);   // convolution: the kernel's lines
+  float* skern = reinterpret_cast<float*>(sbuf + T * N + N);   // convolution: the kernel's lines
   stage_twiddles(stw, A.tw, N);
   for (int e = threadIdx.x; e < T * N; e += kThreads) {
     const int l = e % T, i = e / T;
-    if (l < nlines) stage_elem(A, sbuf + l * N + i, i, lbase[l] + (int64_t)i * A.es);
+    if (l < nlines) stage_elem(A, sbuf + e, i, lbase[l] + (int64_t)i * A.es);
   }
   if (A.convolve) {
     // the kernel's values are copied alongside the data, ahead of the passes
@@ -474,35 +535,32 @@ __global__ void __launch_bounds__(kThreads) fft_strided_ct(PassArgs A) {
       const int l = e % T, i = e / T;
       if (l < nlines)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(
-                         skern + l * N + i)),
+                         skern + e)),
                      "l"(A.post_mul + pbase[l] + (int64_t)i * A.pm_es)
                      : "memory");
     }
   }
   cp_async_wait();
   __syncthreads();
-  passes_ct<N, T, 1>(sbuf, nlines, stw, A.sign, typename RadixPlan<N>::type{});
+  passes_col<N, 1>(sbuf, nlines, stw, A.sign, typename RadixPlan<N>::type{});
   if (A.convolve) {
     // forward transform, product with the kernel (its own strides), inverse
     for (int e = threadIdx.x; e < T * N; e += kThreads) {
-      const int l = e % T, i = e / T;
-      if (l < nlines) {
-        const float f = skern[l * N + i];
-        const float2 v = sbuf[l * N + i];
-        sbuf[l * N + i] = make_float2(v.x * f, v.y * f);
-      }
+      const float f = skern[e];
+      const float2 v = sbuf[e];
+      sbuf[e] = make_float2(v.x * f, v.y * f);
     }
     __syncthreads();
-    passes_ct<N, T, 1>(sbuf, nlines, stw, -A.sign, typename RadixPlan<N>::type{});
+    passes_col<N, 1>(sbuf, nlines, stw, -A.sign, typename RadixPlan<N>::type{});
     for (int e = threadIdx.x; e < T * N; e += kThreads) {
       const int l = e % T, i = e / T;
-      if (l < nlines) A.data[lbase[l] + (int64_t)i * A.es] = sbuf[l * N + i];
+      if (l < nlines && in_write_range(A, i)) A.data[lbase[l] + (int64_t)i * A.es] = sbuf[e];
     }
     return;
   }
   for (int e = threadIdx.x; e < T * N; e += kThreads) {
     const int l = e % T, i = e / T;
-    if (l < nlines) store_elem(A, lbase[l] + (int64_t)i * A.es, sbuf[l * N + i]);
+    if (l < nlines && in_write_range(A, i)) store_elem(A, lbase[l] + (int64_t)i * A.es, sbuf[e]);
   }
 }
 
@@ -781,7 +839,7 @@ int launch_ct(PassArgs& A, bool contiguous, int na, int nb, double bytes, cudaSt
     const size_t smem = (size_t)(L + 1) * N * sizeof(float2);   // lines and the twiddle table
     return launch("fft_contig_kernel", s, [&] { fft_contig_ct<N><<<grid, kThreads, smem, s>>>(A); }, bytes);
   }
-  constexpr int T = ct_tile<N>();
+  constexpr int T = kStrideTile;
   const int64_t grid = ceil_div(nb, T) * (int64_t)na;
   // lines and the twiddle table, and for a convolution the kernel's lines
   const size_t smem = (size_t)(T + 1) * N * sizeof(float2) + (A.convolve ? (size_t)T * N * sizeof(float) : 0);
@@ -815,14 +873,15 @@ int count(const int* lo, const int* hi) {
 }
 
 // Algorithmic bytes of one pass: every line reads its positions inside the
-// read range (4 bytes real, 8 complex), writes all n outputs (4 or 8 bytes)
-// and reads n real factors when it multiplies by post_mul.
+// read range (4 bytes real, 8 complex), writes its positions inside the
+// write range (4 or 8 bytes) and reads n real factors when it multiplies by
+// post_mul.
 double pass_bytes(const PassArgs& A, int na, int nb) {
   const double lines = (double)na * nb;
-  const double rd = count(A.in_lo, A.in_hi);
+  const double rd = count(A.in_lo, A.in_hi), wr = count(A.out_lo, A.out_hi);
   const double ein = A.in_real ? 4.0 : 8.0, eout = A.out_real ? 4.0 : 8.0;
   const double pm = A.post_mul ? 4.0 * A.n : 0.0;
-  return lines * (rd * ein + A.n * eout + pm);
+  return lines * (rd * ein + wr * eout + pm);
 }
 
 int launch_pass(PassArgs A, bool contiguous, cudaStream_t s) {
@@ -897,7 +956,8 @@ void fft3_destroy(FFT3* p) {
 static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real, float* out_real,
                      const float* post_mul, int sign, const int* a_lo, const int* a_hi,
                      const int* b_lo, const int* b_hi, cudaStream_t s, const int* in_lo = nullptr,
-                     const int* in_hi = nullptr, bool convolve = false, int row = 0) {
+                     const int* in_hi = nullptr, bool convolve = false, int row = 0,
+                     const int* out_lo = nullptr, const int* out_hi = nullptr) {
   PassArgs A;
   A.data = data;
   A.in_real = in_real;
@@ -919,6 +979,8 @@ static int axis_pass(const FFT3* p, int axis, float2* data, const float* in_real
     A.ls.b_lo[i] = b_lo[i]; A.ls.b_hi[i] = b_hi[i];
     A.in_lo[i] = in_lo ? in_lo[i] : 0;
     A.in_hi[i] = in_hi ? in_hi[i] : (i == 0 ? ax.n : 0);
+    A.out_lo[i] = out_lo ? out_lo[i] : 0;
+    A.out_hi[i] = out_hi ? out_hi[i] : (i == 0 ? ax.n : 0);
   }
   if (axis == 0) {          // lines (z, y): a = z, b = y
     A.es = 1; A.sa = n1 * n0; A.sb = n0;
@@ -963,11 +1025,18 @@ int fft3_exec_ex(const FFT3* p, float2* data, const float* in_real, float* out_r
                       rx_hi));
     return SPF_OK;
   }
+  // each pass stores only what the next one reads, the last only the
+  // output range needed
+  int rz_lo[2], rz_hi[2];
   wrapped_range(p->n0, need_hw_out, rx_lo, rx_hi);
   wrapped_range(p->n1, need_hw_out, ry_lo, ry_hi);
-  SPF_TRY(axis_pass(p, 0, data, in_real, nullptr, nullptr, sign, fz_lo, fz_hi, fy_lo, fy_hi, s));
-  SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, sign, fz_lo, fz_hi, rx_lo, rx_hi, s));
-  SPF_TRY(axis_pass(p, 2, data, nullptr, out_real, post_mul, sign, ry_lo, ry_hi, rx_lo, rx_hi, s));
+  wrapped_range(p->n2, need_hw_out, rz_lo, rz_hi);
+  SPF_TRY(axis_pass(p, 0, data, in_real, nullptr, nullptr, sign, fz_lo, fz_hi, fy_lo, fy_hi, s, nullptr, nullptr,
+                    false, 0, rx_lo, rx_hi));
+  SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, sign, fz_lo, fz_hi, rx_lo, rx_hi, s, nullptr, nullptr,
+                    false, 0, ry_lo, ry_hi));
+  SPF_TRY(axis_pass(p, 2, data, nullptr, out_real, post_mul, sign, ry_lo, ry_hi, rx_lo, rx_hi, s, nullptr, nullptr,
+                    false, 0, rz_lo, rz_hi));
   return SPF_OK;
 }
 
@@ -994,13 +1063,16 @@ int fft3_convolve(const FFT3* p, float2* data, const float* kernel, int zero_hw_
   wrapped_range(p->n2, zero_hw_in, rz_lo, rz_hi);
   SPF_TRY(axis_pass(p, 2, data, nullptr, nullptr, nullptr, -1, ry_lo, ry_hi, rx_lo, rx_hi, s, rz_lo, rz_hi));
   SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, -1, fz_lo, fz_hi, rx_lo, rx_hi, s, ry_lo, ry_hi));
-  SPF_TRY(axis_pass(p, 0, data, nullptr, nullptr, kernel, -1, fz_lo, fz_hi, fy_lo, fy_hi, s, rx_lo, rx_hi,
-                    /*convolve=*/true));
-  int ox_lo[2], ox_hi[2], oy_lo[2], oy_hi[2];
+  int ox_lo[2], ox_hi[2], oy_lo[2], oy_hi[2], oz_lo[2], oz_hi[2];
   wrapped_range(p->n0, need_hw_out, ox_lo, ox_hi);
   wrapped_range(p->n1, need_hw_out, oy_lo, oy_hi);
-  SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, +1, fz_lo, fz_hi, ox_lo, ox_hi, s));
-  return axis_pass(p, 2, data, nullptr, nullptr, nullptr, +1, oy_lo, oy_hi, ox_lo, ox_hi, s);
+  wrapped_range(p->n2, need_hw_out, oz_lo, oz_hi);
+  SPF_TRY(axis_pass(p, 0, data, nullptr, nullptr, kernel, -1, fz_lo, fz_hi, fy_lo, fy_hi, s, rx_lo, rx_hi,
+                    /*convolve=*/true, 0, ox_lo, ox_hi));
+  SPF_TRY(axis_pass(p, 1, data, nullptr, nullptr, nullptr, +1, fz_lo, fz_hi, ox_lo, ox_hi, s, nullptr, nullptr,
+                    false, 0, oy_lo, oy_hi));
+  return axis_pass(p, 2, data, nullptr, nullptr, nullptr, +1, oy_lo, oy_hi, ox_lo, ox_hi, s, nullptr, nullptr, false,
+                   0, oz_lo, oz_hi);
 }
 
 #define SPF_SIDE_SWITCH(n, expr)       \
@@ -1054,10 +1126,11 @@ int fft3_r2c_modes(const FFT3* p, const float* in, int h, int sign, float2* out,
     default: rc = SPF_ERR_UNSUPPORTED; break;
   }
   SPF_TRY(rc);
+  // the y pass stores the rows the z pass reads, the z pass the planes kept
   SPF_TRY(axis_pass(p, 1, out, nullptr, nullptr, nullptr, sign, f_lo, f_hi, k_lo, k_hi, s, nullptr, nullptr, false,
-                    h));
+                    h, r_lo, r_hi));
   return axis_pass(p, 2, out, nullptr, nullptr, nullptr, sign, r_lo, r_hi, k_lo, k_hi, s, nullptr, nullptr, false,
-                   h);
+                   h, r_lo, r_hi);
 }
 
 bool fft3_real_supported(const FFT3* p) {
@@ -1082,9 +1155,12 @@ int fft3_convolve_real(const FFT3* p, int Nm, const float* x, const float* add, 
   SPF_CHECK_ARG(!ep.part || ep.xin, "fft: epilogue partial sums need xin");
   SPF_TRY(launch_rows(true, p, Nm, x, add, beta, x_new, work, nullptr, ep, s));
   SPF_TRY(axis_pass(p, 1, work, nullptr, nullptr, nullptr, -1, r_lo, r_hi, k_lo, k_hi, s, r_lo, r_hi, false, H));
-  SPF_TRY(axis_pass(p, 2, work, nullptr, nullptr, kernel, -1, f_lo, f_hi, k_lo, k_hi, s, r_lo, r_hi, true, H));
+  // the inverse y pass reads the planes z in the data range only, and the
+  // inverse rows read the rows y in it
+  SPF_TRY(axis_pass(p, 2, work, nullptr, nullptr, kernel, -1, f_lo, f_hi, k_lo, k_hi, s, r_lo, r_hi, true, H,
+                    r_lo, r_hi));
   SPF_TRY(axis_pass(p, 1, work, nullptr, nullptr, nullptr, +1, r_lo, r_hi, k_lo, k_hi, s, nullptr, nullptr, false,
-                    H));
+                    H, r_lo, r_hi));
   return launch_rows(false, p, Nm, nullptr, nullptr, nullptr, nullptr, work, y, ep, s);
 }
 
