@@ -474,36 +474,68 @@ __global__ void class_sum_kernel(const float* __restrict__ img, const int* __res
 // shorter): image i's orientation o = oidx[i] lies in set c = o / chunk at
 // local index o - c chunk, so one pass over the images fills every set's
 // class sums and counts. An index outside [0, n_total) sets the error word.
-__global__ void class_sum_sets_kernel(const float* __restrict__ img, const int* __restrict__ oidx, int n_img,
-                                      int chunk, int n_total, int P2, const float* __restrict__ D, float b_scale,
-                                      const uint32_t* const* __restrict__ inv_tab, float* const* __restrict__ cls_tab,
-                                      float* const* __restrict__ cnt_tab, int* err) {
-  const int chunks = (P2 + 1023) / 1024;
-  const int i = blockIdx.x / chunks, c = blockIdx.x - i * chunks;
-  if (i >= n_img) return;
-  const int o = __ldg(oidx + i);
-  if (o < 0 || o >= n_total) {
-    if (threadIdx.x == 0 && c == 0) atomicOr(err, 4);
-    return;
+// A persistent grid walks the (image, 1024-pixel chunk) tasks, two per
+// iteration with their loads issued together; rows whose pixel count is a
+// multiple of 4 are read as 16-byte vectors.
+constexpr int kClassTask = 1024;
+__global__ void __launch_bounds__(256) class_sum_sets_kernel(
+    const float* __restrict__ img, const int* __restrict__ oidx, int n_img, int chunk, int n_total, int P2,
+    const float* __restrict__ D, float b_scale, const uint32_t* const* __restrict__ inv_tab,
+    float* const* __restrict__ cls_tab, float* const* __restrict__ cnt_tab, int* err) {
+  const int chunks = (P2 + kClassTask - 1) / kClassTask;
+  const int64_t ntask = (int64_t)n_img * chunks;
+  const bool vec = (P2 & 3) == 0;
+  for (int64_t t0 = blockIdx.x; t0 < ntask; t0 += 2 * (int64_t)gridDim.x) {
+    float v[2][4];
+    int o[2], p0[2];
+    int64_t row[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t task = t0 + h * (int64_t)gridDim.x;
+      o[h] = -1;
+      p0[h] = 0;
+      row[h] = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[h][k] = 0.f;
+      if (task >= ntask) continue;
+      const int i = (int)(task / chunks), c = (int)(task - (int64_t)i * chunks);
+      o[h] = __ldg(oidx + i);
+      p0[h] = c * kClassTask + 4 * threadIdx.x;
+      row[h] = (int64_t)i * P2;
+      if (o[h] < 0 || o[h] >= n_total) {
+        if (threadIdx.x == 0 && c == 0) atomicOr(err, 4);
+        o[h] = -1;
+        continue;
+      }
+      if (vec && p0[h] + 3 < P2) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(img + row[h] + p0[h]));
+        v[h][0] = x.x;
+        v[h][1] = x.y;
+        v[h][2] = x.z;
+        v[h][3] = x.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (p0[h] + k < P2) v[h][k] = __ldg(img + row[h] + p0[h] + k);
+      }
+      if (c == 0 && threadIdx.x == 0) {
+        const int set = o[h] / chunk;
+        atomicAdd(cnt_tab[set] + (o[h] - set * chunk), 1.f);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (o[h] < 0) continue;
+      const int set = o[h] / chunk, j = o[h] - set * chunk;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (v[h][k] == 0.f) continue;
+        const int p = p0[h] + k;
+        const float val = b_scale * v[h][k] * (D ? __ldg(D + p) : 1.f);
+        atomicAdd(cls_tab[set] + __ldg(inv_tab[set] + (size_t)j * P2 + p), val);
+      }
+    }
   }
-  const int set = o / chunk, j = o - set * chunk;
-  const float* row = img + (size_t)i * P2;
-  const uint32_t* pos = inv_tab[set] + (size_t)j * P2;
-  float* cls = cls_tab[set];
-  const int p_end = min(P2, (c + 1) * 1024);
-  float v[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int p = c * 1024 + threadIdx.x + 256 * k;
-    v[k] = p < p_end ? b_scale * __ldg(row + p) * (D ? __ldg(D + p) : 1.f) : 0.f;
-  }
-  uint32_t at[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) at[k] = v[k] != 0.f ? __ldg(pos + c * 1024 + threadIdx.x + 256 * k) : 0u;
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (v[k] != 0.f) atomicAdd(cls + at[k], v[k]);
-  if (c == 0 && threadIdx.x == 0) atomicAdd(cnt_tab[set] + j, 1.f);
 }
 
 // inv[ids[i]] = i: sorted position of every point id.
@@ -1467,10 +1499,14 @@ int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* i
   }
   if (n_img == 0 || nsets == 0) return SPF_OK;
   const int P2 = sets[0]->P2;
-  const int64_t blocks = (int64_t)n_img * ceil_div(P2, 1024);
+  int sms = 152, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tasks = (int64_t)n_img * ceil_div(P2, kClassTask);
+  const unsigned blocks = (unsigned)std::min<int64_t>(tasks, (int64_t)sms * 8);
   return launch("class_sum_kernel", s, [&] {
-    class_sum_sets_kernel<<<(unsigned)blocks, 256, 0, s>>>(images, oidx, n_img, chunk, n_total, P2, D, b_scale,
-                                                          inv_tab, cls_tab, cnt_tab, err);
+    class_sum_sets_kernel<<<blocks, 256, 0, s>>>(images, oidx, n_img, chunk, n_total, P2, D, b_scale, inv_tab,
+                                                 cls_tab, cnt_tab, err);
   }, 4.0 * n_img * (double)P2);
 }
 
