@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 CONFIG = "c5"
-DEFAULT_CHUNK = {"c5": 10_000}   # orientations per streamed chunk
+DEFAULT_CHUNK = {"c5": 50_000}   # orientations per streamed chunk (x 36,864 pixels < 2^31 points)
 
 
 def parse():
@@ -317,6 +317,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     drv.plan.status()
     drv.matcher.status()
+    free_b, total_b = torch.cuda.mem_get_info(dev)
 
     value = Ni * M * world / (ms / 1e3)
     # per-kernel table and the dominant kernel's roofline
@@ -372,7 +373,8 @@ def run_ours(args, rank, world):
                    "l2": (f"inputs larger than L2 (images {Ni * P2 * 4 / 1e6:.0f} MB, slices "
                           f"{drv.orient_chunk * P2 * 4 / 1e6:.0f} MB per chunk)"),
                    "orient_chunk": drv.orient_chunk,
-                   "point_sets": "cached" if drv.cache_points else "streamed"},
+                   "point_sets": "cached" if drv.cache_points else "streamed",
+                   "device_memory_in_use_gb": round((total_b - free_b) / 1e9, 1)},
         "nufft_mpts_per_s": {
             "slice_type2": (M * P2) / (stage.get("slice", 0) + 1e-12) / 1e3,
             "merge_type1_rhs_plus_kernel": (Ni * P2) / (stage.get("merge", 0) + 1e-12) / 1e3},
