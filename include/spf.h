@@ -397,6 +397,19 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
  *   floats) are written back on `stream`. Asynchronous for page-locked host
  *   buffers: the inputs must stay unchanged and the outputs are valid once
  *   `stream` has completed the call's work (e.g. cudaStreamSynchronize).
+ * spf_mtip_set_upload: how spf_mtip_iteration_host moves the images to the
+ *   device. SPF_UPLOAD_SM (default): a kernel on the copy stream reads the
+ *   host buffer over the CPU-GPU link and writes the slot (about 190 GB/s on
+ *   a GB300 while the previous call computes, against 35-45 GB/s for the
+ *   copy engines there); taken only when the first and last byte of
+ *   images_host lie in page-locked memory mapped into the device's address
+ *   space (cudaHostAlloc / cudaHostRegister, one allocation for the whole
+ *   buffer) and both ends are 16-byte aligned, else the copy engines are
+ *   used. SPF_UPLOAD_COPY: always cudaMemcpyAsync on the copy stream (no SMs
+ *   taken from the computing call). SPF_ERR_ARG for another mode.
+ * spf_mtip_last_upload_ms: device time of the most recent completed image
+ *   upload of spf_mtip_iteration_host (events around it on the copy stream);
+ *   -1 before the first. Waits for that upload to finish.
  * spf_mtip_status: the plan's, the matcher's and the driver's error words
  *   (waits for the device). spf_mtip_plan / spf_mtip_matcher: the driver's
  *   plan and matcher (owned by the driver) for the other calls of this header.
@@ -405,6 +418,8 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
  * ------------------------------------------------------------------------- */
 #define SPF_IMAGES_F32 0
 #define SPF_IMAGES_U16 1
+#define SPF_UPLOAD_COPY 0
+#define SPF_UPLOAD_SM 1
 typedef struct spf_mtip spf_mtip;
 typedef struct spf_mtip_config {
   int N;
@@ -447,6 +462,8 @@ int spf_mtip_iteration(spf_mtip* h, const float* A, const void* images, int imag
 int spf_mtip_iteration_host(spf_mtip* h, const float* A_host, const void* images_host, int image_type, int n_img,
                             float img_scale, int cg_iters, double lam_rel, int32_t* best_host, float* x_host,
                             double* lambda_out, void* stream);
+int spf_mtip_set_upload(spf_mtip* h, int mode);
+int spf_mtip_last_upload_ms(spf_mtip* h, float* ms);
 
 /* ---------------------------------------------------------------------------
  * Phasing, Sec. II-D: from the merged diffraction volume to a density by

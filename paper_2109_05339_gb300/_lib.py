@@ -19,6 +19,7 @@ SPF_ERR_TIMEOUT = -4
 SPF_ERR_UNSUPPORTED = -5
 SPF_FP32, SPF_BF16, SPF_FP8 = 0, 1, 2
 SPF_IMAGES_F32, SPF_IMAGES_U16 = 0, 1
+SPF_UPLOAD_COPY, SPF_UPLOAD_SM = 0, 1
 SPF_PHASE_ER, SPF_PHASE_HIO = 0, 1
 
 _CODES = {SPF_ERR_ARG: "SPF_ERR_ARG", SPF_ERR_OOM: "SPF_ERR_OOM", SPF_ERR_CUDA: "SPF_ERR_CUDA",
@@ -110,6 +111,8 @@ PROTOTYPES = {
     "spf_mtip_solve": (I, [P, P, P, P, D, I64, I, P, C.POINTER(D), P, P]),
     "spf_mtip_iteration": (I, [P, P, P, I, I, F, I, D, P, P, C.POINTER(D), P]),
     "spf_mtip_iteration_host": (I, [P, P, P, I, I, F, I, D, P, P, C.POINTER(D), P]),
+    "spf_mtip_set_upload": (I, [P, I]),
+    "spf_mtip_last_upload_ms": (I, [P, C.POINTER(F)]),
     "spf_profile_enable": (I, [I]),
     "spf_profile_select": (I, [C.c_char_p]),
     "spf_profile_read": (I, [I, C.c_char_p, I, C.POINTER(C.c_longlong), C.POINTER(D)]),

@@ -134,6 +134,8 @@ struct spf_mtip {
   cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
   float* slotA[2] = {nullptr, nullptr};
   void* slotImg[2] = {nullptr, nullptr};
+  cudaEvent_t up0[2] = {nullptr, nullptr}, up1[2] = {nullptr, nullptr};   // timing of each slot's image upload
+  int upload_mode = SPF_UPLOAD_SM;
   long long host_calls = 0;
 };
 
@@ -191,6 +193,8 @@ void mtip_free(spf_mtip* h) {
     cudaFree(h->slotImg[b]);
     if (h->copied[b]) cudaEventDestroy(h->copied[b]);
     if (h->freed[b]) cudaEventDestroy(h->freed[b]);
+    if (h->up0[b]) cudaEventDestroy(h->up0[b]);
+    if (h->up1[b]) cudaEventDestroy(h->up1[b]);
   }
   if (h->copy) cudaStreamDestroy(h->copy);
   if (h->matcher) spf_matcher_destroy(h->matcher);
@@ -201,6 +205,62 @@ void mtip_free(spf_mtip* h) {
 size_t image_elem(int type) { return type == SPF_IMAGES_U16 ? 2 : 4; }
 
 // FP32 view of the caller's images: 16-bit counts converted into img32.
+// Copy of n16 16-byte vectors from page-locked host memory mapped into the
+// device's address space: the SMs read over the CPU-GPU link, four vectors
+// in flight per thread.
+__global__ void __launch_bounds__(512) upload_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                     size_t n16) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += 4 * stride) {
+    uint4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i + k * stride < n16) v[k] = src[i + k * stride];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i + k * stride < n16) dst[i + k * stride] = v[k];
+  }
+}
+
+// Device address of host bytes [p, p + n) when both ends are page-locked and
+// mapped with the same offset (one registered range), else NULL.
+const void* mapped_range(const void* p, size_t n) {
+  if (n == 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(
+          &a1, static_cast<const char*>(p) + (n - 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+    return nullptr;
+  if (static_cast<const char*>(a1.devicePointer) - static_cast<const char*>(a0.devicePointer) != (ptrdiff_t)(n - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
+// Host-to-device upload of the images on the copy stream, by the mode set.
+int upload_images(spf_mtip* h, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (h->upload_mode == SPF_UPLOAD_SM) {
+    const void* dsrc = mapped_range(src, bytes);
+    if (dsrc && ((uintptr_t)dsrc & 15) == 0 && ((uintptr_t)dst & 15) == 0) {
+      const size_t n16 = bytes / 16, tail = bytes - 16 * n16;
+      int sms = 152;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->cfg.device);
+      if (n16 > 0)
+        SPF_TRY(launch("upload_kernel", s, [&] {
+          upload_kernel<<<sms, 512, 0, s>>>(static_cast<const uint4*>(dsrc), static_cast<uint4*>(dst), n16);
+        }, 2.0 * (double)(16 * n16)));
+      if (tail > 0)
+        SPF_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + 16 * n16, static_cast<const char*>(src) + 16 * n16,
+                                 tail, cudaMemcpyHostToDevice, s));
+      return SPF_OK;
+    }
+  }
+  SPF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+  return SPF_OK;
+}
+
 int images_f32(spf_mtip* h, const void* images, int type, int n_img, const float** out, cudaStream_t s) {
   if (type == SPF_IMAGES_F32) {
     *out = static_cast<const float*>(images);
@@ -242,7 +302,7 @@ int merge_core(spf_mtip* h, const float* img, int n_img, float img_scale, const 
   SPF_TRY(merge_begin(P, s));
   if (h->cache_points) {
     // one pass over the images forms every set's class sums, then each set
-    // spreads its sums and counts
+    // spreads its sums (leaving them zeroed for the next call) and its counts
     SPF_TRY(class_sums_sets(h->sets.data(), (int)h->sets.size(), h->inv_tab, h->cls_tab, h->cnt_tab, img,
                             best_sorted, n_img, h->orient_chunk, M, h->D, img_scale, h->err, s));
     for (size_t c = 0; c < h->sets.size(); ++c)
@@ -376,6 +436,8 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
       e = cudaEventCreateWithFlags(&h->copied[b], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->freed[b], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventRecord(h->freed[b], h->copy);
+      if (e == cudaSuccess) e = cudaEventCreate(&h->up0[b]);
+      if (e == cudaSuccess) e = cudaEventCreate(&h->up1[b]);
     }
     if (rc == SPF_OK && e != cudaSuccess) {
       set_error("driver streams and events: %s", cudaGetErrorString(e));
@@ -607,8 +669,9 @@ int spf_mtip_iteration_host(spf_mtip* h, const float* A_host, const void* images
   // inputs into slot b on the copy stream, once the call two back is done with it
   SPF_CUDA(cudaStreamWaitEvent(h->copy, h->freed[b], 0));
   SPF_CUDA(cudaMemcpyAsync(h->slotA[b], A_host, sizeof(float) * n3, cudaMemcpyHostToDevice, h->copy));
-  SPF_CUDA(cudaMemcpyAsync(h->slotImg[b], images_host, image_elem(image_type) * (size_t)n_img * h->cfg.P2,
-                           cudaMemcpyHostToDevice, h->copy));
+  SPF_CUDA(cudaEventRecord(h->up0[b], h->copy));
+  SPF_TRY(upload_images(h, h->slotImg[b], images_host, image_elem(image_type) * (size_t)n_img * h->cfg.P2, h->copy));
+  SPF_CUDA(cudaEventRecord(h->up1[b], h->copy));
   SPF_CUDA(cudaEventRecord(h->copied[b], h->copy));
   SPF_CUDA(cudaStreamWaitEvent(s, h->copied[b], 0));
   ++h->host_calls;
@@ -617,6 +680,28 @@ int spf_mtip_iteration_host(spf_mtip* h, const float* A_host, const void* images
   SPF_CUDA(cudaMemcpyAsync(best_host, h->best, sizeof(int) * (size_t)n_img, cudaMemcpyDeviceToHost, s));
   SPF_CUDA(cudaMemcpyAsync(x_host, h->x, sizeof(float) * n3, cudaMemcpyDeviceToHost, s));
   SPF_CUDA(cudaEventRecord(h->freed[b], s));
+  return SPF_OK;
+}
+
+int spf_mtip_set_upload(spf_mtip* h, int mode) {
+  clear_error();
+  SPF_TRY(check_handle(h, false));
+  SPF_CHECK_ARG(mode == SPF_UPLOAD_COPY || mode == SPF_UPLOAD_SM, "unknown upload mode %d", mode);
+  h->upload_mode = mode;
+  return SPF_OK;
+}
+
+int spf_mtip_last_upload_ms(spf_mtip* h, float* ms) {
+  clear_error();
+  SPF_TRY(check_handle(h, false));
+  SPF_CHECK_ARG(ms != nullptr, "NULL pointer");
+  *ms = -1.f;
+  if (!h->host_path || h->host_calls == 0) return SPF_OK;
+  DevScope dev(h->cfg.device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  const int b = (int)((h->host_calls - 1) & 1);
+  SPF_CUDA(cudaEventSynchronize(h->up1[b]));
+  SPF_CUDA(cudaEventElapsedTime(ms, h->up0[b], h->up1[b]));
   return SPF_OK;
 }
 

@@ -127,16 +127,26 @@ struct ExplicitPts {
 // Strength of the point with id `id` at position `pos` of the sorted order.
 struct StrPtr {        // v[id]
   static constexpr bool kByPos = false;
+  static constexpr bool kConsume = false;
+  static constexpr bool kSortBatch = false;
   const float* v;
   __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const { return __ldg(v + id); }
 };
-struct StrSorted {     // v[pos]: strengths stored in the sorted order (coalesced)
+// v[pos]: strengths stored in the sorted order (coalesced), consumed: each
+// entry is read by one warp, which sets a nonzero one back to zero, so the
+// array is all zeros after the spread (class sums need no clearing pass).
+// The slicing point set these belong to is sorted by bin only, so each
+// staged batch is ordered by window before it is added.
+struct StrSorted {
   static constexpr bool kByPos = true;
-  const float* v;
-  __device__ __forceinline__ float operator()(uint32_t, uint32_t pos) const { return __ldg(v + pos); }
+  static constexpr bool kConsume = true;
+  static constexpr bool kSortBatch = true;
+  float* v;
 };
 struct StrImage {      // D[p] * scale * image[id]
   static constexpr bool kByPos = false;
+  static constexpr bool kConsume = false;
+  static constexpr bool kSortBatch = false;
   const float* img;
   const float* D;
   FastDiv P2;
@@ -148,6 +158,8 @@ struct StrImage {      // D[p] * scale * image[id]
 };
 struct StrWeights {    // D[p] (ones if D is NULL)
   static constexpr bool kByPos = false;
+  static constexpr bool kConsume = false;
+  static constexpr bool kSortBatch = false;
   const float* D;
   FastDiv P2;
   __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const {
@@ -157,6 +169,8 @@ struct StrWeights {    // D[p] (ones if D is NULL)
 
 struct StrCount {     // D[p] * count[j] for point id = j * P2 + p
   static constexpr bool kByPos = false;
+  static constexpr bool kConsume = false;
+  static constexpr bool kSortBatch = false;
   const float* cnt;
   const float* D;
   FastDiv P2;
@@ -264,7 +278,12 @@ struct SortGeom {
   int nb0, nb1, nb2;
 };
 
-template <int W>
+// Sort key of a point: its tap-origin cell, bin-major, the cells of a bin
+// ordered by their 2^3 cell block. With BinOnly every cell of a bin gets the
+// bin's first key, so a bin's points keep the order in which the sort meets
+// them (runs of neighbouring pixels of one orientation stay together)
+// instead of being ordered by cell.
+template <int W, bool BinOnly = false>
 __device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
   constexpr int H = W / 2;
   int cx = wrap1((int)ceilf(u.x - 0.5f * W) + H, g.nf);
@@ -275,6 +294,7 @@ __device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
   // cell inside the 4^3 bin, ordered by its 2^3 cell pair block first: the
   // points of one block are contiguous (the spreading accumulates a block's
   // points in registers)
+  if (BinOnly) return bin << (3 * B);
   const int pair = (((cz >> 1) & 1) << 2) | (((cy >> 1) & 1) << 1) | ((cx >> 1) & 1);
   const int sub = ((cz & 1) << 2) | ((cy & 1) << 1) | (cx & 1);
   return (bin << (3 * B)) | (pair << 3) | sub;
@@ -298,21 +318,21 @@ __device__ __forceinline__ KeyRun key_run(int key) {
   return {leader, lane - leader, next - lane};
 }
 
-template <int W, class Pts>
+template <int W, class Pts, bool BinOnly>
 __global__ void key_count_kernel(Pts pts, int64_t npts, SortGeom g, int* __restrict__ count) {
   int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int key = -1;
-  if (id < npts) key = point_key<W>(pts((uint32_t)id), g);
+  if (id < npts) key = point_key<W, BinOnly>(pts((uint32_t)id), g);
   const KeyRun run = key_run(key);
   if (key >= 0 && run.rank == 0) atomicAdd(count + key, run.len);
 }
 
-template <int W, class Pts>
+template <int W, class Pts, bool BinOnly>
 __global__ void key_scatter_kernel(Pts pts, int64_t npts, SortGeom g, const int* __restrict__ start,
                                    int* __restrict__ fill, uint32_t* __restrict__ sorted, int* err) {
   int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int key = -1;
-  if (id < npts) key = point_key<W>(pts((uint32_t)id), g);
+  if (id < npts) key = point_key<W, BinOnly>(pts((uint32_t)id), g);
   const KeyRun run = key_run(key);
   int base = 0;
   if (key >= 0 && run.rank == 0) base = atomicAdd(fill + key, run.len);
@@ -976,7 +996,25 @@ __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int l
 // Stage points q[0 .. n) of the queue (lane k: point k) and add them to the
 // register accumulators in order, writing the accumulators back to the
 // subgrid whenever the window corner changes.
-template <int W, class Pts>
+// Ascending sort of one (key, value) pair per lane across the warp (bitonic
+// network over shuffles); equal keys keep their own values.
+__device__ __forceinline__ void warp_sort_pairs(int& key, int& val, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int ok = __shfl_xor_sync(0xffffffffu, key, j);
+      const int ov = __shfl_xor_sync(0xffffffffu, val, j);
+      const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
+      if (keep_min ? ok < key : ok > key) {
+        key = ok;
+        val = ov;
+      }
+    }
+  }
+}
+
+template <int W, class Pts, bool SortBatch>
 __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, int nf, int bx, int by, int bz,
                                              const uint2* queue, int n, float* stage, float* grid, int lane,
                                              int r, int dx, int& cur, float2 (&acc)[SpreadCfg<W>::WZ2][2],
@@ -1039,6 +1077,24 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
       acc[q][1] = __ffma2_rn(zp[q], c11, acc[q][1]);
     }
   };
+  if constexpr (SortBatch) {
+    // points that come in bin order only: visit the batch's records by
+    // window corner, so records of one 2^3 block share the accumulators
+    int skey = keep ? key : 0x7fffffff;
+    int sidx = keep ? __popc(kept & ((1u << lane) - 1u)) : 31;
+    warp_sort_pairs(skey, sidx, lane);
+    for (int k = 0; k < nrec; ++k) {
+      const int key_k = __shfl_sync(0xffffffffu, skey, k);
+      const int idx_k = __shfl_sync(0xffffffffu, sidx, k);
+      if (key_k != cur) {
+        if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
+        cur = key_k;
+      }
+      add(stage + idx_k * C::REC);
+    }
+    __syncwarp();
+    return;
+  }
   int k = 0;
   // a batch whose records all share one window (the usual case: points are
   // sorted by cell block) is added with no per-record window check
@@ -1107,19 +1163,26 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
     // next 128's ids (and sorted-order strengths) while these are queued.
     const uint32_t* ids = sorted + sub.y;
     const uint32_t pos0 = (uint32_t)sub.y;
+    const int n = sub.z;
     uint32_t idn[4];
     float vn[4];
     auto fetch = [&](int b) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int i = b + lane + 32 * e;
-        idn[e] = i < sub.z ? __ldg(ids + i) : 0u;
-        if constexpr (Str::kByPos) vn[e] = i < sub.z ? str(0u, pos0 + i) : 0.f;
+        idn[e] = i < n ? __ldg(ids + i) : 0u;
+        if constexpr (Str::kConsume) vn[e] = i < n ? str.v[pos0 + i] : 0.f;
+      }
+      // the consumed sums are zeroed after all four loads are issued
+      if constexpr (Str::kConsume) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (vn[e] != 0.f) str.v[pos0 + b + lane + 32 * e] = 0.f;
       }
     };
     fetch(0);
     int q = 0;   // queued points
-    for (int base = 0; base < sub.z; base += 128) {
+    for (int base = 0; base < n; base += 128) {
       uint32_t idc[4];
       float vc[4];
 #pragma unroll
@@ -1127,23 +1190,24 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
         idc[e] = idn[e];
         if constexpr (Str::kByPos) vc[e] = vn[e];
       }
-      if (base + 128 < sub.z) fetch(base + 128);
+      if (base + 128 < n) fetch(base + 128);
       if constexpr (!Str::kByPos) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) vc[e] = base + lane + 32 * e < sub.z ? str(idc[e], 0u) : 0.f;
+        for (int e = 0; e < 4; ++e) vc[e] = base + lane + 32 * e < n ? str(idc[e], 0u) : 0.f;
       }
       // one copy of the batch code (not unrolled: it is large)
 #pragma unroll 1
       for (int e = 0; e < 4; ++e) {
         const uint32_t id_e = e == 0 ? idc[0] : e == 1 ? idc[1] : e == 2 ? idc[2] : idc[3];
         const float v_e = e == 0 ? vc[0] : e == 1 ? vc[1] : e == 2 ? vc[2] : vc[3];
-        const bool nz = base + lane + 32 * e < sub.z && v_e != 0.f;
+        const bool nz = base + lane + 32 * e < n && v_e != 0.f;
         const unsigned m = __ballot_sync(0xffffffffu, nz);
         if (nz) queue[q + __popc(m & ((1u << lane) - 1u))] = make_uint2(id_e, __float_as_uint(v_e));
         q += __popc(m);
         __syncwarp();
         if (q >= 32) {
-          spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, 32, stage, grid, lane, r, dx, cur, acc, err);
+          spread_batch<W, Pts, Str::kSortBatch>(pts, ep, nf, bx, by, bz, queue, 32, stage, grid, lane, r, dx, cur, acc,
+                                                   err);
           uint2 tail = make_uint2(0u, 0u);
           if (lane < q - 32) tail = queue[32 + lane];
           __syncwarp();
@@ -1153,7 +1217,9 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
         }
       }
     }
-    if (q > 0) spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, q, stage, grid, lane, r, dx, cur, acc, err);
+    if (q > 0)
+      spread_batch<W, Pts, Str::kSortBatch>(pts, ep, nf, bx, by, bz, queue, q, stage, grid, lane, r, dx, cur, acc,
+                                            err);
     if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
     __syncwarp();
     // add the subgrid to the fine grid and clear it: rows of 12 stored x
@@ -1245,14 +1311,17 @@ int grid_for(int64_t n, int threads = 256) {
 
 // Counting sort of npts points by tap-origin cell into `sorted`.
 template <int W, class Pts>
-int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cudaStream_t s) {
+int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cudaStream_t s,
+                bool bin_only = false) {
   BinSort& b = g.bins;
   SortGeom geom{g.nf, b.nb[0], b.nb[1], b.nb[2]};
   SPF_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int) * b.nkeys, s));
   SPF_CUDA(cudaMemsetAsync(b.fill, 0, sizeof(int) * b.nkeys, s));
   const unsigned nb = (unsigned)ceil_div(npts, 256);
-  SPF_TRY(launch("key_count_kernel", s,
-                 [&] { key_count_kernel<W, Pts><<<nb, 256, 0, s>>>(pts, npts, geom, b.count); }));
+  SPF_TRY(launch("key_count_kernel", s, [&] {
+    if (bin_only) key_count_kernel<W, Pts, true><<<nb, 256, 0, s>>>(pts, npts, geom, b.count);
+    else key_count_kernel<W, Pts, false><<<nb, 256, 0, s>>>(pts, npts, geom, b.count);
+  }));
   SPF_TRY(launch("scan_sums_kernel", s,
                  [&] { scan_sums_kernel<<<kScanBlocks, 256, 0, s>>>(b.count, b.nkeys, b.block_sums); }));
   SPF_TRY(launch("scan_block_sums_kernel", s, [&] {
@@ -1262,7 +1331,8 @@ int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cuda
     scan_apply_kernel<<<kScanBlocks, 256, 0, s>>>(b.count, b.nkeys, b.block_sums, b.start);
   }));
   return launch("key_scatter_kernel", s, [&] {
-    key_scatter_kernel<W, Pts><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err);
+    if (bin_only) key_scatter_kernel<W, Pts, true><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err);
+    else key_scatter_kernel<W, Pts, false><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err);
   });
 }
 
@@ -1303,9 +1373,10 @@ int interp_w(spf_plan* P, Pts pts, int64_t npts, bool use_sort, float* out, cuda
 
 // Sort the points of grid g into `set` and cut its bins into subproblems.
 template <int W, class Pts>
-int sort_and_cut(spf_plan* P, Grid& g, Pts pts, int64_t npts, SortedSet& set, int* err, cudaStream_t s) {
+int sort_and_cut(spf_plan* P, Grid& g, Pts pts, int64_t npts, SortedSet& set, int* err, cudaStream_t s,
+                 bool bin_only = false) {
   BinSort& b = g.bins;
-  SPF_TRY((sort_points<W, Pts>(g, set.ids, pts, npts, err, s)));
+  SPF_TRY((sort_points<W, Pts>(g, set.ids, pts, npts, err, s, bin_only)));
   SPF_CUDA(cudaMemsetAsync(set.nsubs, 0, 2 * sizeof(int), s));
   return launch("build_subs_kernel", s, [&] {
     build_subs_kernel<<<(unsigned)ceil_div(b.nbins, 256), 256, 0, s>>>(b.start, b.nbins, set.subs,
@@ -1493,8 +1564,10 @@ int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* i
                     float* const* cnt_tab, const float* images, const int* oidx, int n_img, int chunk, int n_total,
                     const float* D, float b_scale, int* err, cudaStream_t s) {
   for (int c = 0; c < nsets; ++c) {
-    const spf_points* S = sets[c];
-    SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)S->M * S->P2, s));
+    spf_points* S = sets[c];
+    // a compacted spread leaves the sums zeroed: no clearing pass then
+    if (!S->cls_zero) SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)S->M * S->P2, s));
+    S->cls_zero = false;
     SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
   }
   if (n_img == 0 || nsets == 0) return SPF_OK;
@@ -1529,7 +1602,12 @@ int points_build(spf_plan* P, spf_points* S, cudaStream_t s) {
   if (npts == 0) return SPF_OK;
   const float4* q4 = reinterpret_cast<const float4*>(S->quats);
   QuatPts pn{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
-  SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->g, pn, npts, S->setN, P->err, s))));
+  // slicing needs bin order only (its window is the bin's; the right-hand-
+  // side spread orders each batch by window itself); leaving the points of
+  // a bin in the sort's meeting order keeps runs of one orientation's
+  // neighbouring pixels together, so the interpolation's stores touch fewer
+  // sectors
+  SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->g, pn, npts, S->setN, P->err, s, true))));
   if (S->flags & SPF_POINTS_SLICE_ONLY) return SPF_OK;
   SPF_TRY(launch("inverse_order_kernel", s, [&] {
     inverse_order_kernel<<<grid_for(npts), 256, 0, s>>>(S->setN.ids, npts, S->invN);
@@ -1553,8 +1631,9 @@ int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oid
                  cudaStream_t s, int mode, bool want_rhs, bool want_kernel) {
   const int64_t npts = (int64_t)S->M * S->P2;
   if (!(mode & kMergeSumsDone)) {
-  SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)npts, s));
-  SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
+    if (!S->cls_zero) SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)npts, s));
+    SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
+    S->cls_zero = false;
   }
   if (n_img > 0 && !(mode & kMergeSumsDone)) {
     const int chunks = (int)ceil_div(S->P2, 1024);
@@ -1568,9 +1647,12 @@ int merge_points(spf_plan* P, spf_points* S, const float* images, const int* oid
   const bool clear = (mode & kMergeClear) != 0, finish = (mode & kMergeFinish) != 0;
   if (want_rhs) {
     QuatPts pts{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
+    // the spread reads the sums in sorted order and zeroes the nonzero ones,
+    // so the set's sums are all zero afterwards
     StrSorted str{S->cls};
     SPF_W_SWITCH(P->w, SPF_TRY((spread_sorted<W, QuatPts, StrSorted>(P, P->g, pts, str, npts, S->setN,
                                                                     P->err, s, clear))));
+    S->cls_zero = true;
     if (finish) SPF_TRY(type1_finish(P, P->g, rhs, accumulate, s));
   }
   if (want_kernel) {

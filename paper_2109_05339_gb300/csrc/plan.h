@@ -108,6 +108,7 @@ struct spf_points {
   uint32_t* invN = nullptr;   // position of point id in setN's sorted order
   float* cls = nullptr;       // class sums of weighted images, in setN's sorted order
   float* cnt = nullptr;       // M class counts
+  bool cls_zero = false;      // cls holds zeros only (the right-hand-side spread consumed it)
 };
 
 namespace spf {

@@ -31,7 +31,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import SPF_IMAGES_F32, SPF_IMAGES_U16, MtipConfig, check, lib
+from ._lib import SPF_IMAGES_F32, SPF_IMAGES_U16, SPF_UPLOAD_COPY, SPF_UPLOAD_SM, MtipConfig, check, lib
 from .api import COUNT_DTYPES, PRECISIONS, Matcher, Plan, _dev_index, _f32, _ptr, _stream
 from .dist import allreduce_sum_, global_count
 
@@ -246,6 +246,20 @@ class MTIP:
                                           int(cg_iters), float(lam_rel), _ptr(best_out), _ptr(x_out),
                                           C.byref(lam), _stream(self.device)))
         return best_out, x_out, lam.value
+
+    def set_upload(self, mode):
+        """How iteration_host moves the images: 'sm' (default: a kernel reads
+        the page-locked host buffer; falls back to the copy engines for
+        buffers that are not one mapped page-locked range) or 'copy' (copy
+        engines only)."""
+        check(lib.spf_mtip_set_upload(self._h, {"copy": SPF_UPLOAD_COPY, "sm": SPF_UPLOAD_SM}[mode]))
+
+    def last_upload_ms(self):
+        """Device time of the latest image upload of iteration_host (-1 before
+        the first); waits for it."""
+        ms = C.c_float()
+        check(lib.spf_mtip_last_upload_ms(self._h, C.byref(ms)))
+        return ms.value
 
     def status(self):
         check(lib.spf_mtip_status(self._h))

@@ -114,3 +114,72 @@ def test_iteration_with_a_process_group_equals_without(c1):
     np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][2] == out[1][2]
     assert rel_l2(out[1][1], out[0][1]) < 1e-6
+
+
+def test_repeated_iterations_reuse_zeroed_class_sums(c1):
+    """Kept point sets: each merge spreads only the nonzero class sums and
+    leaves them zeroed, so the next iteration forms its sums without a
+    clearing pass. Three iterations on the same inputs give the same matches
+    and, up to the order of atomic additions, the same model as the first
+    and as the oracle."""
+    import torch
+    from paper_2109_05339_gb300 import MTIP
+    pb, counts, s, ref = c1
+    N, P2, M, n = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0], counts.shape[0]
+    drv = MTIP(N, 1.0, P2, n, M, orient_chunk=25, cache_points=True)
+    args = (to_dev(pb.A.astype(np.float32)), to_dev(pb.quats.astype(np.float32)),
+            to_dev(pb.q_lab.astype(np.float32)), to_dev(counts.astype(np.float32)), 1.0 / s)
+    outs = []
+    for _ in range(3):
+        res, x, lam = drv.iteration(*args, cg_iters=3)
+        torch.cuda.synchronize()
+        outs.append((res["best"].cpu().numpy(), x.cpu().numpy().copy()))
+    drv.plan.status()
+    for best, x in outs[1:]:
+        np.testing.assert_array_equal(best, outs[0][0])
+        assert rel_l2(x, outs[0][1]) < 1e-6
+    # a fourth merge (at the oracle's argmins) on the sums left zeroed
+    x2, _ = drv.solve(*args, torch.as_tensor(ref["match"]["best"], dtype=torch.int32, device="cuda"), cg_iters=3)
+    torch.cuda.synchronize()
+    assert rel_l2(x2.cpu().numpy(), ref["x"]) < 1e-5
+    drv.close()
+
+
+@pytest.mark.parametrize("mode,pinned", [("sm", True), ("copy", True), ("sm", False)])
+def test_host_buffer_iteration_equals_device_iteration(c1, mode, pinned):
+    """The iteration from host buffers (16-bit counts; page-locked images read
+    by the SMs or moved by the copy engines, or pageable images, which take
+    the copy engines in either mode) gives the matches and the merged model
+    of the iteration on device buffers, call after call (the two input slots
+    alternate)."""
+    import torch
+    from paper_2109_05339_gb300 import MTIP
+    pb, counts, s, ref = c1
+    N, P2, M, n = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0], counts.shape[0]
+    # 16-bit counts (the c1 images hold up to about 9e4 photons a pixel: halved)
+    c16 = np.floor(counts / 2).astype(np.uint16)
+    assert c16.max() > 32767 and c16.max() == np.floor(counts.max() / 2)   # the top bit is used and kept
+    q = to_dev(pb.quats.astype(np.float32))
+    ql = to_dev(pb.q_lab.astype(np.float32))
+    drv = MTIP(N, 1.0, P2, n, M, cache_points=True, host_images="u16")
+    drv.set_orientations(q, ql)
+    drv.set_upload(mode)
+    A_h = torch.from_numpy(pb.A.astype(np.float32))
+    img_h = torch.from_numpy(c16.view(np.int16))
+    if pinned:
+        A_h, img_h = A_h.pin_memory(), img_h.pin_memory()
+    outs = []
+    for _ in range(3):
+        best, x, lam = drv.iteration_host(A_h, img_h, 2.0 / s, cg_iters=3)
+        torch.cuda.synchronize()
+        outs.append((best.numpy().copy(), x.numpy().copy(), lam))
+    assert drv.last_upload_ms() >= 0.0
+    res, xd, lamd = drv.iteration(to_dev(pb.A.astype(np.float32)), q, ql, to_dev(c16.astype(np.float32)),
+                                  2.0 / s, cg_iters=3)
+    torch.cuda.synchronize()
+    drv.status()
+    for best, x, lam in outs:
+        np.testing.assert_array_equal(best, res["best"].cpu().numpy())
+        assert lam == lamd
+        assert rel_l2(x, xd.cpu().numpy()) < 1e-6
+    drv.close()
