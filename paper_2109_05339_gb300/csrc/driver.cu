@@ -206,18 +206,21 @@ size_t image_elem(int type) { return type == SPF_IMAGES_U16 ? 2 : 4; }
 
 // FP32 view of the caller's images: 16-bit counts converted into img32.
 // Copy of n16 16-byte vectors from page-locked host memory mapped into the
-// device's address space: the SMs read over the CPU-GPU link, four vectors
-// in flight per thread.
+// device's address space: the SMs read over the CPU-GPU link, kUploadVec
+// vectors in flight per thread, so that a few CTAs (few SMs taken from the
+// call computing alongside) keep the link busy.
+constexpr int kUploadVec = 8;
+constexpr int kUploadCtas = 32;
 __global__ void __launch_bounds__(512) upload_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
                                                      size_t n16) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += 4 * stride) {
-    uint4 v[4];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += kUploadVec * stride) {
+    uint4 v[kUploadVec];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < kUploadVec; ++k)
       if (i + k * stride < n16) v[k] = src[i + k * stride];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < kUploadVec; ++k)
       if (i + k * stride < n16) dst[i + k * stride] = v[k];
   }
 }
@@ -245,11 +248,9 @@ int upload_images(spf_mtip* h, void* dst, const void* src, size_t bytes, cudaStr
     const void* dsrc = mapped_range(src, bytes);
     if (dsrc && ((uintptr_t)dsrc & 15) == 0 && ((uintptr_t)dst & 15) == 0) {
       const size_t n16 = bytes / 16, tail = bytes - 16 * n16;
-      int sms = 152;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->cfg.device);
       if (n16 > 0)
         SPF_TRY(launch("upload_kernel", s, [&] {
-          upload_kernel<<<sms, 512, 0, s>>>(static_cast<const uint4*>(dsrc), static_cast<uint4*>(dst), n16);
+          upload_kernel<<<kUploadCtas, 512, 0, s>>>(static_cast<const uint4*>(dsrc), static_cast<uint4*>(dst), n16);
         }, 2.0 * (double)(16 * n16)));
       if (tail > 0)
         SPF_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + 16 * n16, static_cast<const char*>(src) + 16 * n16,
