@@ -672,6 +672,8 @@ static void points_free(spf_points* S) {
   cudaFree(S->setN.ids);
   cudaFree(S->setN.subs);
   cudaFree(S->setN.nsubs);
+  cudaFree(S->setN.bsubs);
+  cudaFree(S->setN.nbsubs);
   cudaFree(S->setT.ids);
   cudaFree(S->setT.subs);
   cudaFree(S->setT.nsubs);
@@ -712,6 +714,9 @@ int spf_points_create(spf_points** out, spf_plan* plan, const float* quats, int 
   A((void**)&S->setN.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
   A((void**)&S->setN.subs, sizeof(int4) * S->setN.max_subs, "subproblems");
   A((void**)&S->setN.nsubs, 2 * sizeof(int), "subproblem count");
+  S->setN.max_bsubs = 8 * (int64_t)plan->g.bins.nbins + npts / kSubPts + 1;
+  A((void**)&S->setN.bsubs, sizeof(int4) * S->setN.max_bsubs, "block subproblems");
+  A((void**)&S->setN.nbsubs, 2 * sizeof(int), "block subproblem count");
   if (full) {
     A((void**)&S->setT.ids, sizeof(uint32_t) * std::max<int64_t>(npts, 1), "sorted ids");
     A((void**)&S->setT.subs, sizeof(int4) * S->setT.max_subs, "subproblems");

@@ -175,6 +175,8 @@ void mtip_free(spf_mtip* h) {
   cudaFree(h->stream_set.setN.ids);
   cudaFree(h->stream_set.setN.subs);
   cudaFree(h->stream_set.setN.nsubs);
+  cudaFree(h->stream_set.setN.bsubs);
+  cudaFree(h->stream_set.setN.nbsubs);
   cudaFree(h->quats_sorted);
   cudaFree(h->qlab);
   cudaFree(h->order);
@@ -424,6 +426,9 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
     A((void**)&S.setN.ids, sizeof(uint32_t) * (size_t)np, "streamed sorted ids");
     A((void**)&S.setN.subs, sizeof(int4) * (size_t)S.setN.max_subs, "streamed subproblems");
     A((void**)&S.setN.nsubs, 2 * sizeof(int), "streamed subproblem count");
+    S.setN.max_bsubs = 8 * (int64_t)h->plan->g.bins.nbins + np / kSubPts + 1;
+    A((void**)&S.setN.bsubs, sizeof(int4) * (size_t)S.setN.max_bsubs, "streamed block subproblems");
+    A((void**)&S.setN.nbsubs, 2 * sizeof(int), "streamed block subproblem count");
   }
   if (rc == SPF_OK && c.host_image_type >= 0) {
     h->host_path = true;

@@ -128,25 +128,20 @@ struct ExplicitPts {
 struct StrPtr {        // v[id]
   static constexpr bool kByPos = false;
   static constexpr bool kConsume = false;
-  static constexpr bool kSortBatch = false;
   const float* v;
   __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const { return __ldg(v + id); }
 };
 // v[pos]: strengths stored in the sorted order (coalesced), consumed: each
 // entry is read by one warp, which sets a nonzero one back to zero, so the
 // array is all zeros after the spread (class sums need no clearing pass).
-// The slicing point set these belong to is sorted by bin only, so each
-// staged batch is ordered by window before it is added.
 struct StrSorted {
   static constexpr bool kByPos = true;
   static constexpr bool kConsume = true;
-  static constexpr bool kSortBatch = true;
   float* v;
 };
 struct StrImage {      // D[p] * scale * image[id]
   static constexpr bool kByPos = false;
   static constexpr bool kConsume = false;
-  static constexpr bool kSortBatch = false;
   const float* img;
   const float* D;
   FastDiv P2;
@@ -159,7 +154,6 @@ struct StrImage {      // D[p] * scale * image[id]
 struct StrWeights {    // D[p] (ones if D is NULL)
   static constexpr bool kByPos = false;
   static constexpr bool kConsume = false;
-  static constexpr bool kSortBatch = false;
   const float* D;
   FastDiv P2;
   __device__ __forceinline__ float operator()(uint32_t id, uint32_t) const {
@@ -170,7 +164,6 @@ struct StrWeights {    // D[p] (ones if D is NULL)
 struct StrCount {     // D[p] * count[j] for point id = j * P2 + p
   static constexpr bool kByPos = false;
   static constexpr bool kConsume = false;
-  static constexpr bool kSortBatch = false;
   const float* cnt;
   const float* D;
   FastDiv P2;
@@ -279,11 +272,11 @@ struct SortGeom {
 };
 
 // Sort key of a point: its tap-origin cell, bin-major, the cells of a bin
-// ordered by their 2^3 cell block. With BinOnly every cell of a bin gets the
-// bin's first key, so a bin's points keep the order in which the sort meets
+// ordered by their 2^3 cell block. With BlockOnly the cells of one 2^3 block
+// share a key, so a block's points keep the order in which the sort meets
 // them (runs of neighbouring pixels of one orientation stay together)
 // instead of being ordered by cell.
-template <int W, bool BinOnly = false>
+template <int W, bool BlockOnly = false>
 __device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
   constexpr int H = W / 2;
   int cx = wrap1((int)ceilf(u.x - 0.5f * W) + H, g.nf);
@@ -294,8 +287,8 @@ __device__ __forceinline__ int point_key(float3 u, const SortGeom& g) {
   // cell inside the 4^3 bin, ordered by its 2^3 cell pair block first: the
   // points of one block are contiguous (the spreading accumulates a block's
   // points in registers)
-  if (BinOnly) return bin << (3 * B);
   const int pair = (((cz >> 1) & 1) << 2) | (((cy >> 1) & 1) << 1) | ((cx >> 1) & 1);
+  if (BlockOnly) return (bin << (3 * B)) | (pair << 3);
   const int sub = ((cz & 1) << 2) | ((cy & 1) << 1) | (cx & 1);
   return (bin << (3 * B)) | (pair << 3) | sub;
 }
@@ -318,21 +311,21 @@ __device__ __forceinline__ KeyRun key_run(int key) {
   return {leader, lane - leader, next - lane};
 }
 
-template <int W, class Pts, bool BinOnly>
+template <int W, class Pts, bool BlockOnly>
 __global__ void key_count_kernel(Pts pts, int64_t npts, SortGeom g, int* __restrict__ count) {
   int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int key = -1;
-  if (id < npts) key = point_key<W, BinOnly>(pts((uint32_t)id), g);
+  if (id < npts) key = point_key<W, BlockOnly>(pts((uint32_t)id), g);
   const KeyRun run = key_run(key);
   if (key >= 0 && run.rank == 0) atomicAdd(count + key, run.len);
 }
 
-template <int W, class Pts, bool BinOnly>
+template <int W, class Pts, bool BlockOnly>
 __global__ void key_scatter_kernel(Pts pts, int64_t npts, SortGeom g, const int* __restrict__ start,
                                    int* __restrict__ fill, uint32_t* __restrict__ sorted, int* err) {
   int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int key = -1;
-  if (id < npts) key = point_key<W, BinOnly>(pts((uint32_t)id), g);
+  if (id < npts) key = point_key<W, BlockOnly>(pts((uint32_t)id), g);
   const KeyRun run = key_run(key);
   int base = 0;
   if (key >= 0 && run.rank == 0) base = atomicAdd(fill + key, run.len);
@@ -453,6 +446,30 @@ __global__ void build_subs_kernel(const int* __restrict__ start, int nbins, int4
     return;
   }
   for (int q = 0; q < k; ++q) subs[o + q] = make_int4(b, s0 + q * kSubPts, min(kSubPts, c - q * kSubPts), 0);
+}
+
+// Cut each 2^3 cell block's sorted range (keys bin 512 + block 8 .. + 7) into
+// subproblems of at most kSubPts points; the block is numbered on the grid
+// of blocks (2 nb per axis).
+__global__ void build_block_subs_kernel(const int* __restrict__ start, int nbins, int nb0, int nb1,
+                                        int4* __restrict__ subs, int64_t max_subs, int* __restrict__ nsubs,
+                                        int* err) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nbins * 8) return;
+  const int b = q >> 3, pr = q & 7;
+  const int s0 = start[(int64_t)b * kBinCells + pr * 8], s1 = start[(int64_t)b * kBinCells + pr * 8 + 8];
+  const int c = s1 - s0;
+  if (c <= 0) return;
+  const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
+  const int kx = 2 * bx + (pr & 1), ky = 2 * by + ((pr >> 1) & 1), kz = 2 * bz + (pr >> 2);
+  const int blk = (kz * (2 * nb1) + ky) * (2 * nb0) + kx;
+  const int k = (c + kSubPts - 1) / kSubPts;
+  const int o = atomicAdd(nsubs, k);
+  if (o + k > max_subs) {
+    atomicOr(err, 1);
+    return;
+  }
+  for (int u = 0; u < k; ++u) subs[o + u] = make_int4(blk, s0 + u * kSubPts, min(kSubPts, c - u * kSubPts), 0);
 }
 
 // Class sums: cls[inv[j P2 + p]] += b_scale D[p] img[i][p] and cnt[j] += 1
@@ -642,25 +659,30 @@ __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G
 }
 
 // ---- type 2 on the tensor cores -------------------------------------------
-// For the points of one bin (4^3 cells) all W^3 taps lie in the S^3 window
-// of G (S = W + 3) whose corner is the bin's first cell minus H. With the
+// For the points of one block of B^3 cells (B = 2: a 2^3 cell block of the
+// sorted set) all W^3 taps lie in the S^3 window of G (S = W + B - 1) whose
+// corner is the block's first cell minus H. With the
 // window as the matrix B[n][x] = G[z][y][x], n = z S + y, and each point's x
 // weights placed at their window columns, A[p][x] = phi_x,p(x) (zero outside
 // its W columns), the product T = A B^T holds T[p][n] = sum_x G[z][y][x]
 // phi_x,p(x), and c_p = sum_(z,y) T[p][z S + y] phi_z,p(z) phi_y,p(y). T is
 // formed by tcgen05.mma (kind::tf32; M = 128 points, N = S^2 rounded up to
-// 16, K = 16 window columns) into tensor memory; one thread per point reads
-// its row back and contracts it with its z and y weights.
+// 16, K = 8 window columns per step) into tensor memory; one thread per
+// point reads its row back and contracts it with its z and y weights. At
+// w = 7 the window is 8^3: N = 64, one K step.
 //
 // FP32 accuracy from TF32 inputs: every operand value v is split into
 // hi = tf32(v) and lo = v - hi, and T = A_hi B_hi + A_hi B_lo + A_lo B_hi;
 // the dropped A_lo B_lo term and the tensor core's truncation of lo are
 // O(2^-21) relative. Both parts share a 128-byte swizzled row of the operand
 // tile: hi at K 0..15, lo at K 16..31.
+constexpr int kIBlockLog = 1;                       // interpolation blocks of 2^3 cells
+constexpr int kIBlock = 1 << kIBlockLog;
+
 template <int W>
 struct InterpTcCfg {
   static constexpr int H = W / 2;
-  static constexpr int S = kBin + W - 1;            // window cells per axis
+  static constexpr int S = kIBlock + W - 1;         // window cells per axis
   static constexpr int NN = ((S * S + 15) / 16) * 16;   // MMA N
   static constexpr int KSTEPS = S <= 8 ? 1 : 2;     // 8 window columns per MMA
   static constexpr int PTS = 128;                   // points per MMA (M)
@@ -701,8 +723,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
       ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// e[i] = w[i - o] for 0 <= i - o < W, else 0; o in [0, 3]; i in [0, L).
-template <int W, int L>
+// e[i] = w[i - o] for 0 <= i - o < W, else 0; o in [0, MAXO]; i in [0, L).
+template <int W, int L, int MAXO = 3>
 __device__ __forceinline__ void shift_weights(const float* w, int o, float* e) {
   float t[L];
 #pragma unroll
@@ -712,7 +734,7 @@ __device__ __forceinline__ void shift_weights(const float* w, int o, float* e) {
     t[i] = (o & 1) ? b : a;
   }
 #pragma unroll
-  for (int i = 0; i < L; ++i) e[i] = (o & 2) ? (i >= 2 ? t[i - 2] : 0.f) : t[i];
+  for (int i = 0; i < L; ++i) e[i] = MAXO >= 2 && (o & 2) ? (i >= 2 ? t[i - 2] : 0.f) : t[i];
 }
 
 template <int W, class Pts>
@@ -767,17 +789,21 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
     __syncthreads();
     if (stop) break;
     const int4 sub = subs[sidx];
-    const int bx = sub.x % g.nb0, by = (sub.x / g.nb0) % g.nb1, bz = sub.x / (g.nb0 * g.nb1);
-    const int ox0 = bx * kBin - C::H, oy0 = by * kBin - C::H, oz0 = bz * kBin - C::H;
-    // window -> B (hi | lo), 4 columns per task; every load of the thread is
+    // block coordinates on the grid of kIBlock^3-cell blocks
+    const int nbx = g.nb0 << (kBinLog - kIBlockLog), nby = g.nb1 << (kBinLog - kIBlockLog);
+    const int bx = sub.x % nbx, by = (sub.x / nbx) % nby, bz = sub.x / (nbx * nby);
+    const int ox0 = bx * kIBlock - C::H, oy0 = by * kIBlock - C::H, oz0 = bz * kIBlock - C::H;
+    // window -> B (hi | lo), 4 columns per task (the window's S columns and
+    // the zeros up to the K steps' columns); every load of the thread is
     // issued before the first is used
     {
-      constexpr int TASKS = S * S * 4, ITER = (TASKS + 127) / 128;
+      constexpr int CH = C::KSTEPS * 2;   // 4-column chunks the MMA reads
+      constexpr int TASKS = S * S * CH, ITER = (TASKS + 127) / 128;
       float v[ITER][4];
 #pragma unroll
       for (int k = 0; k < ITER; ++k) {
         const int task = t + 128 * k;
-        const int n = task >> 2, c = task & 3;
+        const int n = task / CH, c = task - n * CH;
         const int z = n / S, y = n - z * S;
         const float* row = G + ((size_t)wrap1(oz0 + z, nf) * nf + wrap1(oy0 + y, nf)) * nf;
 #pragma unroll
@@ -790,7 +816,7 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
       for (int k = 0; k < ITER; ++k) {
         const int task = t + 128 * k;
         if (task < TASKS) {
-          const int n = task >> 2, c = task & 3;
+          const int n = task / CH, c = task - n * CH;
           float4 hi, lo;
           split_tf32(v[k][0], hi.x, lo.x);
           split_tf32(v[k][1], hi.y, lo.y);
@@ -818,20 +844,22 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
         const int cx = wrap1((int)ceilf(u.x - 0.5f * W) + C::H, nf);
         const int cy = wrap1((int)ceilf(u.y - 0.5f * W) + C::H, nf);
         const int cz = wrap1((int)ceilf(u.z - 0.5f * W) + C::H, nf);
-        ok = (cx >> kBinLog) == bx && (cy >> kBinLog) == by && (cz >> kBinLog) == bz;
+        ok = (cx >> kIBlockLog) == bx && (cy >> kIBlockLog) == by && (cz >> kIBlockLog) == bz;
         if (!ok) atomicOr(err, 1);   // cannot happen when sorting and interpolation agree
-        ox = cx & (kBin - 1);
-        oy = cy & (kBin - 1);
-        oz = cz & (kBin - 1);
+        ox = cx & (kIBlock - 1);
+        oy = cy & (kIBlock - 1);
+        oz = cz & (kIBlock - 1);
       }
       float wx[W], wy[W], wz[W];
       es_weights3<W>(u, ep, wx, wy, wz);
       {
-        // A row t: the x weights at their window columns, hi | lo
-        float ax[16];
-        shift_weights<W, 16>(wx, ox, ax);
+        // A row t: the x weights at their window columns, hi | lo (the
+        // columns the K steps read)
+        constexpr int L = 8 * C::KSTEPS;
+        float ax[L];
+        shift_weights<W, L, kIBlock - 1>(wx, ox, ax);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < L / 4; ++c) {
           float4 hi, lo;
           split_tf32(ok ? ax[4 * c] : 0.f, hi.x, lo.x);
           split_tf32(ok ? ax[4 * c + 1] : 0.f, hi.y, lo.y);
@@ -843,8 +871,8 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
       }
       // y and z weights at their window rows, kept in registers over the MMA
       float ey_r[S], ez_r[S];
-      shift_weights<W, S>(wy, oy, ey_r);
-      shift_weights<W, S>(wz, oz, ez_r);
+      shift_weights<W, S, kIBlock - 1>(wy, oy, ey_r);
+      shift_weights<W, S, kIBlock - 1>(wz, oz, ez_r);
       fence_proxy_async_smem();
       tc_fence_before();
       __syncthreads();
@@ -996,25 +1024,7 @@ __device__ __forceinline__ void flush_columns(float* grid, int lx, int ly, int l
 // Stage points q[0 .. n) of the queue (lane k: point k) and add them to the
 // register accumulators in order, writing the accumulators back to the
 // subgrid whenever the window corner changes.
-// Ascending sort of one (key, value) pair per lane across the warp (bitonic
-// network over shuffles); equal keys keep their own values.
-__device__ __forceinline__ void warp_sort_pairs(int& key, int& val, int lane) {
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int ok = __shfl_xor_sync(0xffffffffu, key, j);
-      const int ov = __shfl_xor_sync(0xffffffffu, val, j);
-      const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
-      if (keep_min ? ok < key : ok > key) {
-        key = ok;
-        val = ov;
-      }
-    }
-  }
-}
-
-template <int W, class Pts, bool SortBatch>
+template <int W, class Pts>
 __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, int nf, int bx, int by, int bz,
                                              const uint2* queue, int n, float* stage, float* grid, int lane,
                                              int r, int dx, int& cur, float2 (&acc)[SpreadCfg<W>::WZ2][2],
@@ -1077,24 +1087,6 @@ __device__ __forceinline__ void spread_batch(const Pts& pts, const EsPoly& ep, i
       acc[q][1] = __ffma2_rn(zp[q], c11, acc[q][1]);
     }
   };
-  if constexpr (SortBatch) {
-    // points that come in bin order only: visit the batch's records by
-    // window corner, so records of one 2^3 block share the accumulators
-    int skey = keep ? key : 0x7fffffff;
-    int sidx = keep ? __popc(kept & ((1u << lane) - 1u)) : 31;
-    warp_sort_pairs(skey, sidx, lane);
-    for (int k = 0; k < nrec; ++k) {
-      const int key_k = __shfl_sync(0xffffffffu, skey, k);
-      const int idx_k = __shfl_sync(0xffffffffu, sidx, k);
-      if (key_k != cur) {
-        if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
-        cur = key_k;
-      }
-      add(stage + idx_k * C::REC);
-    }
-    __syncwarp();
-    return;
-  }
   int k = 0;
   // a batch whose records all share one window (the usual case: points are
   // sorted by cell block) is added with no per-record window check
@@ -1206,7 +1198,7 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
         q += __popc(m);
         __syncwarp();
         if (q >= 32) {
-          spread_batch<W, Pts, Str::kSortBatch>(pts, ep, nf, bx, by, bz, queue, 32, stage, grid, lane, r, dx, cur, acc,
+          spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, 32, stage, grid, lane, r, dx, cur, acc,
                                                    err);
           uint2 tail = make_uint2(0u, 0u);
           if (lane < q - 32) tail = queue[32 + lane];
@@ -1218,7 +1210,7 @@ spread_kernel(Pts pts, Str str, SortGeom g, EsPoly ep, const uint32_t* __restric
       }
     }
     if (q > 0)
-      spread_batch<W, Pts, Str::kSortBatch>(pts, ep, nf, bx, by, bz, queue, q, stage, grid, lane, r, dx, cur, acc,
+      spread_batch<W, Pts>(pts, ep, nf, bx, by, bz, queue, q, stage, grid, lane, r, dx, cur, acc,
                                             err);
     if (cur >= 0) flush_columns<W>(grid, cur & 15, (cur >> 4) & 15, cur >> 8, r, dx, acc);
     __syncwarp();
@@ -1312,14 +1304,14 @@ int grid_for(int64_t n, int threads = 256) {
 // Counting sort of npts points by tap-origin cell into `sorted`.
 template <int W, class Pts>
 int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cudaStream_t s,
-                bool bin_only = false) {
+                bool block_only = false) {
   BinSort& b = g.bins;
   SortGeom geom{g.nf, b.nb[0], b.nb[1], b.nb[2]};
   SPF_CUDA(cudaMemsetAsync(b.count, 0, sizeof(int) * b.nkeys, s));
   SPF_CUDA(cudaMemsetAsync(b.fill, 0, sizeof(int) * b.nkeys, s));
   const unsigned nb = (unsigned)ceil_div(npts, 256);
   SPF_TRY(launch("key_count_kernel", s, [&] {
-    if (bin_only) key_count_kernel<W, Pts, true><<<nb, 256, 0, s>>>(pts, npts, geom, b.count);
+    if (block_only) key_count_kernel<W, Pts, true><<<nb, 256, 0, s>>>(pts, npts, geom, b.count);
     else key_count_kernel<W, Pts, false><<<nb, 256, 0, s>>>(pts, npts, geom, b.count);
   }));
   SPF_TRY(launch("scan_sums_kernel", s,
@@ -1331,7 +1323,7 @@ int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cuda
     scan_apply_kernel<<<kScanBlocks, 256, 0, s>>>(b.count, b.nkeys, b.block_sums, b.start);
   }));
   return launch("key_scatter_kernel", s, [&] {
-    if (bin_only) key_scatter_kernel<W, Pts, true><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err);
+    if (block_only) key_scatter_kernel<W, Pts, true><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err);
     else key_scatter_kernel<W, Pts, false><<<nb, 256, 0, s>>>(pts, npts, geom, b.start, b.fill, sorted, err);
   });
 }
@@ -1342,7 +1334,8 @@ template <int W, class Pts>
 int interp_tc(spf_plan* P, Pts pts, const SortedSet& set, float* out, cudaStream_t s) {
   using C = InterpTcCfg<W>;
   Grid& g = P->g;
-  SPF_CUDA(cudaMemsetAsync(set.nsubs + 1, 0, sizeof(int), s));   // work cursor
+  SPF_CHECK_ARG(set.bsubs != nullptr, "interpolation needs the set's 2^3-block subproblems");
+  SPF_CUDA(cudaMemsetAsync(set.nbsubs + 1, 0, sizeof(int), s));   // work cursor
   SPF_CUDA(cudaFuncSetAttribute(interp_tc_kernel<W, Pts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)C::SMEM));
   SortGeom geom{g.nf, g.bins.nb[0], g.bins.nb[1], g.bins.nb[2]};
@@ -1350,8 +1343,8 @@ int interp_tc(spf_plan* P, Pts pts, const SortedSet& set, float* out, cudaStream
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   return launch("interp_tc_kernel", s, [&] {
-    interp_tc_kernel<W, Pts><<<C::CTAS * sms, 128, C::SMEM, s>>>(g.real, pts, geom, ep, set.ids, set.subs,
-                                                           set.nsubs, out, P->err);
+    interp_tc_kernel<W, Pts><<<C::CTAS * sms, 128, C::SMEM, s>>>(g.real, pts, geom, ep, set.ids, set.bsubs,
+                                                           set.nbsubs, out, P->err);
   });
 }
 
@@ -1374,13 +1367,19 @@ int interp_w(spf_plan* P, Pts pts, int64_t npts, bool use_sort, float* out, cuda
 // Sort the points of grid g into `set` and cut its bins into subproblems.
 template <int W, class Pts>
 int sort_and_cut(spf_plan* P, Grid& g, Pts pts, int64_t npts, SortedSet& set, int* err, cudaStream_t s,
-                 bool bin_only = false) {
+                 bool block_only = false) {
   BinSort& b = g.bins;
-  SPF_TRY((sort_points<W, Pts>(g, set.ids, pts, npts, err, s, bin_only)));
+  SPF_TRY((sort_points<W, Pts>(g, set.ids, pts, npts, err, s, block_only)));
   SPF_CUDA(cudaMemsetAsync(set.nsubs, 0, 2 * sizeof(int), s));
-  return launch("build_subs_kernel", s, [&] {
+  SPF_TRY(launch("build_subs_kernel", s, [&] {
     build_subs_kernel<<<(unsigned)ceil_div(b.nbins, 256), 256, 0, s>>>(b.start, b.nbins, set.subs,
                                                                       set.max_subs, set.nsubs, err);
+  }));
+  if (!set.bsubs) return SPF_OK;
+  SPF_CUDA(cudaMemsetAsync(set.nbsubs, 0, 2 * sizeof(int), s));
+  return launch("build_subs_kernel", s, [&] {
+    build_block_subs_kernel<<<(unsigned)ceil_div((int64_t)b.nbins * 8, 256), 256, 0, s>>>(
+        b.start, b.nbins, b.nb[0], b.nb[1], set.bsubs, set.max_bsubs, set.nbsubs, err);
   });
 }
 
@@ -1602,11 +1601,10 @@ int points_build(spf_plan* P, spf_points* S, cudaStream_t s) {
   if (npts == 0) return SPF_OK;
   const float4* q4 = reinterpret_cast<const float4*>(S->quats);
   QuatPts pn{q4, S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
-  // slicing needs bin order only (its window is the bin's; the right-hand-
-  // side spread orders each batch by window itself); leaving the points of
-  // a bin in the sort's meeting order keeps runs of one orientation's
-  // neighbouring pixels together, so the interpolation's stores touch fewer
-  // sectors
+  // slicing works per 2^3 cell block and the right-hand-side spread per
+  // block window, so the cells of a block share a key: the block's points
+  // stay in the sort's meeting order (runs of one orientation's neighbouring
+  // pixels), and the interpolation's stores touch fewer sectors
   SPF_W_SWITCH(P->w, SPF_TRY((sort_and_cut<W, QuatPts>(P, P->g, pn, npts, S->setN, P->err, s, true))));
   if (S->flags & SPF_POINTS_SLICE_ONLY) return SPF_OK;
   SPF_TRY(launch("inverse_order_kernel", s, [&] {

@@ -61,6 +61,11 @@ struct SortedSet {
   int4* subs = nullptr;
   int* nsubs = nullptr;
   int64_t max_subs = 0;
+  // optional: the same points cut per 2^3 cell block (interpolation's
+  // subproblems), (block, first, npts, 0)
+  int4* bsubs = nullptr;
+  int* nbsubs = nullptr;
+  int64_t max_bsubs = 0;
 };
 
 }  // namespace spf
