@@ -26,6 +26,7 @@
 //     subgrids go back to the fine grid as vector reductions once per
 //     subproblem. No shared-memory atomics are used.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "plan.h"
@@ -676,13 +677,16 @@ __global__ void __launch_bounds__(256) interp_kernel(const float* __restrict__ G
 // the dropped A_lo B_lo term and the tensor core's truncation of lo are
 // O(2^-21) relative. Both parts share a 128-byte swizzled row of the operand
 // tile: hi at K 0..15, lo at K 16..31.
-constexpr int kIBlockLog = 1;                       // interpolation blocks of 2^3 cells
-constexpr int kIBlock = 1 << kIBlockLog;
+// Interpolation works per block of 2^BLOG cells per axis: 2^3 cell blocks
+// where the points are dense, the 4^3 bins where they are sparse (a block's
+// MMA groups of 128 points would then run mostly empty).
+constexpr int kIBlockDense = 256;   // points per 2^3 block from which blocks pay off
 
-template <int W>
+template <int W, int BLOG>
 struct InterpTcCfg {
   static constexpr int H = W / 2;
-  static constexpr int S = kIBlock + W - 1;         // window cells per axis
+  static constexpr int BS = 1 << BLOG;              // block cells per axis
+  static constexpr int S = BS + W - 1;              // window cells per axis
   static constexpr int NN = ((S * S + 15) / 16) * 16;   // MMA N
   static constexpr int KSTEPS = S <= 8 ? 1 : 2;     // 8 window columns per MMA
   static constexpr int PTS = 128;                   // points per MMA (M)
@@ -737,12 +741,12 @@ __device__ __forceinline__ void shift_weights(const float* w, int o, float* e) {
   for (int i = 0; i < L; ++i) e[i] = MAXO >= 2 && (o & 2) ? (i >= 2 ? t[i - 2] : 0.f) : t[i];
 }
 
-template <int W, class Pts>
-__global__ void __launch_bounds__(128, InterpTcCfg<W>::CTAS)
+template <int W, int BLOG, class Pts>
+__global__ void __launch_bounds__(128, InterpTcCfg<W, BLOG>::CTAS)
 interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
                  const uint32_t* __restrict__ sorted, const int4* __restrict__ subs, int* __restrict__ nsubs,
                  float* __restrict__ out, int* err) {
-  using C = InterpTcCfg<W>;
+  using C = InterpTcCfg<W, BLOG>;
   constexpr int S = C::S;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -789,10 +793,10 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
     __syncthreads();
     if (stop) break;
     const int4 sub = subs[sidx];
-    // block coordinates on the grid of kIBlock^3-cell blocks
-    const int nbx = g.nb0 << (kBinLog - kIBlockLog), nby = g.nb1 << (kBinLog - kIBlockLog);
+    // block coordinates on the grid of C::BS^3-cell blocks
+    const int nbx = g.nb0 << (kBinLog - BLOG), nby = g.nb1 << (kBinLog - BLOG);
     const int bx = sub.x % nbx, by = (sub.x / nbx) % nby, bz = sub.x / (nbx * nby);
-    const int ox0 = bx * kIBlock - C::H, oy0 = by * kIBlock - C::H, oz0 = bz * kIBlock - C::H;
+    const int ox0 = bx * C::BS - C::H, oy0 = by * C::BS - C::H, oz0 = bz * C::BS - C::H;
     // window -> B (hi | lo), 4 columns per task (the window's S columns and
     // the zeros up to the K steps' columns); every load of the thread is
     // issued before the first is used
@@ -844,11 +848,11 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
         const int cx = wrap1((int)ceilf(u.x - 0.5f * W) + C::H, nf);
         const int cy = wrap1((int)ceilf(u.y - 0.5f * W) + C::H, nf);
         const int cz = wrap1((int)ceilf(u.z - 0.5f * W) + C::H, nf);
-        ok = (cx >> kIBlockLog) == bx && (cy >> kIBlockLog) == by && (cz >> kIBlockLog) == bz;
+        ok = (cx >> BLOG) == bx && (cy >> BLOG) == by && (cz >> BLOG) == bz;
         if (!ok) atomicOr(err, 1);   // cannot happen when sorting and interpolation agree
-        ox = cx & (kIBlock - 1);
-        oy = cy & (kIBlock - 1);
-        oz = cz & (kIBlock - 1);
+        ox = cx & (C::BS - 1);
+        oy = cy & (C::BS - 1);
+        oz = cz & (C::BS - 1);
       }
       float wx[W], wy[W], wz[W];
       es_weights3<W>(u, ep, wx, wy, wz);
@@ -857,7 +861,7 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
         // columns the K steps read)
         constexpr int L = 8 * C::KSTEPS;
         float ax[L];
-        shift_weights<W, L, kIBlock - 1>(wx, ox, ax);
+        shift_weights<W, L, C::BS - 1>(wx, ox, ax);
 #pragma unroll
         for (int c = 0; c < L / 4; ++c) {
           float4 hi, lo;
@@ -871,8 +875,8 @@ interp_tc_kernel(const float* __restrict__ G, Pts pts, SortGeom g, EsPoly ep,
       }
       // y and z weights at their window rows, kept in registers over the MMA
       float ey_r[S], ez_r[S];
-      shift_weights<W, S, kIBlock - 1>(wy, oy, ey_r);
-      shift_weights<W, S, kIBlock - 1>(wz, oz, ez_r);
+      shift_weights<W, S, C::BS - 1>(wy, oy, ey_r);
+      shift_weights<W, S, C::BS - 1>(wz, oz, ez_r);
       fence_proxy_async_smem();
       tc_fence_before();
       __syncthreads();
@@ -1331,21 +1335,28 @@ int sort_points(Grid& g, uint32_t* sorted, Pts pts, int64_t npts, int* err, cuda
 // Tensor-core interpolation of an already sorted set (its subproblems give
 // the bins) from g.real.
 template <int W, class Pts>
-int interp_tc(spf_plan* P, Pts pts, const SortedSet& set, float* out, cudaStream_t s) {
-  using C = InterpTcCfg<W>;
+int interp_tc(spf_plan* P, Pts pts, const SortedSet& set, int64_t npts, float* out, cudaStream_t s) {
   Grid& g = P->g;
-  SPF_CHECK_ARG(set.bsubs != nullptr, "interpolation needs the set's 2^3-block subproblems");
-  SPF_CUDA(cudaMemsetAsync(set.nbsubs + 1, 0, sizeof(int), s));   // work cursor
-  SPF_CUDA(cudaFuncSetAttribute(interp_tc_kernel<W, Pts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)C::SMEM));
   SortGeom geom{g.nf, g.bins.nb[0], g.bins.nb[1], g.bins.nb[2]};
   const EsPoly& ep = P->poly;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
-  return launch("interp_tc_kernel", s, [&] {
-    interp_tc_kernel<W, Pts><<<C::CTAS * sms, 128, C::SMEM, s>>>(g.real, pts, geom, ep, set.ids, set.bsubs,
-                                                           set.nbsubs, out, P->err);
-  });
+  // 2^3 blocks when a block holds a few MMA groups on average over the
+  // occupied part of the grid (about half the cells), else 4^3 bins
+  const bool blocks = set.bsubs && npts >= (int64_t)kIBlockDense * 8 * g.bins.nbins / 2;
+  auto run = [&](auto blog, const int4* subs, int* nsubs) -> int {
+    constexpr int BLOG = decltype(blog)::value;
+    using C = InterpTcCfg<W, BLOG>;
+    SPF_CUDA(cudaMemsetAsync(nsubs + 1, 0, sizeof(int), s));   // work cursor
+    SPF_CUDA(cudaFuncSetAttribute(interp_tc_kernel<W, BLOG, Pts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)C::SMEM));
+    return launch("interp_tc_kernel", s, [&] {
+      interp_tc_kernel<W, BLOG, Pts><<<C::CTAS * sms, 128, C::SMEM, s>>>(g.real, pts, geom, ep, set.ids, subs,
+                                                                       nsubs, out, P->err);
+    });
+  };
+  if (blocks) return run(std::integral_constant<int, 1>{}, set.bsubs, set.nbsubs);
+  return run(std::integral_constant<int, kBinLog>{}, set.subs, set.nsubs);
 }
 
 template <int W, class Pts>
@@ -1620,7 +1631,7 @@ int slice_points(spf_plan* P, spf_points* S, const float* A, float* out, cudaStr
   if (npts == 0) return SPF_OK;
   SPF_TRY(type2_setup(P, A, s, false));
   QuatPts pts{reinterpret_cast<const float4*>(S->quats), S->qlab, FastDiv((uint32_t)S->P2), P->g.cells_per_q, nullptr, 0, P->err, (float)P->g.nf, 1.f / (float)P->g.nf};
-  SPF_W_SWITCH(P->w, SPF_TRY((interp_tc<W, QuatPts>(P, pts, S->setN, out, s))));
+  SPF_W_SWITCH(P->w, SPF_TRY((interp_tc<W, QuatPts>(P, pts, S->setN, npts, out, s))));
   return SPF_OK;
 }
 

@@ -92,3 +92,38 @@ def test_slice_only_set_slices_identically_and_refuses_merge(c1):
     with pytest.raises(SpfError):
         ps.merge(to_dev(c1["images"]), to_dev(c1["best"], torch.int32))
     ps.close()
+
+
+def test_dense_point_set_slicing_per_cell_block():
+    """A point set dense enough (4,000 orientations of the 16 x 16 detector
+    on the 17^3 model: 1.0e6 points, about 700 per 2^3 cell block) that the
+    interpolation runs per 2^3 block instead of per 4^3 bin; every output
+    against the per-call CUDA-core path, and 4,096 sampled outputs against
+    the FP64 direct sum."""
+    import torch
+    from oracle import nudft
+    from paper_2109_05339_gb300 import Plan, PointSet
+    pb = problem("c1")
+    N = pb.cfg.N
+    rng = np.random.default_rng(32)
+    q = rng.standard_normal((4000, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    quats = to_dev(q.astype(np.float32))
+    qlab = to_dev(pb.q_lab.astype(np.float32))
+    P2 = pb.q_lab.shape[0]
+    plan = Plan(N, 1.0, 1e-6, max_points=4000 * P2)
+    nbins = ((plan.nf + 3) // 4) ** 3
+    assert 4000 * P2 >= 256 * 4 * nbins          # the block path's density threshold
+    ps = PointSet(plan, quats, qlab)
+    A = to_dev(pb.A.astype(np.float32))
+    a = ps.slice(A)
+    b = plan.slice_model(A, quats, qlab)
+    torch.cuda.synchronize()
+    plan.status()
+    assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 2e-6
+    pick = rng.choice(4000 * P2, 4096, replace=False)
+    t = rotation.nufft_points(f32(q.astype(np.float32)), f32(pb.q_lab.astype(np.float32)), N, 1.0).reshape(-1, 3)
+    ref = nudft.type2(f32(pb.A.astype(np.float32)), t[pick]).real
+    assert rel_l2(a.cpu().numpy().reshape(-1)[pick], ref) < 1e-5
+    ps.close()
+    plan.close()
