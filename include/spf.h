@@ -297,6 +297,13 @@ int spf_matcher_destroy(spf_matcher* m);
 int spf_matcher_status(spf_matcher* m);
 int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float img_scale,
                            void* stream);
+/* The same for images given as 16-bit photon counts (n_img x P2 uint16,
+ * device, 8-byte aligned rows read as vectors when P2 % 4 == 0): the
+ * quantised copies and the FP32 re-rank read the counts themselves (exact in
+ * FP32), so no FP32 copy is needed. BF16 and FP8 matchers only
+ * (SPF_ERR_UNSUPPORTED for SPF_FP32, whose CUDA-core path reads FP32 rows). */
+int spf_matcher_set_images_u16(spf_matcher* m, const uint16_t* images, int n_img, float img_scale,
+                               void* stream);
 /* Pixel weights for the distance, d_ij = sum_p D[p] (x_ip - y_jp)^2 (D >= 0;
  * D = 0 excludes a pixel, e.g. behind the beam stop of Sec. II-C). D: P2
  * floats (device) or NULL for all ones. Takes effect for the next

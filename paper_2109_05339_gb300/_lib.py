@@ -81,6 +81,7 @@ PROTOTYPES = {
     "spf_matcher_destroy": (I, [P]),
     "spf_matcher_status": (I, [P]),
     "spf_matcher_set_images": (I, [P, P, I, F, P]),
+    "spf_matcher_set_images_u16": (I, [P, P, I, F, P]),
     "spf_matcher_set_mask": (I, [P, P, P]),
     "spf_matcher_add_slices": (I, [P, P, I, I, P]),
     "spf_matcher_set_schedule": (I, [P, I]),

@@ -414,13 +414,20 @@ class Matcher:
         check(lib.spf_matcher_set_rerank(self._h, int(bool(deferred))))
 
     def set_images(self, images, img_scale=1.0):
-        _f32(images, "images", self.device)
+        """FP32 images, or (BF16 / FP8 matchers) 16-bit photon counts, which
+        the quantisation and the FP32 re-rank read directly."""
+        counts = images.dtype in COUNT_DTYPES
+        if counts:
+            if images.device.type != "cuda" or images.device.index != self.device or not images.is_contiguous():
+                raise ValueError("images must be a contiguous tensor on the matcher's device")
+        else:
+            _f32(images, "images", self.device)
         if images.dim() != 2 or images.shape[1] != self.P2:
             raise ValueError(f"images must be (n, {self.P2})")
         self._images = images          # the C side keeps this pointer
         self.n_img = images.shape[0]
-        check(lib.spf_matcher_set_images(self._h, _ptr(images), self.n_img, float(img_scale),
-                                         _stream(self.device)))
+        fn = lib.spf_matcher_set_images_u16 if counts else lib.spf_matcher_set_images
+        check(fn(self._h, _ptr(images), self.n_img, float(img_scale), _stream(self.device)))
 
     def add_slices(self, slices, orient_offset=0):
         _f32(slices, "slices", self.device)

@@ -113,6 +113,8 @@ int results_launch(spf_matcher* m, int32_t* best_idx, float* best_d, float* seco
                    int32_t* topk_idx, float* topk_d, cudaStream_t s);
 int quantize_rows(spf_matcher* m, const float* src, int rows, float scale, void* dst, float* scales,
                   float* norms, cudaStream_t s);
+int quantize_rows_u16(spf_matcher* m, const uint16_t* src, int rows, float scale, void* dst, float* scales,
+                      float* norms, cudaStream_t s);
 int tc_kpad(int P2, int precision);
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -597,12 +599,36 @@ int spf_matcher_set_images(spf_matcher* m, const float* images, int n_img, float
   if (dev.rc != SPF_OK) return dev.rc;
   cudaStream_t s = as_stream(stream);
   m->images = images;
+  m->images16 = nullptr;
   m->n_img = n_img;
   m->img_scale = img_scale;
   if (m->precision == SPF_FP32)
     SPF_TRY(row_norms_w(images, n_img, m->P2, img_scale, m->wsq, m->x2, s));
   else
     SPF_TRY(quantize_rows(m, images, n_img, img_scale, m->xq, m->xs, m->x2, s));
+  return state_reset(m, s);
+}
+
+int spf_matcher_set_images_u16(spf_matcher* m, const uint16_t* images, int n_img, float img_scale,
+                               void* stream) {
+  clear_error();
+  SPF_CHECK_ARG(m != nullptr, "matcher is NULL");
+  if (m->precision == SPF_FP32) {
+    set_error("16-bit images need a BF16 or FP8 matcher");
+    return SPF_ERR_UNSUPPORTED;
+  }
+  SPF_CHECK_ARG(n_img >= 0 && n_img <= m->max_images, "n_img %d exceeds max_images %d", n_img,
+                m->max_images);
+  SPF_CHECK_ARG(n_img == 0 || images, "images is NULL");
+  SPF_CHECK_ARG(((uintptr_t)images & 1) == 0, "images must be 2-byte aligned");
+  DeviceScope dev(m->device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  cudaStream_t s = as_stream(stream);
+  m->images = nullptr;
+  m->images16 = images;
+  m->n_img = n_img;
+  m->img_scale = img_scale;
+  SPF_TRY(quantize_rows_u16(m, images, n_img, img_scale, m->xq, m->xs, m->x2, s));
   return state_reset(m, s);
 }
 

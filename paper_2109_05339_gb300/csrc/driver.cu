@@ -40,8 +40,8 @@ int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats,
               bool want_kernel);
 int merge_begin(spf_plan* P, cudaStream_t s);
 int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* inv_tab, float* const* cls_tab,
-                    float* const* cnt_tab, const float* images, const int* oidx, int n_img, int chunk, int n_total,
-                    const float* D, float b_scale, int* err, cudaStream_t s);
+                    float* const* cnt_tab, const float* images, const uint16_t* images16, const int* oidx, int n_img,
+                    int chunk, int n_total, const float* D, float b_scale, int* err, cudaStream_t s);
 int merge_finish(spf_plan* P, float* rhs, float* kernel_hat, int accumulate, cudaStream_t s);
 int cg_begin(spf_plan* P, const float* khat, double lambda, const float* rhs, const float* x0,
              float* x, double* res, cudaStream_t s);
@@ -118,7 +118,8 @@ struct spf_mtip {
   float** cnt_tab = nullptr;
   spf_points stream_set;           // streaming: one slice-only set, re-sorted per chunk
   float* slices = nullptr;         // orient_chunk x P2, or n_orient x P2 when kept
-  float* img32 = nullptr;          // max_images x P2: 16-bit counts converted to FP32
+  float* img32 = nullptr;          // max_images x P2: 16-bit counts converted to FP32 (FP32
+                                   // matching or streamed merges only)
   int* best_sorted = nullptr;      // max_images
   int* best = nullptr;             // max_images (caller numbering)
   int* topk_tmp = nullptr;         // max_images x topk
@@ -206,7 +207,6 @@ void mtip_free(spf_mtip* h) {
 
 size_t image_elem(int type) { return type == SPF_IMAGES_U16 ? 2 : 4; }
 
-// FP32 view of the caller's images: 16-bit counts converted into img32.
 // Copy of n16 16-byte vectors from page-locked host memory mapped into the
 // device's address space: the SMs read over the CPU-GPU link, kUploadVec
 // vectors in flight per thread, so that a few CTAs (few SMs taken from the
@@ -264,22 +264,39 @@ int upload_images(spf_mtip* h, void* dst, const void* src, size_t bytes, cudaStr
   return SPF_OK;
 }
 
-int images_f32(spf_mtip* h, const void* images, int type, int n_img, const float** out, cudaStream_t s) {
+// The images of a call: FP32 rows, or 16-bit photon counts, which the BF16 /
+// FP8 matcher and the class sums of kept point sets read themselves; an
+// FP32 copy is made only for the consumers that need one (the FP32 matcher,
+// the streamed merge).
+struct ImgIn {
+  const float* f = nullptr;
+  const uint16_t* u = nullptr;
+};
+
+int images_in(spf_mtip* h, const void* images, int type, int n_img, bool match, bool merge, ImgIn* in,
+              cudaStream_t s) {
   if (type == SPF_IMAGES_F32) {
-    *out = static_cast<const float*>(images);
+    in->f = static_cast<const float*>(images);
     return SPF_OK;
   }
-  SPF_TRY(counts_to_f32(static_cast<const uint16_t*>(images), (int64_t)n_img * h->cfg.P2, h->img32, s));
-  *out = h->img32;
+  in->u = static_cast<const uint16_t*>(images);
+  const bool need_f32 = (match && h->matcher->precision == SPF_FP32) || (merge && !h->cache_points);
+  if (need_f32) {
+    SPF_TRY(counts_to_f32(in->u, (int64_t)n_img * h->cfg.P2, h->img32, s));
+    in->f = h->img32;
+  }
   return SPF_OK;
 }
 
 // Slicing and matching over every orientation chunk; results in the driver's
 // numbering into best_sorted (and the matcher's candidate lists).
-int match_core(spf_mtip* h, const float* A, const float* img, int n_img, float img_scale, cudaStream_t s) {
+int match_core(spf_mtip* h, const float* A, const ImgIn& img, int n_img, float img_scale, cudaStream_t s) {
   spf_plan* P = h->plan;
   const int P2 = h->cfg.P2, M = h->cfg.n_orient;
-  SPF_TRY(spf_matcher_set_images(h->matcher, img, n_img, img_scale, s));
+  if (img.u && h->matcher->precision != SPF_FP32)
+    SPF_TRY(spf_matcher_set_images_u16(h->matcher, img.u, n_img, img_scale, s));
+  else
+    SPF_TRY(spf_matcher_set_images(h->matcher, img.f, n_img, img_scale, s));
   for (int c = 0, c0 = 0; c0 < M; ++c, c0 += h->orient_chunk) {
     const int m = std::min(h->orient_chunk, M - c0);
     float* out = h->keep_slices ? h->slices + (size_t)c0 * P2 : h->slices;
@@ -298,7 +315,7 @@ int match_core(spf_mtip* h, const float* A, const float* img, int n_img, float i
 }
 
 // Deferred merge at driver-numbered orientations into rhs and khat.
-int merge_core(spf_mtip* h, const float* img, int n_img, float img_scale, const int* best_sorted, float* rhs,
+int merge_core(spf_mtip* h, const ImgIn& img, int n_img, float img_scale, const int* best_sorted, float* rhs,
                float* khat, cudaStream_t s) {
   spf_plan* P = h->plan;
   const int P2 = h->cfg.P2, M = h->cfg.n_orient;
@@ -306,15 +323,16 @@ int merge_core(spf_mtip* h, const float* img, int n_img, float img_scale, const 
   if (h->cache_points) {
     // one pass over the images forms every set's class sums, then each set
     // spreads its sums (leaving them zeroed for the next call) and its counts
-    SPF_TRY(class_sums_sets(h->sets.data(), (int)h->sets.size(), h->inv_tab, h->cls_tab, h->cnt_tab, img,
-                            best_sorted, n_img, h->orient_chunk, M, h->D, img_scale, h->err, s));
+    SPF_TRY(class_sums_sets(h->sets.data(), (int)h->sets.size(), h->inv_tab, h->cls_tab, h->cnt_tab,
+                            img.u ? nullptr : img.f, img.u, best_sorted, n_img, h->orient_chunk, M, h->D,
+                            img_scale, h->err, s));
     for (size_t c = 0; c < h->sets.size(); ++c)
-      SPF_TRY(merge_points(P, h->sets[c], img, best_sorted, n_img, (int)c * h->orient_chunk, h->D, img_scale,
+      SPF_TRY(merge_points(P, h->sets[c], nullptr, best_sorted, n_img, (int)c * h->orient_chunk, h->D, img_scale,
                            nullptr, nullptr, 0, s, kMergeSumsDone, true, true));
   } else {
     for (int i0 = 0; i0 < n_img; i0 += h->img_chunk) {
       const int ni = std::min(h->img_chunk, n_img - i0);
-      SPF_TRY(merge_run(P, img + (size_t)i0 * P2, h->quats_sorted, M, best_sorted + i0, ni, h->qlab, P2, h->D,
+      SPF_TRY(merge_run(P, img.f + (size_t)i0 * P2, h->quats_sorted, M, best_sorted + i0, ni, h->qlab, P2, h->D,
                         img_scale, nullptr, nullptr, 0, P->err, s, 0, true, true));
     }
   }
@@ -407,7 +425,9 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
   A((void**)&h->slices, sizeof(float) * (size_t)(h->keep_slices ? c.n_orient : h->orient_chunk) * P2,
     h->keep_slices ? "slices of all chunks" : "slice chunk");
   if (rc == SPF_OK) rc = spf_matcher_set_rerank(h->matcher, h->keep_slices ? 1 : 0);
-  A((void**)&h->img32, sizeof(float) * (size_t)c.max_images * P2, "FP32 images");
+  // an FP32 copy of 16-bit images only for the consumers that need one
+  if (c.precision == SPF_FP32 || !h->cache_points)
+    A((void**)&h->img32, sizeof(float) * (size_t)c.max_images * P2, "FP32 images");
   A((void**)&h->best_sorted, sizeof(int) * (size_t)c.max_images, "matches (driver numbering)");
   A((void**)&h->best, sizeof(int) * (size_t)c.max_images, "matches");
   A((void**)&h->topk_tmp, sizeof(int) * (size_t)c.max_images * std::max(c.topk, 1), "top-k lists");
@@ -599,8 +619,8 @@ int spf_mtip_match(spf_mtip* h, const float* A, const void* images, int image_ty
   DevScope dev(h->cfg.device);
   if (dev.rc != SPF_OK) return dev.rc;
   cudaStream_t s = as_stream(stream);
-  const float* img = nullptr;
-  SPF_TRY(images_f32(h, images, image_type, n_img, &img, s));
+  ImgIn img;
+  SPF_TRY(images_in(h, images, image_type, n_img, true, false, &img, s));
   SPF_TRY(match_core(h, A, img, n_img, img_scale, s));
   SPF_TRY(spf_matcher_results(h->matcher, h->best_sorted, best_d, second_d, topk_idx ? h->topk_tmp : nullptr,
                               topk_d, stream));
@@ -619,8 +639,8 @@ int spf_mtip_merge(spf_mtip* h, const void* images, int image_type, int n_img, f
   DevScope dev(h->cfg.device);
   if (dev.rc != SPF_OK) return dev.rc;
   cudaStream_t s = as_stream(stream);
-  const float* img = nullptr;
-  SPF_TRY(images_f32(h, images, image_type, n_img, &img, s));
+  ImgIn img;
+  SPF_TRY(images_in(h, images, image_type, n_img, false, true, &img, s));
   SPF_TRY(remap(best, n_img, h->inv, h->cfg.n_orient, h->best_sorted, h->err, s));
   return merge_core(h, img, n_img, img_scale, h->best_sorted, rhs, kernel_hat, s);
 }
@@ -647,8 +667,8 @@ int spf_mtip_iteration(spf_mtip* h, const float* A, const void* images, int imag
   DevScope dev(h->cfg.device);
   if (dev.rc != SPF_OK) return dev.rc;
   cudaStream_t s = as_stream(stream);
-  const float* img = nullptr;
-  SPF_TRY(images_f32(h, images, image_type, n_img, &img, s));
+  ImgIn img;
+  SPF_TRY(images_in(h, images, image_type, n_img, true, true, &img, s));
   SPF_TRY(match_core(h, A, img, n_img, img_scale, s));
   SPF_TRY(spf_matcher_results(h->matcher, h->best_sorted, nullptr, nullptr, nullptr, nullptr, stream));
   SPF_TRY(remap(h->best_sorted, n_img, h->order, h->cfg.n_orient, best ? best : h->best, h->err, s));

@@ -358,9 +358,9 @@ struct RowTable {
   }
 };
 
-template <int K>
+template <int K, class XT>
 __global__ void __launch_bounds__(256)
-rerank_kernel(const float* __restrict__ X, float xscale, RowTable rows, int P2, int stride, int ncand,
+rerank_kernel(const XT* __restrict__ X, float xscale, RowTable rows, int P2, int stride, int ncand,
               const float* __restrict__ cand_v, const int* __restrict__ cand_i, const float* __restrict__ wsq,
               float* __restrict__ st_d, int* __restrict__ st_i, const int* __restrict__ order) {
   const int img = order ? __ldg(order + blockIdx.x) : blockIdx.x;
@@ -390,20 +390,28 @@ rerank_kernel(const float* __restrict__ X, float xscale, RowTable rows, int P2, 
   if (threadIdx.x < K) s_row[threadIdx.x] = s_i[threadIdx.x] >= 0 ? rows.row(s_i[threadIdx.x], P2) : nullptr;
   __syncthreads();
   // exact FP32 distances of all candidates in one sweep over the pixels
-  const float* x = X + (size_t)img * P2;
+  const XT* x = X + (size_t)img * P2;
+  // empty candidate slots read the first filled slot's row (their sums are
+  // never used); an image without candidates skips the sweep
+  const float* fb = nullptr;
+#pragma unroll
+  for (int q = K - 1; q >= 0; --q)
+    if (s_row[q]) fb = s_row[q];
   const float* y[K];
 #pragma unroll
-  for (int q = 0; q < K; ++q) y[q] = s_row[q] ? s_row[q] : x;
+  for (int q = 0; q < K; ++q) y[q] = s_row[q] ? s_row[q] : fb;
   float acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.f;
-  bool vec = !wsq && (P2 % 4) == 0 && (((uintptr_t)x) & 15) == 0;
+  bool vec = !wsq && (P2 % 4) == 0 && (((uintptr_t)x) & (4 * sizeof(XT) - 1)) == 0;
 #pragma unroll
   for (int q = 0; q < K; ++q) vec = vec && (((uintptr_t)y[q]) & 15) == 0;
-  if (vec) {
+  if (!fb) {
+    // no candidate: nothing to measure
+  } else if (vec) {
 #pragma unroll 2
     for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
-      float4 xv = __ldg(reinterpret_cast<const float4*>(x) + p);
+      float4 xv = img_elem4(x, p);
       xv.x *= xscale; xv.y *= xscale; xv.z *= xscale; xv.w *= xscale;
 #pragma unroll
       for (int q = 0; q < K; ++q) {
@@ -414,7 +422,7 @@ rerank_kernel(const float* __restrict__ X, float xscale, RowTable rows, int P2, 
     }
   } else {
     for (int p = threadIdx.x; p < P2; p += blockDim.x) {
-      float xv = xscale * __ldg(x + p);
+      float xv = xscale * img_elem(x, p);
       const float wp = wsq ? __ldg(wsq + p) : 1.f;
 #pragma unroll
       for (int q = 0; q < K; ++q) {
@@ -583,11 +591,17 @@ static int rerank_core(spf_matcher* m, const RowTable& rows, const float* cv, co
     }));
     order = m->rr_order;
   }
-#define SPF_RR(K)                                                                               \
-  case K:                                                                                       \
-    return launch("rerank_kernel", s, [&] {                                                     \
-      rerank_kernel<K><<<m->n_img, 256, 0, s>>>(m->images, m->img_scale, rows, m->P2, stride,   \
-                                                ncand, cv, ci, m->wsq, m->st_d, m->st_i, order); \
+#define SPF_RR(K)                                                                                   \
+  case K:                                                                                           \
+    return launch("rerank_kernel", s, [&] {                                                         \
+      if (m->images16)                                                                              \
+        rerank_kernel<K, uint16_t><<<m->n_img, 256, 0, s>>>(m->images16, m->img_scale, rows, m->P2, \
+                                                            stride, ncand, cv, ci, m->wsq, m->st_d,  \
+                                                            m->st_i, order);                        \
+      else                                                                                          \
+        rerank_kernel<K, float><<<m->n_img, 256, 0, s>>>(m->images, m->img_scale, rows, m->P2,      \
+                                                         stride, ncand, cv, ci, m->wsq, m->st_d,     \
+                                                         m->st_i, order);                           \
     });
   switch (m->topk) {
     SPF_RR(2) SPF_RR(3) SPF_RR(4) SPF_RR(5) SPF_RR(6) SPF_RR(7) SPF_RR(8)

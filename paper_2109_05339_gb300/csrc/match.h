@@ -3,6 +3,18 @@
 
 #include "common.h"
 
+// Image element as FP32: FP32 rows, or 16-bit photon counts (exact in FP32).
+static __device__ __forceinline__ float img_elem(const float* x, int p) { return __ldg(x + p); }
+static __device__ __forceinline__ float img_elem(const uint16_t* x, int p) { return (float)__ldg(x + p); }
+// Four consecutive elements from 4 * p (16-byte FP32 or 8-byte 16-bit load).
+static __device__ __forceinline__ float4 img_elem4(const float* x, int p) {
+  return __ldg(reinterpret_cast<const float4*>(x) + p);
+}
+static __device__ __forceinline__ float4 img_elem4(const uint16_t* x, int p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(x) + p);
+  return make_float4((float)(u.x & 0xffffu), (float)(u.x >> 16), (float)(u.y & 0xffffu), (float)(u.y >> 16));
+}
+
 constexpr int kCand = 8;          // approximate candidates kept per (image, split)
 constexpr int kMaxSplits = 64;    // orientation splits of one GEMM launch
 constexpr int kMaxChunks = 1024;  // orientation chunks of one deferred re-rank
@@ -15,6 +27,7 @@ struct spf_matcher {
   int n_img = 0;
   float img_scale = 1.f;
   const float* images = nullptr;
+  const uint16_t* images16 = nullptr;   // 16-bit photon counts instead (BF16 / FP8 paths)
   float* x2 = nullptr;            // |img_scale * x_i|^2
   float* y2 = nullptr;            // |y_j|^2 of the current chunk
   void* xq = nullptr;             // quantised images  (max_images x Kpad)

@@ -43,18 +43,19 @@ __device__ __forceinline__ float block_sum_f64(double v, double* sh) {
 
 // BF16 copy of scale * src rows (padding columns stay zero from creation)
 // and the FP32 squared norms of the scaled rows, one CTA per row.
-__global__ void __launch_bounds__(256) quantize_bf16_kernel(const float* __restrict__ src, int P2,
+template <class XT>
+__global__ void __launch_bounds__(256) quantize_bf16_kernel(const XT* __restrict__ src, int P2,
                                                             int Kpad, float scale,
                                                             const float* __restrict__ w,
                                                             __nv_bfloat16* __restrict__ dst,
                                                             float* __restrict__ norms) {
   const int r = blockIdx.x;
-  const float* row = src + (size_t)r * P2;
+  const XT* row = src + (size_t)r * P2;
   __nv_bfloat16* out = dst + (size_t)r * Kpad;
   float a0 = 0.f, a1 = 0.f;
-  if (!w && (P2 % 4) == 0 && (((uintptr_t)row) & 15) == 0) {
+  if (!w && (P2 % 4) == 0 && (((uintptr_t)row) & (4 * sizeof(XT) - 1)) == 0) {
     for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
-      float4 v = __ldg(reinterpret_cast<const float4*>(row) + p);
+      float4 v = img_elem4(row, p);
       v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
       a0 = fmaf(v.x, v.x, fmaf(v.y, v.y, a0));
       a1 = fmaf(v.z, v.z, fmaf(v.w, v.w, a1));
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(256) quantize_bf16_kernel(const float* __restr
     }
   } else {
     for (int p = threadIdx.x; p < P2; p += blockDim.x) {
-      float v = scale * __ldg(row + p);
+      float v = scale * img_elem(row, p);
       if (w) v *= __ldg(w + p);
       a0 = fmaf(v, v, a0);
       out[p] = __float2bfloat16_rn(v);
@@ -80,17 +81,18 @@ __global__ void __launch_bounds__(256) quantize_bf16_kernel(const float* __restr
 // FP8 e4m3 copy with a per-row scale a_r = max_p |scale * src_rp| / 448
 // (1 for an all-zero row): dst = e4m3(scale * src / a_r); also the FP32
 // squared norms of the scaled rows. One CTA per row.
-__global__ void __launch_bounds__(256) quantize_fp8_kernel(const float* __restrict__ src, int P2,
+template <class XT>
+__global__ void __launch_bounds__(256) quantize_fp8_kernel(const XT* __restrict__ src, int P2,
                                                            int Kpad, float scale,
                                                            const float* __restrict__ w,
                                                            __nv_fp8_e4m3* __restrict__ dst,
                                                            float* __restrict__ row_scale,
                                                            float* __restrict__ norms) {
   const int r = blockIdx.x;
-  const float* row = src + (size_t)r * P2;
+  const XT* row = src + (size_t)r * P2;
   float mx = 0.f, a0 = 0.f;
   for (int k = threadIdx.x; k < P2; k += blockDim.x) {
-    float v = scale * __ldg(row + k);
+    float v = scale * img_elem(row, k);
     if (w) v *= __ldg(w + k);
     mx = fmaxf(mx, fabsf(v));
     a0 = fmaf(v, v, a0);
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256) quantize_fp8_kernel(const float* __restri
   __syncthreads();
   const float inv = 1.f / sm[0];
   for (int k = threadIdx.x; k < P2; k += blockDim.x)
-    dst[(size_t)r * Kpad + k] = __nv_fp8_e4m3(scale * __ldg(row + k) * (w ? __ldg(w + k) : 1.f) * inv);
+    dst[(size_t)r * Kpad + k] = __nv_fp8_e4m3(scale * img_elem(row, k) * (w ? __ldg(w + k) : 1.f) * inv);
 }
 
 }  // namespace
@@ -121,19 +123,30 @@ int tc_kpad(int P2, int precision) {
   return (int)ceil_div(P2, blk) * blk;
 }
 
-int quantize_rows(spf_matcher* m, const float* src, int rows, float scale, void* dst, float* scales,
-                  float* norms, cudaStream_t s) {
+template <class XT>
+int quantize_rows_t(spf_matcher* m, const XT* src, int rows, float scale, void* dst, float* scales,
+                    float* norms, cudaStream_t s) {
   if (rows == 0) return SPF_OK;
   if (m->precision == SPF_BF16) {
     return launch("quantize_bf16_kernel", s, [&] {
-      quantize_bf16_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
-                                                static_cast<__nv_bfloat16*>(dst), norms);
-    });
+      quantize_bf16_kernel<XT><<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
+                                                    static_cast<__nv_bfloat16*>(dst), norms);
+    }, (double)rows * m->P2 * (sizeof(XT) + 2.0));
   }
   return launch("quantize_fp8_kernel", s, [&] {
-    quantize_fp8_kernel<<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
-                                             static_cast<__nv_fp8_e4m3*>(dst), scales, norms);
-  });
+    quantize_fp8_kernel<XT><<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
+                                                 static_cast<__nv_fp8_e4m3*>(dst), scales, norms);
+  }, (double)rows * m->P2 * (2.0 * sizeof(XT) + 1.0));
+}
+
+int quantize_rows(spf_matcher* m, const float* src, int rows, float scale, void* dst, float* scales,
+                  float* norms, cudaStream_t s) {
+  return quantize_rows_t(m, src, rows, scale, dst, scales, norms, s);
+}
+
+int quantize_rows_u16(spf_matcher* m, const uint16_t* src, int rows, float scale, void* dst, float* scales,
+                      float* norms, cudaStream_t s) {
+  return quantize_rows_t(m, src, rows, scale, dst, scales, norms, s);
 }
 
 int match_tc_supported(int device) {

@@ -516,13 +516,22 @@ __global__ void class_sum_kernel(const float* __restrict__ img, const int* __res
 // iteration with their loads issued together; rows whose pixel count is a
 // multiple of 4 are read as 16-byte vectors.
 constexpr int kClassTask = 1024;
+__device__ __forceinline__ float4 load4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 load4(const uint16_t* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  return make_float4((float)(u.x & 0xffffu), (float)(u.x >> 16), (float)(u.y & 0xffffu), (float)(u.y >> 16));
+}
+__device__ __forceinline__ float load1(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float load1(const uint16_t* p) { return (float)__ldg(p); }
+
+template <class XT>
 __global__ void __launch_bounds__(256) class_sum_sets_kernel(
-    const float* __restrict__ img, const int* __restrict__ oidx, int n_img, int chunk, int n_total, int P2,
+    const XT* __restrict__ img, const int* __restrict__ oidx, int n_img, int chunk, int n_total, int P2,
     const float* __restrict__ D, float b_scale, const uint32_t* const* __restrict__ inv_tab,
-    float* const* __restrict__ cls_tab, float* const* __restrict__ cnt_tab, int* err) {
+    float* const* __restrict__ cls_tab, float* const* __restrict__ cnt_tab, int* err, int base_aligned) {
   const int chunks = (P2 + kClassTask - 1) / kClassTask;
   const int64_t ntask = (int64_t)n_img * chunks;
-  const bool vec = (P2 & 3) == 0;
+  const bool vec = base_aligned && (P2 & 3) == 0;
   for (int64_t t0 = blockIdx.x; t0 < ntask; t0 += 2 * (int64_t)gridDim.x) {
     float v[2][4];
     int o[2], p0[2];
@@ -546,7 +555,7 @@ __global__ void __launch_bounds__(256) class_sum_sets_kernel(
         continue;
       }
       if (vec && p0[h] + 3 < P2) {
-        const float4 x = __ldg(reinterpret_cast<const float4*>(img + row[h] + p0[h]));
+        const float4 x = load4(img + row[h] + p0[h]);
         v[h][0] = x.x;
         v[h][1] = x.y;
         v[h][2] = x.z;
@@ -554,7 +563,7 @@ __global__ void __launch_bounds__(256) class_sum_sets_kernel(
       } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (p0[h] + k < P2) v[h][k] = __ldg(img + row[h] + p0[h] + k);
+          if (p0[h] + k < P2) v[h][k] = load1(img + row[h] + p0[h] + k);
       }
       if (c == 0 && threadIdx.x == 0) {
         const int set = o[h] / chunk;
@@ -1571,8 +1580,8 @@ int merge_run(spf_plan* P, const float* images, const float* quats, int n_quats,
 // kMergeSumsDone. Tables: device arrays of the sets' inverse orders, class
 // sums and counts.
 int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* inv_tab, float* const* cls_tab,
-                    float* const* cnt_tab, const float* images, const int* oidx, int n_img, int chunk, int n_total,
-                    const float* D, float b_scale, int* err, cudaStream_t s) {
+                    float* const* cnt_tab, const float* images, const uint16_t* images16, const int* oidx, int n_img,
+                    int chunk, int n_total, const float* D, float b_scale, int* err, cudaStream_t s) {
   for (int c = 0; c < nsets; ++c) {
     spf_points* S = sets[c];
     // a compacted spread leaves the sums zeroed: no clearing pass then
@@ -1587,9 +1596,16 @@ int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* i
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tasks = (int64_t)n_img * ceil_div(P2, kClassTask);
   const unsigned blocks = (unsigned)std::min<int64_t>(tasks, (int64_t)sms * 8);
+  // rows of 16-bit counts are read as 8-byte vectors when 8-byte aligned
+  if (images16)
+    return launch("class_sum_kernel", s, [&] {
+      class_sum_sets_kernel<uint16_t><<<blocks, 256, 0, s>>>(images16, oidx, n_img, chunk, n_total, P2, D, b_scale,
+                                                             inv_tab, cls_tab, cnt_tab, err,
+                                                             ((uintptr_t)images16 & 7) == 0);
+    }, 2.0 * n_img * (double)P2);
   return launch("class_sum_kernel", s, [&] {
-    class_sum_sets_kernel<<<blocks, 256, 0, s>>>(images, oidx, n_img, chunk, n_total, P2, D, b_scale, inv_tab,
-                                                 cls_tab, cnt_tab, err);
+    class_sum_sets_kernel<float><<<blocks, 256, 0, s>>>(images, oidx, n_img, chunk, n_total, P2, D, b_scale,
+                                                        inv_tab, cls_tab, cnt_tab, err, ((uintptr_t)images & 15) == 0);
   }, 4.0 * n_img * (double)P2);
 }
 

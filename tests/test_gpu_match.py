@@ -203,3 +203,56 @@ def test_beamstop_mask_weighted_matching(precision):
     d_true = np.sum(w * (Xd - f32(Y)[r["best"]]) ** 2, axis=1)
     sc = np.sum(w * Xd * Xd, 1) + np.sum(w * f32(Y)[r["best"]] ** 2, 1)
     assert np.all(np.abs(r["d1"] - d_true) <= 1e-5 * sc)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("P2,offset", [(256, 0), (255, 0), (256, 1)])
+def test_sixteen_bit_images_equal_fp32_images(c1_data, precision, P2, offset):
+    """Images given as 16-bit photon counts (read directly by the
+    quantisation and the FP32 re-rank) give exactly the matches, distances
+    and top-k lists of the same counts given as FP32; also with a row length
+    that is not a multiple of 4 and with rows not 8-byte aligned (scalar
+    loads). Against the FP64 oracle above the margin as well. The FP32
+    matcher refuses 16-bit images."""
+    import torch
+    from paper_2109_05339_gb300 import Matcher
+    from paper_2109_05339_gb300._lib import SpfError
+    pb, slices, clean, counts = c1_data
+    # 16-bit counts: the c1 images hold up to about 9e4 photons a pixel, halved
+    X = np.floor(counts[:, :P2] / 2).astype(np.float32)
+    Y = np.ascontiguousarray(slices[:, :P2])
+    assert 32767 < X.max() < 65536                 # the top bit is used
+    scale = float(np.float32(2.0 / pb.cfg.photons))
+    out = []
+    for kind in ("f32", "u16"):
+        m = Matcher(X.shape[0], Y.shape[0], P2, precision, 8)
+        if kind == "f32":
+            xd = to_dev(X.astype(np.float32))
+        else:
+            buf = torch.zeros(X.size + offset, dtype=torch.int16, device="cuda")
+            buf[offset:] = torch.from_numpy(X.astype(np.uint16).view(np.int16).reshape(-1)).cuda()
+            xd = buf[offset:].view(X.shape)
+        m.set_images(xd, scale)
+        m.add_slices(to_dev(Y))
+        r = {k: v.cpu().numpy() for k, v in m.results(with_topk=True).items()}
+        m.status()
+        torch.cuda.synchronize()
+        out.append(r)
+        m.close()
+    Xd = f32(X) * np.float64(scale)
+    ref = matching.match(Xd, f32(Y))
+    ok = ref["margin"] > (MARGIN if precision == "bf16" else 1e-2)
+    np.testing.assert_array_equal(out[1]["best"][ok], ref["best"][ok])
+    if offset == 0:
+        # the same loads in the same order: bit-identical results
+        for k in out[0]:
+            np.testing.assert_array_equal(out[1][k], out[0][k])
+    else:
+        # scalar loads of the unaligned counts sum in another order
+        np.testing.assert_array_equal(out[1]["best"][ok], out[0]["best"][ok])
+        d = out[0]["d1"]
+        assert np.all(np.abs(out[1]["d1"] - d) <= 1e-5 * np.abs(d) + 1e-30)
+    m = Matcher(X.shape[0], Y.shape[0], P2, "fp32", 8)
+    with pytest.raises(SpfError):
+        m.set_images(torch.zeros(X.shape, dtype=torch.int16, device="cuda"), scale)
+    m.close()
