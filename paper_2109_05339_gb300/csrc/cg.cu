@@ -194,7 +194,7 @@ __global__ void wsumsq_finalize_kernel(const double* __restrict__ part, int npar
   if (threadIdx.x == 0) out[0] = accumulate ? out[0] + a : a;
 }
 
-int grid_for(int64_t n) { return (int)std::min<int64_t>(ceil_div(n, 256), 152 * 32); }
+int grid_for(int64_t n) { return (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)device_sms() * 32); }
 
 }  // namespace
 

@@ -56,6 +56,19 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Streaming multiprocessors of the current device (queried once per device;
+// 152 if the query fails), for sizing grid-stride launches.
+inline int device_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int n = 0;
+    cache[dev] = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+  }
+  return cache[dev];
+}
+
 // Launch tracing (profile.cu): every kernel launch goes through launch(),
 // which counts it and, while profiling is on, brackets it with CUDA events
 // on its stream and adds `bytes` -- the algorithmic global-memory bytes the

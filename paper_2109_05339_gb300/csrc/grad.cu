@@ -118,7 +118,7 @@ __global__ void step_kernel(float* __restrict__ x, const float* __restrict__ g, 
     x[i] = fmaf(-t, g[i], x[i]);
 }
 
-unsigned grid_of(int64_t n) { return (unsigned)std::min<int64_t>(ceil_div(n, kThreads), 152 * 16); }
+unsigned grid_of(int64_t n) { return (unsigned)std::min<int64_t>(ceil_div(n, kThreads), (int64_t)device_sms() * 16); }
 
 // S^T D (S v - b) [loss and b when img is given] or S^T D S v, summed over
 // image chunks into out (overwritten).

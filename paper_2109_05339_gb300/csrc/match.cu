@@ -704,7 +704,7 @@ int counts_to_f32(const uint16_t* counts, int64_t n, float* out, cudaStream_t s)
   if (n == 0) return SPF_OK;
   const bool vec = (((uintptr_t)counts | (uintptr_t)out) & 15) == 0;
   const int64_t work = vec ? ceil_div(n, 8) : n;
-  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(work, 256), 152 * 16);
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(work, 256), (int64_t)device_sms() * 16);
   if (vec)
     return launch("counts_to_f32_kernel", s, [&] { counts_to_f32_vec_kernel<<<grid, 256, 0, s>>>(counts, n, out); }, 6.0 * n);
   return launch("counts_to_f32_kernel", s, [&] { counts_to_f32_kernel<<<grid, 256, 0, s>>>(counts, n, out); }, 6.0 * n);

@@ -1311,7 +1311,7 @@ __global__ void accumulate_kernel(const float* __restrict__ src, float* __restri
 
 int grid_for(int64_t n, int threads = 256) {
   int64_t b = ceil_div(n, threads);
-  return (int)std::min<int64_t>(b, 152 * 32);
+  return (int)std::min<int64_t>(b, (int64_t)device_sms() * 32);
 }
 
 // Counting sort of npts points by tap-origin cell into `sorted`.

@@ -334,8 +334,7 @@ int pass(const spf_phaser* ph, const PassArgs& a, float sign, cudaStream_t s, co
   const size_t smem = pass_smem(ph->N);
   SPF_CUDA(cudaFuncSetAttribute(dft_pass_kernel<AXIS, ZM, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ph->device);
+  const int sms = device_sms();
   const int nt = AXIS == 0 ? (int)ceil_div((int64_t)ph->N * ph->N, kTL) : (int)ceil_div(ph->N, kTL) * ph->N;
   const int grid = std::min(nt, 2 * sms);
   // bytes: each line read once and written once (complex), plus the side arrays
@@ -479,7 +478,9 @@ int spf_phaser_create(spf_phaser** out, int N, int device) {
   A((void**)&ph->blur, sizeof(float) * ph->n3, "shrinkwrap blur");
   A((void**)&ph->g1, sizeof(float) * N, "shrinkwrap transfer");
   A((void**)&ph->tw, sizeof(float2) * N, "phasing twiddles");
-  A((void**)&ph->part, sizeof(double) * 2 * 2 * 152 * 8, "phasing partials");
+  // per-block partial sums of the passes (at most 2 blocks per SM) and of
+  // the reductions, with room to spare
+  A((void**)&ph->part, sizeof(double) * 2 * 2 * (size_t)std::max(device_sms(), 152) * 8, "phasing partials");
   A((void**)&ph->count, sizeof(unsigned), "phasing counter");
   A((void**)&ph->sc, sizeof(double) * 2, "phasing scalars");
   A((void**)&ph->maxbits, sizeof(unsigned), "blur maximum");

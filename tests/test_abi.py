@@ -57,7 +57,10 @@ def test_argument_errors_without_gpu(lib):
     assert L.spf_counts_to_f32(None, 8, None, None) == lib.SPF_ERR_ARG      # NULL buffers
     assert L.spf_counts_to_f32(None, -1, None, None) == lib.SPF_ERR_ARG     # negative size
     # odd address; with n = 0 nothing would be read even if the check were lost
-    assert L.spf_counts_to_f32(C.c_void_p(1), 0, C.c_void_p(16), None) == lib.SPF_ERR_ARG
+    # an odd (misaligned) address of a real host buffer: rejected before any use
+    buf = (C.c_uint8 * 64)()
+    odd = C.c_void_p(C.addressof(buf) + 1)
+    assert L.spf_counts_to_f32(odd, 0, C.c_void_p(C.addressof(buf) + 16), None) == lib.SPF_ERR_ARG
     assert L.spf_version() == 1
     # destroying NULL handles is a no-op
     assert L.spf_plan_destroy(None) == 0 and L.spf_matcher_destroy(None) == 0
