@@ -591,19 +591,12 @@ def run_e2e(args, drv, pb, images, img_scale, dev, M, Ni, world):
     e1.record(comp)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # the host-to-device rate of this machine for the step's image upload, alone
-    d_img = torch.empty(h_img.shape, dtype=h_img.dtype, device=dev)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(comp)
-    d_img.copy_(h_img, non_blocking=True)
-    c1.record(comp)
-    torch.cuda.synchronize()
-    h2d_gbs = h_img.numel() * 2 / (c0.elapsed_time(c1) / 1e3) / 1e9
-    del d_img
     up_ms = drv.last_upload_ms()
     return {"value": Ni * M * world / (ms / 1e3), "unit": "matches/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "h2d_gbs_alone": h2d_gbs,
-            "image_upload_ms_last_step": up_ms, "upload": "sm",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "image_upload_ms_last_step": up_ms,
+            "image_upload_gbs": (h_img.numel() * 2 / (up_ms / 1e3) / 1e9) if up_ms > 0 else None,
+            "upload": "upload kernel reading the page-locked buffer (spf_mtip_set_upload SM mode)",
             "api": "spf_mtip_iteration_host (one C-ABI call per step, host buffers in and out)",
             "note": "model and 16-bit images of step i+1 copied on the library's copy stream while step i "
                     "computes; orientation set and detector taken once before timing"}
