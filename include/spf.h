@@ -404,6 +404,15 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
  *   floats) are written back on `stream`. Asynchronous for page-locked host
  *   buffers: the inputs must stay unchanged and the outputs are valid once
  *   `stream` has completed the call's work (e.g. cudaStreamSynchronize).
+ * spf_mtip_upload_host / spf_mtip_release_upload: the upload half of
+ *   spf_mtip_iteration_host for callers that run the steps themselves (an
+ *   image-sharded run whose merge sums are reduced across processes between
+ *   merge and solve, Sec. II-C). upload_host copies A_host and images_host
+ *   into the next device slot exactly as the iteration does and returns the
+ *   slot's device pointers (A_dev: N^3 floats, images_dev: n_img x P2 of
+ *   host_image_type), valid for work enqueued on `stream`; release_upload
+ *   marks the slot free once the work enqueued on `stream` so far completes.
+ *   One upload is held at a time (SPF_ERR_ARG for a second before release).
  * spf_mtip_set_upload: how spf_mtip_iteration_host moves the images to the
  *   device. SPF_UPLOAD_SM (default): a kernel on the copy stream reads the
  *   host buffer over the CPU-GPU link and writes the slot (about 190 GB/s on
@@ -471,6 +480,9 @@ int spf_mtip_iteration_host(spf_mtip* h, const float* A_host, const void* images
                             double* lambda_out, void* stream);
 int spf_mtip_set_upload(spf_mtip* h, int mode);
 int spf_mtip_last_upload_ms(spf_mtip* h, float* ms);
+int spf_mtip_upload_host(spf_mtip* h, const float* A_host, const void* images_host, int image_type, int n_img,
+                         float** A_dev, const void** images_dev, void* stream);
+int spf_mtip_release_upload(spf_mtip* h, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Phasing, Sec. II-D: from the merged diffraction volume to a density by

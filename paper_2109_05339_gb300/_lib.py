@@ -113,6 +113,8 @@ PROTOTYPES = {
     "spf_mtip_iteration": (I, [P, P, P, I, I, F, I, D, P, P, C.POINTER(D), P]),
     "spf_mtip_iteration_host": (I, [P, P, P, I, I, F, I, D, P, P, C.POINTER(D), P]),
     "spf_mtip_set_upload": (I, [P, I]),
+    "spf_mtip_upload_host": (I, [P, P, P, I, I, C.POINTER(P), C.POINTER(P), P]),
+    "spf_mtip_release_upload": (I, [P, P]),
     "spf_mtip_last_upload_ms": (I, [P, C.POINTER(F)]),
     "spf_profile_enable": (I, [I]),
     "spf_profile_select": (I, [C.c_char_p]),

@@ -137,6 +137,7 @@ struct spf_mtip {
   void* slotImg[2] = {nullptr, nullptr};
   cudaEvent_t up0[2] = {nullptr, nullptr}, up1[2] = {nullptr, nullptr};   // timing of each slot's image upload
   int upload_mode = SPF_UPLOAD_SM;
+  int held_slot = -1;              // slot handed out by spf_mtip_upload_host, not yet released
   long long host_calls = 0;
 };
 
@@ -261,6 +262,34 @@ int upload_images(spf_mtip* h, void* dst, const void* src, size_t bytes, cudaStr
     }
   }
   SPF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+  return SPF_OK;
+}
+
+int check_images(const spf_mtip* h, const void* images, int type, int n_img);
+
+int check_upload(const spf_mtip* h, int image_type, const void* images_host, int n_img) {
+  SPF_CHECK_ARG(h->host_path, "the driver was created without host-buffer slots (host_image_type = -1)");
+  SPF_CHECK_ARG(image_type == h->cfg.host_image_type, "image type %d differs from the slots' type %d", image_type,
+                h->cfg.host_image_type);
+  return check_images(h, images_host, image_type, n_img);
+}
+
+// The model and the images of a host-buffer call into slot b = the call
+// count's parity, on the copy stream once the call two back has released
+// that slot; `s` waits for the copies.
+int upload_slot(spf_mtip* h, const float* A_host, const void* images_host, int image_type, int n_img,
+                cudaStream_t s, int* slot) {
+  const int b = (int)(h->host_calls & 1);
+  const size_t n3 = (size_t)h->cfg.N * h->cfg.N * h->cfg.N;
+  SPF_CUDA(cudaStreamWaitEvent(h->copy, h->freed[b], 0));
+  SPF_CUDA(cudaMemcpyAsync(h->slotA[b], A_host, sizeof(float) * n3, cudaMemcpyHostToDevice, h->copy));
+  SPF_CUDA(cudaEventRecord(h->up0[b], h->copy));
+  SPF_TRY(upload_images(h, h->slotImg[b], images_host, image_elem(image_type) * (size_t)n_img * h->cfg.P2, h->copy));
+  SPF_CUDA(cudaEventRecord(h->up1[b], h->copy));
+  SPF_CUDA(cudaEventRecord(h->copied[b], h->copy));
+  SPF_CUDA(cudaStreamWaitEvent(s, h->copied[b], 0));
+  ++h->host_calls;
+  *slot = b;
   return SPF_OK;
 }
 
@@ -681,31 +710,48 @@ int spf_mtip_iteration_host(spf_mtip* h, const float* A_host, const void* images
                             double* lambda_out, void* stream) {
   clear_error();
   SPF_TRY(check_handle(h, true));
-  SPF_CHECK_ARG(h->host_path, "the driver was created without host-buffer slots (host_image_type = -1)");
-  SPF_CHECK_ARG(image_type == h->cfg.host_image_type, "image type %d differs from the slots' type %d", image_type,
-                h->cfg.host_image_type);
-  SPF_TRY(check_images(h, images_host, image_type, n_img));
+  SPF_TRY(check_upload(h, image_type, images_host, n_img));
   SPF_CHECK_ARG(A_host && best_host && x_host, "NULL pointer");
   SPF_CHECK_ARG(lam_rel > 0.0 && cg_iters >= 0, "lam_rel > 0 and cg_iters >= 0 required");
   DevScope dev(h->cfg.device);
   if (dev.rc != SPF_OK) return dev.rc;
   cudaStream_t s = as_stream(stream);
-  const int b = (int)(h->host_calls & 1);
   const size_t n3 = (size_t)h->cfg.N * h->cfg.N * h->cfg.N;
-  // inputs into slot b on the copy stream, once the call two back is done with it
-  SPF_CUDA(cudaStreamWaitEvent(h->copy, h->freed[b], 0));
-  SPF_CUDA(cudaMemcpyAsync(h->slotA[b], A_host, sizeof(float) * n3, cudaMemcpyHostToDevice, h->copy));
-  SPF_CUDA(cudaEventRecord(h->up0[b], h->copy));
-  SPF_TRY(upload_images(h, h->slotImg[b], images_host, image_elem(image_type) * (size_t)n_img * h->cfg.P2, h->copy));
-  SPF_CUDA(cudaEventRecord(h->up1[b], h->copy));
-  SPF_CUDA(cudaEventRecord(h->copied[b], h->copy));
-  SPF_CUDA(cudaStreamWaitEvent(s, h->copied[b], 0));
-  ++h->host_calls;
+  int b = 0;
+  SPF_TRY(upload_slot(h, A_host, images_host, image_type, n_img, s, &b));
   SPF_TRY(spf_mtip_iteration(h, h->slotA[b], h->slotImg[b], image_type, n_img, img_scale, cg_iters, lam_rel,
                              h->best, h->x, lambda_out, stream));
   SPF_CUDA(cudaMemcpyAsync(best_host, h->best, sizeof(int) * (size_t)n_img, cudaMemcpyDeviceToHost, s));
   SPF_CUDA(cudaMemcpyAsync(x_host, h->x, sizeof(float) * n3, cudaMemcpyDeviceToHost, s));
   SPF_CUDA(cudaEventRecord(h->freed[b], s));
+  return SPF_OK;
+}
+
+int spf_mtip_upload_host(spf_mtip* h, const float* A_host, const void* images_host, int image_type, int n_img,
+                         float** A_dev, const void** images_dev, void* stream) {
+  clear_error();
+  SPF_TRY(check_handle(h, false));
+  SPF_TRY(check_upload(h, image_type, images_host, n_img));
+  SPF_CHECK_ARG(A_host && A_dev && images_dev, "NULL pointer");
+  SPF_CHECK_ARG(h->held_slot < 0, "the previous upload was not released (spf_mtip_release_upload)");
+  DevScope dev(h->cfg.device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  int b = 0;
+  SPF_TRY(upload_slot(h, A_host, images_host, image_type, n_img, as_stream(stream), &b));
+  h->held_slot = b;
+  *A_dev = h->slotA[b];
+  *images_dev = h->slotImg[b];
+  return SPF_OK;
+}
+
+int spf_mtip_release_upload(spf_mtip* h, void* stream) {
+  clear_error();
+  SPF_TRY(check_handle(h, false));
+  SPF_CHECK_ARG(h->held_slot >= 0, "no upload is held");
+  DevScope dev(h->cfg.device);
+  if (dev.rc != SPF_OK) return dev.rc;
+  SPF_CUDA(cudaEventRecord(h->freed[h->held_slot], as_stream(stream)));
+  h->held_slot = -1;
   return SPF_OK;
 }
 

@@ -36,6 +36,17 @@ from .api import COUNT_DTYPES, PRECISIONS, Matcher, Plan, _dev_index, _f32, _ptr
 from .dist import allreduce_sum_, global_count
 
 
+class _DevArray:
+    # a device buffer of the library seen by torch without a copy
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _device_view(ptr, shape, typestr, device):
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device=torch.device("cuda", device))
+
+
 def morton_order(quats_host):
     """The driver's renumbering: permutation sorting unit quaternions (w, x, y,
     z) by the Morton code of (x, y, z) quantised to 10 bits per axis."""
@@ -94,6 +105,7 @@ class MTIP:
         self.x = torch.empty((N,) * 3, dtype=torch.float32, device=d)
         self._best = torch.empty(n_img, dtype=torch.int32, device=d)
         self._key = None
+        self._orient = None
         self._mask = None
 
     # -- configuration --------------------------------------------------------
@@ -108,6 +120,7 @@ class MTIP:
         self._key = None
         check(lib.spf_mtip_set_orientations(self._h, _ptr(quats), _ptr(q_lab), _stream(self.device)))
         self._key = key
+        self._orient = (quats, q_lab)
 
     def set_mask(self, D):
         """Pixel weights D (P2,) for matching, merging and lambda; None: ones."""
@@ -240,8 +253,10 @@ class MTIP:
             best_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
         if x_out is None:
             x_out = torch.empty((self.N,) * 3, dtype=torch.float32, pin_memory=True)
-        lam = C.c_double()
         t = SPF_IMAGES_F32 if self.host_images == "f32" else SPF_IMAGES_U16
+        if self.group is not None:
+            return self._iteration_host_group(A_host, images_host, t, img_scale, cg_iters, lam_rel, best_out, x_out)
+        lam = C.c_double()
         check(lib.spf_mtip_iteration_host(self._h, _ptr(A_host), _ptr(images_host), t, n, C.c_float(img_scale),
                                           int(cg_iters), float(lam_rel), _ptr(best_out), _ptr(x_out),
                                           C.byref(lam), _stream(self.device)))
@@ -260,6 +275,28 @@ class MTIP:
         ms = C.c_float()
         check(lib.spf_mtip_last_upload_ms(self._h, C.byref(ms)))
         return ms.value
+
+    def _iteration_host_group(self, A_host, images_host, t, img_scale, cg_iters, lam_rel, best_out, x_out):
+        # image-sharded: the library uploads into its slot, the steps run with
+        # the merge sums reduced over the group between merge and solve
+        if getattr(self, "_orient", None) is None:
+            raise RuntimeError("set_orientations first")
+        n = images_host.shape[0]
+        a_dev, i_dev = C.c_void_p(), C.c_void_p()
+        st = _stream(self.device)
+        check(lib.spf_mtip_upload_host(self._h, _ptr(A_host), _ptr(images_host), t, n, C.byref(a_dev),
+                                       C.byref(i_dev), st))
+        try:
+            A = _device_view(a_dev.value, (self.N,) * 3, "<f4", self.device)
+            imgs = _device_view(i_dev.value, (n, self.P2), "<f4" if t == SPF_IMAGES_F32 else "<i2", self.device)
+            q, ql = self._orient
+            res = self.match(A, q, ql, imgs, img_scale)
+            x, lam = self.solve(A, q, ql, imgs, img_scale, res["best"], cg_iters, lam_rel)
+            best_out.copy_(res["best"], non_blocking=True)
+            x_out.copy_(x, non_blocking=True)
+        finally:
+            check(lib.spf_mtip_release_upload(self._h, st))
+        return best_out, x_out, lam
 
     def status(self):
         check(lib.spf_mtip_status(self._h))

@@ -2,9 +2,12 @@
 type-1 sums, then a reduction): each process holds half of the images,
 matches and merges them, the right-hand sides and Toeplitz kernels are
 summed over a gloo group, and both solve the same system. The merged model,
-lambda and the matches equal one process merging all images. Both processes
-share one GPU; their kernels never wait on each other (the reduction runs on
-the host through gloo)."""
+lambda and the matches equal one process merging all images, with the
+images on the device and from host buffers (the library's upload into its
+device slots, then the steps with the reduction between merge and solve,
+three calls so that both slots are used). Both processes share one GPU;
+their kernels never wait on each other (the reduction runs on the host
+through gloo)."""
 import os
 import socket
 import subprocess
@@ -28,7 +31,7 @@ import torch
 import torch.distributed as dist
 import synth
 from paper_2109_05339_gb300 import MTIP
-rank, world, port, out = int(sys.argv[1]), int(sys.argv[2]), sys.argv[3], sys.argv[4]
+rank, world, port, out, mode = int(sys.argv[1]), int(sys.argv[2]), sys.argv[3], sys.argv[4], sys.argv[5]
 torch.cuda.set_device(0)
 dist.init_process_group("gloo", rank=rank, world_size=world, init_method=f"tcp://127.0.0.1:{port}",
                         timeout=datetime.timedelta(seconds=120))
@@ -41,17 +44,29 @@ q = torch.from_numpy(d["quats"]).to(dev)
 ql = torch.from_numpy(d["qlab"]).to(dev)
 imgs = torch.from_numpy(d["counts"][lo:hi]).to(dev)
 drv = MTIP(A.shape[0], 1.0, ql.shape[0], hi - lo, q.shape[0], orient_chunk=int(d["chunk"]), cache_points=True,
-           process_group=dist.group.WORLD)
-res, x, lam = drv.iteration(A, q, ql, imgs, float(d["scale"]), cg_iters=3)
+           process_group=dist.group.WORLD, host_images="f32" if mode == "host" else None)
+if mode == "host":
+    # host buffers: the library's upload, then the steps with the reduction
+    drv.set_orientations(q, ql)
+    A_h = torch.from_numpy(d["A"]).pin_memory()
+    img_h = torch.from_numpy(d["counts"][lo:hi]).pin_memory()
+    for _ in range(3):
+        best, x, lam = drv.iteration_host(A_h, img_h, float(d["scale"]), cg_iters=3)
+    torch.cuda.synchronize()
+    best, x = best.clone(), x.clone()
+else:
+    res, x, lam = drv.iteration(A, q, ql, imgs, float(d["scale"]), cg_iters=3)
+    best = res["best"]
 torch.cuda.synchronize()
 drv.status()
-np.savez(os.path.join(out, f"rank{rank}.npz"), best=res["best"].cpu().numpy(), x=x.cpu().numpy(), lam=lam)
+np.savez(os.path.join(out, f"rank{rank}.npz"), best=best.cpu().numpy(), x=x.cpu().numpy(), lam=lam)
 drv.close()
 dist.destroy_process_group()
 '''
 
 
-def test_two_image_shards_equal_one_process():
+@pytest.mark.parametrize("mode", ["device", "host"])
+def test_two_image_shards_equal_one_process(mode):
     import torch
     from paper_2109_05339_gb300 import MTIP
     from oracle import slicing
@@ -68,7 +83,7 @@ def test_two_image_shards_equal_one_process():
             so.bind(("127.0.0.1", 0))
             port = so.getsockname()[1]
         env = dict(os.environ, SPF_ROOT=ROOT)
-        procs = [subprocess.Popen([sys.executable, "-c", CHILD, str(r), "2", str(port), tmp], env=env)
+        procs = [subprocess.Popen([sys.executable, "-c", CHILD, str(r), "2", str(port), tmp, mode], env=env)
                  for r in range(2)]
         rcs = []
         for p in procs:
