@@ -1584,7 +1584,7 @@ int class_sums_sets(spf_points* const* sets, int nsets, const uint32_t* const* i
                     int chunk, int n_total, const float* D, float b_scale, int* err, cudaStream_t s) {
   for (int c = 0; c < nsets; ++c) {
     spf_points* S = sets[c];
-    // a compacted spread leaves the sums zeroed: no clearing pass then
+    // the right-hand-side spread leaves the sums zeroed: no clearing pass then
     if (!S->cls_zero) SPF_CUDA(cudaMemsetAsync(S->cls, 0, sizeof(float) * (size_t)S->M * S->P2, s));
     S->cls_zero = false;
     SPF_CUDA(cudaMemsetAsync(S->cnt, 0, sizeof(float) * (size_t)S->M, s));
