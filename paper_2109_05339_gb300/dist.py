@@ -6,6 +6,10 @@ the images: each node sums its own images and the node sums are added
 right-hand side A^H D b and the Toeplitz kernel K^ are summed over the ranks,
 and every rank then runs the same CG solve on identical inputs. lambda is
 scaled by the global image count.
+
+The reduction helpers sit apart from the driver binding (mtip.py) because they
+import without the native library: the two-process gloo test runs them on CPU
+ranks, and the driver calls them between its merge and solve entry points.
 """
 from __future__ import annotations
 
