@@ -268,8 +268,11 @@ int spf_toeplitz_apply(spf_plan* plan, const float* kernel_hat, double lambda,
 /* ---------------------------------------------------------------------------
  * Orientation matching, Sec. II-B: for every image the model image nearest in
  * Euclidean distance d_ij = |x_i|^2 + |y_j|^2 - 2 x_i . y_j (x_i = img_scale *
- * image i). The cross term runs in `precision`; the best `topk` candidates per
- * image are then re-ranked with exact FP32 distances sum_p (x_ip - y_jp)^2,
+ * image i). The cross term runs in `precision`; with BF16 and FP8 the norms
+ * are those of the quantised rows, so the approximate distance is the distance
+ * between the quantised image and model image (0 for an image equal to a model
+ * image). The best `topk` candidates per image by that distance are then
+ * re-ranked with exact FP32 distances sum_p (x_ip - y_jp)^2,
  * so the returned argmin and distances are FP32-exact over the candidates.
  * Ties go to the lower orientation index. Model images can be streamed in
  * chunks: orient_offset is added to the indices of each chunk, and the

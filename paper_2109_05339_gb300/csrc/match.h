@@ -28,8 +28,8 @@ struct spf_matcher {
   float img_scale = 1.f;
   const float* images = nullptr;
   const uint16_t* images16 = nullptr;   // 16-bit photon counts instead (BF16 / FP8 paths)
-  float* x2 = nullptr;            // |img_scale * x_i|^2
-  float* y2 = nullptr;            // |y_j|^2 of the current chunk
+  float* x2 = nullptr;            // |img_scale * x_i|^2 (of the quantised rows on the tensor-core paths)
+  float* y2 = nullptr;            // |y_j|^2 of the current chunk (likewise)
   void* xq = nullptr;             // quantised images  (max_images x Kpad)
   void* yq = nullptr;             // quantised slices  (max_orient x Kpad)
   float* xs = nullptr;            // FP8 per-image scales

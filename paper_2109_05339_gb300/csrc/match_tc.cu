@@ -42,7 +42,11 @@ __device__ __forceinline__ float block_sum_f64(double v, double* sh) {
 }
 
 // BF16 copy of scale * src rows (padding columns stay zero from creation)
-// and the FP32 squared norms of the scaled rows, one CTA per row.
+// and the squared norms of the quantised rows, one CTA per row. With the
+// norms of the quantised rows the approximate distance is the exact distance
+// between the quantised image and model image (up to the FP32 accumulation of
+// the cross term): an image equal to a model image scores 0 against it, and
+// the rounding of the two rows enters only through their difference.
 template <class XT>
 __global__ void __launch_bounds__(256) quantize_bf16_kernel(const XT* __restrict__ src, int P2,
                                                             int Kpad, float scale,
@@ -57,9 +61,10 @@ __global__ void __launch_bounds__(256) quantize_bf16_kernel(const XT* __restrict
     for (int p = threadIdx.x; p < P2 / 4; p += blockDim.x) {
       float4 v = img_elem4(row, p);
       v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
-      a0 = fmaf(v.x, v.x, fmaf(v.y, v.y, a0));
-      a1 = fmaf(v.z, v.z, fmaf(v.w, v.w, a1));
       __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+      const float2 ql = __bfloat1622float2(lo), qh = __bfloat1622float2(hi);
+      a0 = fmaf(ql.x, ql.x, fmaf(ql.y, ql.y, a0));
+      a1 = fmaf(qh.x, qh.x, fmaf(qh.y, qh.y, a1));
       uint2 pk;
       pk.x = *reinterpret_cast<uint32_t*>(&lo);
       pk.y = *reinterpret_cast<uint32_t*>(&hi);
@@ -69,8 +74,10 @@ __global__ void __launch_bounds__(256) quantize_bf16_kernel(const XT* __restrict
     for (int p = threadIdx.x; p < P2; p += blockDim.x) {
       float v = scale * img_elem(row, p);
       if (w) v *= __ldg(w + p);
-      a0 = fmaf(v, v, a0);
-      out[p] = __float2bfloat16_rn(v);
+      const __nv_bfloat16 q = __float2bfloat16_rn(v);
+      const float qf = __bfloat162float(q);
+      a0 = fmaf(qf, qf, a0);
+      out[p] = q;
     }
   }
   __shared__ double sh[8];
@@ -78,42 +85,77 @@ __global__ void __launch_bounds__(256) quantize_bf16_kernel(const XT* __restrict
   if (threadIdx.x == 0) norms[r] = n;
 }
 
+// One e4m3 code (round to nearest, saturating), its square added to sq
+// (exact: 8 significant bits).
+__device__ __forceinline__ uint32_t fp8_code(float v, float& sq) {
+  __nv_fp8_e4m3 q;
+  q.__x = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  const float f = static_cast<float>(q);
+  sq = fmaf(f, f, sq);
+  return q.__x;
+}
+
 // FP8 e4m3 copy with a per-row scale a_r = max_p |scale * src_rp| / 448
-// (1 for an all-zero row): dst = e4m3(scale * src / a_r); also the FP32
-// squared norms of the scaled rows. One CTA per row.
+// (1 for an all-zero row): dst = e4m3(scale * src / a_r); also the squared
+// norms of the quantised rows, a_r^2 sum_p dst_p^2 (the distance between
+// quantised rows, as for BF16). One CTA per row, two passes over it: the
+// maximum, then the codes. Long rows take 512 threads, two CTAs per SM, so
+// that about 300 rows (45 MB of FP32 rows of 36,864 pixels) are in flight and
+// the second pass reads the row from L2; where the row allows, four elements
+// a step (16-byte FP32 or 8-byte 16-bit loads, one 4-byte store of codes),
+// four steps unrolled so that each thread has four loads in flight.
 template <class XT>
-__global__ void __launch_bounds__(256) quantize_fp8_kernel(const XT* __restrict__ src, int P2,
-                                                           int Kpad, float scale,
-                                                           const float* __restrict__ w,
-                                                           __nv_fp8_e4m3* __restrict__ dst,
-                                                           float* __restrict__ row_scale,
-                                                           float* __restrict__ norms) {
+__global__ void __launch_bounds__(512, 2) quantize_fp8_kernel(const XT* __restrict__ src, int P2,
+                                                            int Kpad, float scale,
+                                                            const float* __restrict__ w,
+                                                            __nv_fp8_e4m3* __restrict__ dst,
+                                                            float* __restrict__ row_scale,
+                                                            float* __restrict__ norms) {
   const int r = blockIdx.x;
   const XT* row = src + (size_t)r * P2;
-  float mx = 0.f, a0 = 0.f;
-  for (int k = threadIdx.x; k < P2; k += blockDim.x) {
-    float v = scale * img_elem(row, k);
-    if (w) v *= __ldg(w + k);
-    mx = fmaxf(mx, fabsf(v));
-    a0 = fmaf(v, v, a0);
+  __nv_fp8_e4m3* out = dst + (size_t)r * Kpad;
+  const bool vec = (P2 % 4) == 0 && (((uintptr_t)row) & (4 * sizeof(XT) - 1)) == 0;
+  const int n4 = vec ? P2 / 4 : 0;
+  const float4 one = make_float4(1.f, 1.f, 1.f, 1.f);
+  float mx = 0.f;
+#pragma unroll 4
+  for (int p = threadIdx.x; p < n4; p += blockDim.x) {
+    const float4 v = img_elem4(row, p);
+    const float4 c = w ? __ldg(reinterpret_cast<const float4*>(w) + p) : one;
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(scale * v.x * c.x), fabsf(scale * v.y * c.y)),
+                         fmaxf(fabsf(scale * v.z * c.z), fabsf(scale * v.w * c.w))));
   }
+  for (int k = 4 * n4 + threadIdx.x; k < P2; k += blockDim.x)
+    mx = fmaxf(mx, fabsf(scale * img_elem(row, k) * (w ? __ldg(w + k) : 1.f)));
   __shared__ float sm[32];
-  __shared__ double sh[8];
-  float n = block_sum_f64((double)a0, sh);
+  __shared__ double sh[32];
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     float m = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sm[w]);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, sm[i]);
     sm[0] = m > 0.f ? m / 448.f : 1.f;
     row_scale[r] = sm[0];
-    norms[r] = n;
   }
   __syncthreads();
-  const float inv = 1.f / sm[0];
-  for (int k = threadIdx.x; k < P2; k += blockDim.x)
-    dst[(size_t)r * Kpad + k] = __nv_fp8_e4m3(scale * img_elem(row, k) * (w ? __ldg(w + k) : 1.f) * inv);
+  const float a = sm[0], inv = 1.f / a;
+  float a0 = 0.f;
+#pragma unroll 4
+  for (int p = threadIdx.x; p < n4; p += blockDim.x) {
+    const float4 v = img_elem4(row, p);
+    const float4 c = w ? __ldg(reinterpret_cast<const float4*>(w) + p) : one;
+    const uint32_t b0 = fp8_code(scale * v.x * c.x * inv, a0), b1 = fp8_code(scale * v.y * c.y * inv, a0);
+    const uint32_t b2 = fp8_code(scale * v.z * c.z * inv, a0), b3 = fp8_code(scale * v.w * c.w * inv, a0);
+    reinterpret_cast<uint32_t*>(out)[p] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+  }
+  for (int k = 4 * n4 + threadIdx.x; k < P2; k += blockDim.x) {
+    __nv_fp8_e4m3 q;
+    q.__x = (__nv_fp8_storage_t)fp8_code(scale * img_elem(row, k) * (w ? __ldg(w + k) : 1.f) * inv, a0);
+    out[k] = q;
+  }
+  const float n = block_sum_f64((double)a0, sh);
+  if (threadIdx.x == 0) norms[r] = n * a * a;
 }
 
 }  // namespace
@@ -133,10 +175,11 @@ int quantize_rows_t(spf_matcher* m, const XT* src, int rows, float scale, void* 
                                                     static_cast<__nv_bfloat16*>(dst), norms);
     }, (double)rows * m->P2 * (sizeof(XT) + 2.0));
   }
+  const int threads = m->P2 >= 8192 ? 512 : 256;
   return launch("quantize_fp8_kernel", s, [&] {
-    quantize_fp8_kernel<XT><<<rows, 256, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
-                                                 static_cast<__nv_fp8_e4m3*>(dst), scales, norms);
-  }, (double)rows * m->P2 * (2.0 * sizeof(XT) + 1.0));
+    quantize_fp8_kernel<XT><<<rows, threads, 0, s>>>(src, m->P2, m->Kpad, scale, m->wsq,
+                                                     static_cast<__nv_fp8_e4m3*>(dst), scales, norms);
+  }, (double)rows * m->P2 * (sizeof(XT) + 1.0));
 }
 
 int quantize_rows(spf_matcher* m, const float* src, int rows, float scale, void* dst, float* scales,

@@ -51,7 +51,7 @@ def _check(r, ref, X, Y):
     return ok
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_noise_free_images_recover_exactly(c1_data, precision):
     pb, slices, clean, _ = c1_data
     r = _run(precision, clean, slices, 1.0)
@@ -60,7 +60,7 @@ def test_noise_free_images_recover_exactly(c1_data, precision):
     np.testing.assert_array_equal(r["best"], ref["best"])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_poisson_images_above_margin(c1_data, precision):
     pb, slices, _, counts = c1_data
     s = 1.0 / pb.cfg.photons
@@ -108,8 +108,8 @@ def test_deferred_rerank_over_chunks(c1_data, precision):
     torch.cuda.synchronize()
     Xd = f32(X) * np.float64(scale)
     ref = matching.match(Xd, f32(slices))
-    ok = _check(r, ref, Xd, f32(slices)) if precision != "fp8" else ref["margin"] > 1e-2
-    np.testing.assert_array_equal(r["best"][ok], ref["best"][ok])
+    ok = _check(r, ref, Xd, f32(slices))
+    assert ok.sum() >= 1
     assert np.all(np.diff(r["topk_d"], axis=1) >= 0)
     m.close()
 
@@ -140,7 +140,7 @@ def test_tensor_core_ragged_tiles(precision, n_img, n_orient, P2, schedule):
     X = (Y[pick] + rng.normal(0, 0.05, (n_img, P2))).astype(np.float32)
     ref = matching.match(f32(X), f32(Y))
     r = _run(precision, X, Y, 1.0, schedule=schedule)
-    ok = ref["margin"] > (MARGIN if precision == "bf16" else 1e-2)
+    ok = ref["margin"] > MARGIN
     np.testing.assert_array_equal(r["best"][ok], ref["best"][ok])
     d_true = np.sum((f32(X) - f32(Y)[r["best"]]) ** 2, axis=1)
     scale = np.sum(f32(X) ** 2, 1) + np.sum(f32(Y)[r["best"]] ** 2, 1)
@@ -148,30 +148,26 @@ def test_tensor_core_ragged_tiles(precision, n_img, n_orient, P2, schedule):
 
 
 def test_fp8_precision_study(c1_data):
-    """Config-3 study: FP8 e4m3 cross term with per-row scales and FP32 re-rank
-    of the top 8; agreement with the FP64 argmin must be complete wherever the
-    margin exceeds the FP8 error scale, and is reported below it."""
+    """Config-3 study: FP8 e4m3 cross term with per-row scales, norms of the
+    quantised rows and the FP32 re-rank of the top 8 agrees with the FP64
+    argmin on every Poisson image above the margin and recovers the generating
+    orientation of every noise-free image, as BF16 does. (With the norms of
+    the unquantised rows, a noise-free image scored about 2^-4 / sqrt(P2) of
+    |x|^2 against its own model image, more than the margins between
+    neighbouring c1 model images, down to 4e-5, and 30% of the noise-free
+    images lost their orientation before the re-rank.)"""
     pb, slices, clean, counts = c1_data
     s = np.float32(1.0 / pb.cfg.photons)
     X = f32(counts) * np.float64(s)
     ref = matching.match(X, f32(slices))
-    r8 = _run("fp8", counts, slices, s)
-    rb = _run("bf16", counts, slices, s)
-    for r in (r8, rb):
-        agree = r["best"] == ref["best"]
-        assert np.all(agree[ref["margin"] > 1e-2])
-    # noise-free images: the BF16 path recovers every generating orientation
-    # (its exact distance is 0 and it survives to the FP32 re-rank); FP8's
-    # rounding (2^-4 relative) exceeds the margins between neighbouring model
-    # images (down to 4e-5 here), so FP8 recovers exactly where the margin
-    # exceeds its error scale and the rest is reported
+    ok = ref["margin"] > MARGIN
+    assert ok.sum() >= 50
+    for p in ("fp8", "bf16"):
+        np.testing.assert_array_equal(_run(p, counts, slices, s)["best"][ok], ref["best"][ok])
     refc = matching.match(f32(clean), f32(slices))
     np.testing.assert_array_equal(refc["best"], pb.img_pick)
-    rbc = _run("bf16", clean, slices, 1.0)
-    np.testing.assert_array_equal(rbc["best"], pb.img_pick)
-    r8c = _run("fp8", clean, slices, 1.0)
-    clear = refc["margin"] > 1e-2
-    np.testing.assert_array_equal(r8c["best"][clear], pb.img_pick[clear])
+    for p in ("fp8", "bf16"):
+        np.testing.assert_array_equal(_run(p, clean, slices, 1.0)["best"], pb.img_pick)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
@@ -195,9 +191,8 @@ def test_beamstop_mask_weighted_matching(precision):
     m.status()
     Xd = f32(X) * np.float64(scale)
     ref = matching.match(Xd, f32(Y), D=f32(D))
-    ok = ref["margin"] > (MARGIN if precision != "fp8" else 1e-2)
-    if precision != "fp8":
-        assert ok.sum() > 60
+    ok = ref["margin"] > MARGIN
+    assert ok.sum() > 60
     np.testing.assert_array_equal(r["best"][ok], ref["best"][ok])
     w = f32(D)
     d_true = np.sum(w * (Xd - f32(Y)[r["best"]]) ** 2, axis=1)
@@ -241,7 +236,7 @@ def test_sixteen_bit_images_equal_fp32_images(c1_data, precision, P2, offset):
         m.close()
     Xd = f32(X) * np.float64(scale)
     ref = matching.match(Xd, f32(Y))
-    ok = ref["margin"] > (MARGIN if precision == "bf16" else 1e-2)
+    ok = ref["margin"] > MARGIN
     np.testing.assert_array_equal(out[1]["best"][ok], ref["best"][ok])
     if offset == 0:
         # the same loads in the same order: bit-identical results
