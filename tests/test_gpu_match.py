@@ -60,6 +60,19 @@ def test_noise_free_images_recover_exactly(c1_data, precision):
     np.testing.assert_array_equal(r["best"], ref["best"])
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_quantised_pass_ranks_the_generating_orientation_first(c1_data, precision):
+    """With the norms of the quantised rows, the tensor-core pass scores a
+    noise-free image 0 against its own model image, so two candidates per
+    image suffice for the re-rank to recover every generating orientation.
+    (With the norms of the unquantised rows, a numpy model of this pass kept
+    it among the best 2 for 34% of these images under FP8 and 98% under
+    BF16.)"""
+    pb, slices, clean, _ = c1_data
+    r = _run(precision, clean, slices, 1.0, topk=2)
+    np.testing.assert_array_equal(r["best"], pb.img_pick)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_poisson_images_above_margin(c1_data, precision):
     pb, slices, _, counts = c1_data
