@@ -100,6 +100,7 @@ int cg_objective(spf_plan* P, const float* khat, const float* rhs, const float* 
 int weighted_sumsq(spf_plan* P, const float* img, int64_t n, int P2, const float* D, float scale,
                    double* out, int accumulate, cudaStream_t s);
 // match.cu / match_tc.cu
+int simt_splits(int n_img, int n_orient, int n_sms);
 int simt_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
                 cudaStream_t s);
 int row_norms(const float* src, int rows, int P2, float scale, float* out, cudaStream_t s);
@@ -632,13 +633,6 @@ int spf_matcher_set_images_u16(spf_matcher* m, const uint16_t* images, int n_img
   return state_reset(m, s);
 }
 
-static int choose_splits(const spf_matcher* m, int n_orient, int tile_m, int tile_n) {
-  int img_tiles = (int)ceil_div(m->n_img, tile_m);
-  int or_tiles = (int)ceil_div(n_orient, tile_n);
-  int want = (int)ceil_div(2 * m->n_sms, std::max(1, img_tiles));
-  return std::max(1, std::min({want, or_tiles, kMaxSplits}));
-}
-
 int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient, int orient_offset,
                            void* stream) {
   clear_error();
@@ -655,7 +649,7 @@ int spf_matcher_add_slices(spf_matcher* m, const float* slices, int n_orient, in
   int nsplit;
   if (m->precision == SPF_FP32) {
     SPF_TRY(row_norms_w(slices, n_orient, m->P2, 1.f, m->wsq, m->y2, s));
-    nsplit = choose_splits(m, n_orient, 128, 128);
+    nsplit = simt_splits(m->n_img, n_orient, m->n_sms);
     SPF_TRY(simt_launch(m, slices, n_orient, orient_offset, nsplit, s));
   } else {
     SPF_TRY(quantize_rows(m, slices, n_orient, 1.f, m->yq, m->ys, m->y2, s));

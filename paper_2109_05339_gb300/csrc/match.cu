@@ -516,6 +516,28 @@ __global__ void results_kernel(const float* __restrict__ st_d, const int* __rest
 
 }  // namespace
 
+// Orientation splits of a CUDA-core launch: the split count whose makespan,
+// (waves of CTAs over two per SM) x (orientation tiles per split), is
+// smallest; counts that would leave a split empty are skipped. The merged top
+// list does not depend on the count (candidates merge in (score, index)
+// order).
+int simt_splits(int n_img, int n_orient, int n_sms) {
+  const int64_t img_tiles = ceil_div(n_img, BM), or_tiles = ceil_div(n_orient, BN);
+  const int64_t slots = 2 * (int64_t)std::max(n_sms, 1);
+  int best = 1;
+  int64_t best_span = INT64_MAX;
+  for (int sp = 1; sp <= std::min<int64_t>(or_tiles, kMaxSplits); ++sp) {
+    const int64_t tps = ceil_div(or_tiles, sp);
+    if (ceil_div(or_tiles, tps) != sp) continue;
+    const int64_t span = ceil_div(img_tiles * sp, slots) * tps;
+    if (span < best_span) {
+      best_span = span;
+      best = sp;
+    }
+  }
+  return best;
+}
+
 int simt_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
                 cudaStream_t s) {
   int n_ot = (int)ceil_div(n_orient, BN);

@@ -18,6 +18,7 @@
 #include "match.h"
 
 namespace spf {
+int simt_splits(int n_img, int n_orient, int n_sms);
 int simt_launch(spf_matcher* m, const float* slices, int n_orient, int orient_offset, int nsplit,
                 cudaStream_t s);
 int row_norms(const float* src, int rows, int P2, float scale, float* out, cudaStream_t s);
@@ -147,10 +148,7 @@ extern "C" int spf_match_orientations_static(const float* images, int n_img, flo
   SPF_TRY(state_reset(&m, s));
   if (n_orient > 0) {
     SPF_TRY(row_norms(slices, n_orient, P2, 1.f, m.y2, s));
-    const int img_tiles = (int)ceil_div(n_img, 128);
-    const int or_tiles = (int)ceil_div(n_orient, 128);
-    const int want = (int)ceil_div(2 * m.n_sms, img_tiles);
-    const int nsplit = std::max(1, std::min(std::min(want, or_tiles), kMaxSplits));
+    const int nsplit = simt_splits(n_img, n_orient, m.n_sms);
     SPF_TRY(simt_launch(&m, slices, n_orient, 0, nsplit, s));
     SPF_TRY(rerank_launch(&m, slices, n_orient, 0, nsplit, s));
   }
