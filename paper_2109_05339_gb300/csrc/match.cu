@@ -119,36 +119,69 @@ __device__ __forceinline__ void list_insert_ordered(float* tv, int* ti, float s,
 // ----------------------------------------------------- FP32 SIMT GEMM ----
 // CTA tile: 128 images x 128 orientations, 256 threads, each computing an 8x8
 // block as four 4x4 quadrants (rows ty*4 and 64+ty*4, columns tx*4 and
-// 64+tx*4, conflict-free float4 shared reads). k-tiles of 8 are double-
-// buffered in shared memory with a register prefetch of the next tile.
-// Grid: (image tiles, orientation splits); a CTA walks its range of
+// 64+tx*4, conflict-free float4 shared reads). k-tiles of 16 are double-
+// buffered in shared memory; the next tile is prefetched through 8 registers
+// a thread in two halves: its image rows are loaded at the start of a tile and
+// stored half-way through, its model-image rows loaded then and stored at the
+// end, so each load has half a tile of FMAs to arrive and one barrier serves
+// 16 k. Grid: (image tiles, orientation splits); a CTA walks its range of
 // orientation tiles and keeps a running top-8 per image row in shared memory.
-constexpr int BM = 128, BN = 128, BK = 8;
+constexpr int BM = 128, BN = 128, BK = 16;
 
-template <bool VEC>
+// Thread t's share of a 128 x 16 k-tile: row r0 + t / 2, the 8 elements from
+// k0 + (t % 2) * 8 (zero beyond rows or P2), scaled and (WGT) weighted.
+template <bool VEC, bool WGT>
 __device__ __forceinline__ void simt_load(const float* __restrict__ X, int rows, int P2, int r0, int k0,
-                                          float scale, const float* __restrict__ w, float (&v)[4]) {
+                                          float scale, const float* __restrict__ w, float (&v)[8]) {
   const int t = threadIdx.x;
-  const int row = r0 + (t >> 1), k = k0 + (t & 1) * 4;
+  const int row = r0 + (t >> 1), k = k0 + (t & 1) * 8;
   if (VEC) {
-    if (row < rows && k < P2) {
-      float4 q = __ldg(reinterpret_cast<const float4*>(X + (size_t)row * P2 + k));
-      v[0] = scale * q.x; v[1] = scale * q.y; v[2] = scale * q.z; v[3] = scale * q.w;
-    } else {
-      v[0] = v[1] = v[2] = v[3] = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (row < rows && k + 4 * h < P2) {
+        float4 q = __ldg(reinterpret_cast<const float4*>(X + (size_t)row * P2 + k + 4 * h));
+        v[4 * h] = scale * q.x; v[4 * h + 1] = scale * q.y; v[4 * h + 2] = scale * q.z; v[4 * h + 3] = scale * q.w;
+      } else {
+        v[4 * h] = v[4 * h + 1] = v[4 * h + 2] = v[4 * h + 3] = 0.f;
+      }
     }
   } else {
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
+    for (int e = 0; e < 8; ++e)
       v[e] = (row < rows && k + e < P2) ? scale * __ldg(X + (size_t)row * P2 + k + e) : 0.f;
   }
-  if (w) {
+  if (WGT) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] *= (k + e < P2) ? __ldg(w + k + e) : 0.f;
+    for (int e = 0; e < 8; ++e) v[e] *= (k + e < P2) ? __ldg(w + k + e) : 0.f;
   }
 }
 
-template <bool VEC>
+// v (from simt_load) into the k-major shared tile T[BK][128].
+__device__ __forceinline__ void simt_store(float* T, const float (&v)[8]) {
+  const int t = threadIdx.x;
+  const int row = t >> 1, k = (t & 1) * 8;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) T[(k + e) * BM + row] = v[e];
+}
+
+// 8 k steps of the 8 x 8 register tile from the k-major tiles A and B.
+__device__ __forceinline__ void simt_fma8(const float* A, const float* B, int tx, int ty, float (&acc)[8][8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float4 a0 = *reinterpret_cast<const float4*>(A + k * BM + ty * 4);
+    float4 a1 = *reinterpret_cast<const float4*>(A + k * BM + 64 + ty * 4);
+    float4 b0 = *reinterpret_cast<const float4*>(B + k * BN + tx * 4);
+    float4 b1 = *reinterpret_cast<const float4*>(B + k * BN + 64 + tx * 4);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+  }
+}
+
+template <bool VEC, bool WGT>
 __global__ void __launch_bounds__(256, 2)
 simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const float* __restrict__ Y,
                   int n_orient, int orient_offset, int P2, const float* __restrict__ y2,
@@ -173,7 +206,6 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
       Lv[tid * kCand + q] = FLT_MAX;
       Li[tid * kCand + q] = -1;
     }
-  const int srow = tid >> 1, sk = (tid & 1) * 4;
 
   for (int ot = ot_begin; ot < ot_end; ++ot) {
     const int j0 = ot * BN;
@@ -182,46 +214,28 @@ simt_match_kernel(const float* __restrict__ X, int n_img, float xscale, const fl
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-    float ra[4], rb[4];
-    simt_load<VEC>(X, n_img, P2, i0, 0, xscale, wsq, ra);
-    simt_load<VEC>(Y, n_orient, P2, j0, 0, 1.f, wsq, rb);
+    float rv[8];
     __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      As[(sk + e) * BM + srow] = ra[e];
-      Bs[(sk + e) * BN + srow] = rb[e];
-    }
+    simt_load<VEC, WGT>(X, n_img, P2, i0, 0, xscale, wsq, rv);
+    simt_store(As, rv);
+    simt_load<VEC, WGT>(Y, n_orient, P2, j0, 0, 1.f, wsq, rv);
+    simt_store(Bs, rv);
     __syncthreads();
     int buf = 0;
     for (int k0 = 0; k0 < P2; k0 += BK) {
       const bool more = k0 + BK < P2;
-      if (more) {
-        simt_load<VEC>(X, n_img, P2, i0, k0 + BK, xscale, wsq, ra);
-        simt_load<VEC>(Y, n_orient, P2, j0, k0 + BK, 1.f, wsq, rb);
-      }
       const float* A = As + buf * BK * BM;
       const float* B = Bs + buf * BK * BN;
-#pragma unroll
-      for (int k = 0; k < BK; ++k) {
-        float4 a0 = *reinterpret_cast<const float4*>(A + k * BM + ty * 4);
-        float4 a1 = *reinterpret_cast<const float4*>(A + k * BM + 64 + ty * 4);
-        float4 b0 = *reinterpret_cast<const float4*>(B + k * BN + tx * 4);
-        float4 b1 = *reinterpret_cast<const float4*>(B + k * BN + 64 + tx * 4);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
-      }
+      if (more) simt_load<VEC, WGT>(X, n_img, P2, i0, k0 + BK, xscale, wsq, rv);
+      simt_fma8(A, B, tx, ty, acc);
       if (more) {
-        float* An = As + (buf ^ 1) * BK * BM;
-        float* Bn = Bs + (buf ^ 1) * BK * BN;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          An[(sk + e) * BM + srow] = ra[e];
-          Bn[(sk + e) * BN + srow] = rb[e];
-        }
+        // the other buffers were last read before the previous barrier
+        simt_store(As + (buf ^ 1) * BK * BM, rv);
+        simt_load<VEC, WGT>(Y, n_orient, P2, j0, k0 + BK, 1.f, wsq, rv);
+      }
+      simt_fma8(A + 8 * BM, B + 8 * BN, tx, ty, acc);
+      if (more) {
+        simt_store(Bs + (buf ^ 1) * BK * BN, rv);
         __syncthreads();
         buf ^= 1;
       }
@@ -545,22 +559,15 @@ int simt_launch(spf_matcher* m, const float* slices, int n_orient, int orient_of
   dim3 grid((unsigned)ceil_div(m->n_img, BM), (unsigned)nsplit);
   size_t smem = sizeof(float) * (2 * BK * BM + 2 * BK * BN + BM * (BN + 1) + 2 * BM * kCand);
   const bool vec = (m->P2 % 4) == 0 && ((uintptr_t)m->images % 16) == 0 && ((uintptr_t)slices % 16) == 0;
-  if (vec) {
-    SPF_CUDA(cudaFuncSetAttribute(simt_match_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  auto go = [&](auto kernel) -> int {
+    SPF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return launch("simt_match_kernel", s, [&] {
-      simt_match_kernel<true><<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient,
-                                                      orient_offset, m->P2, m->y2, tps, m->wsq,
-                                                      m->cand_v, m->cand_i);
+      kernel<<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient, orient_offset, m->P2,
+                                     m->y2, tps, m->wsq, m->cand_v, m->cand_i);
     });
-  }
-  SPF_CUDA(cudaFuncSetAttribute(simt_match_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
-  return launch("simt_match_kernel", s, [&] {
-    simt_match_kernel<false><<<grid, 256, smem, s>>>(m->images, m->n_img, m->img_scale, slices, n_orient,
-                                                     orient_offset, m->P2, m->y2, tps, m->wsq,
-                                                     m->cand_v, m->cand_i);
-  });
+  };
+  if (m->wsq) return vec ? go(simt_match_kernel<true, true>) : go(simt_match_kernel<false, true>);
+  return vec ? go(simt_match_kernel<true, false>) : go(simt_match_kernel<false, false>);
 }
 
 int row_norms_w(const float* src, int rows, int P2, float scale, const float* w, float* out,
