@@ -9,8 +9,11 @@ sample. Steps, in the paper's order:
    and of the weights (Toeplitz kernel), then ``cg_iters`` conjugate-gradient
    steps from x0 = A with lambda = lam_rel * sum(D).
 
-Parity unpinned beyond its parts: every part is pinned in its own module;
-the composition itself has no independent reference.
+Every part is pinned in its own module; the composition is pinned by the
+fixed point that Eq. 2 fixes: images equal to the model's own slices at
+reference orientations (direct NUDFT sums) are matched to those orientations
+exactly and x = x0 solves the normal equations, so the iteration returns the
+model (tests/test_oracle_mtip.py).
 """
 import numpy as np
 
