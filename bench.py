@@ -382,7 +382,7 @@ def run_ours(args, rank, world):
                    "l2": (f"inputs larger than L2 (images {Ni * P2 * 4 / 1e6:.0f} MB, slices "
                           f"{drv.orient_chunk * P2 * 4 / 1e6:.0f} MB per chunk)"),
                    "orient_chunk": drv.orient_chunk,
-                   "point_sets": "cached" if drv.cache_points else "streamed",
+                   "point_sets": drv.point_mode,
                    "images_on_device": "16-bit photon counts" if counts16 is not None else "FP32",
                    "device_memory_in_use_gb": round((total_b - free_b) / 1e9, 1)},
         "nufft_mpts_per_s": {

@@ -353,10 +353,11 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
  * driver renumbers it along a Morton curve of the quaternions (neighbouring
  * indices are neighbours on SO(3), which keeps candidate model images of
  * images re-ranked together in L2). Its points are either sorted per
- * orientation chunk once and kept (about 16 bytes per orientation x pixel),
- * or, beyond the memory budget, re-sorted per chunk for slicing on every
- * iteration while the merge spreads image chunks at their matched
- * orientations. Orientation indices passed in or out are in the caller's
+ * orientation chunk once and kept (about 16 bytes per orientation x pixel);
+ * or only their sort for slicing is kept (about 4 bytes per orientation x
+ * pixel) while the merge spreads image chunks at their matched orientations;
+ * or, beyond that budget too, they are re-sorted per chunk for slicing on
+ * every iteration and the merge spreads image chunks. Orientation indices passed in or out are in the caller's
  * numbering; exact distance ties resolve to the lower index in the driver's.
  *
  * An iteration (spf_mtip_iteration): (1) the model A is sliced at every
@@ -376,16 +377,18 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
  *   per call; n_orient orientations; orient_chunk orientations sliced and
  *   matched per chunk (0: all); img_chunk images merged per type-1 pass when
  *   streaming (0: all); precision and topk as spf_matcher_create;
- *   cache_points 1 keep the sorted point sets, 0 stream, -1 keep them when
- *   16 * n_orient * P2 bytes fit point_budget_bytes (<= 0: half of the
- *   device's free memory at create); host_image_type SPF_IMAGES_F32 /
+ *   cache_points 1 keep the sorted point sets, 2 keep slice-only sets and
+ *   merge image chunks, 0 stream (re-sort per chunk, merge image chunks),
+ *   -1 choose: 1 when 16 * n_orient * P2 bytes fit point_budget_bytes (<= 0:
+ *   half of the device's free memory at create), else 2 when 4 * n_orient *
+ *   P2 bytes do, else 0; host_image_type SPF_IMAGES_F32 /
  *   SPF_IMAGES_U16 allocates two device input slots for
  *   spf_mtip_iteration_host, -1 none; device ordinal.
  * spf_mtip_create allocates the plan, the matcher, a slice chunk, an FP32
  *   image buffer (max_images x P2), the merge and CG buffers and the host-path
  *   slots. Synchronous. spf_mtip_set_orientations copies quats (n_orient x 4)
- *   and q_lab (P2 x 3) and, when keeping point sets, creates and sorts them
- *   (it allocates: a set-up call); synchronous. spf_mtip_set_mask: pixel
+ *   and q_lab (P2 x 3) and, when keeping point sets (full or slice-only),
+ *   creates and sorts them (it allocates: a set-up call); synchronous. spf_mtip_set_mask: pixel
  *   weights D (P2 floats, device, >= 0, caller-owned and kept until replaced)
  *   for matching, merging and lambda, or NULL for ones; synchronous.
  * spf_mtip_match: best (n_img, device) in the caller's numbering; best_d,

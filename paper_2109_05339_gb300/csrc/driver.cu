@@ -6,10 +6,11 @@
 // it renumbers them along a Morton curve of the quaternions (orientations
 // close in index are close on SO(3), so images re-ranked together share
 // candidate model images in L2), and either sorts the rotated points of every
-// orientation chunk once and keeps them (16 bytes per orientation x pixel) or,
-// when that exceeds the memory budget, re-sorts each chunk's points for
-// slicing alone on every iteration and merges image chunks at their matched
-// orientations. An iteration:
+// orientation chunk once and keeps them (16 bytes per orientation x pixel);
+// or, when that exceeds the memory budget, keeps only each chunk's sort for
+// slicing (4 bytes per orientation x pixel) and merges image chunks at their
+// matched orientations; or, when that too exceeds it, re-sorts each chunk's
+// points for slicing on every iteration. An iteration:
 //   1. slicing (Sec. II-A) and matching (Sec. II-B), streamed in orientation
 //      chunks through one slice buffer; the matcher's running top-k survives
 //      across chunks;
@@ -95,6 +96,7 @@ std::vector<int> morton_order(const std::vector<float>& q, int M) {
 }
 
 constexpr int64_t kPointSetBytes = 16;   // per kept (orientation, pixel): two sort orders, inverse, class sum
+constexpr int64_t kSliceSetBytes = 4;    // per kept (orientation, pixel) of a slice-only set: its sort order
 
 }  // namespace
 }  // namespace spf
@@ -104,6 +106,7 @@ struct spf_mtip {
   spf_plan* plan = nullptr;
   spf_matcher* matcher = nullptr;
   bool cache_points = false;
+  bool slice_sets = false;         // slice-only point sets kept per chunk; the merge streams
   bool keep_slices = false;        // slices of all chunks kept: one deferred re-rank
   int orient_chunk = 0, img_chunk = 0;
   // orientation set in the driver's numbering
@@ -112,11 +115,11 @@ struct spf_mtip {
   float* qlab = nullptr;           // P2 x 3
   int* order = nullptr;            // driver index -> caller index
   int* inv = nullptr;              // caller index -> driver index
-  std::vector<spf_points*> sets;   // kept point sets, one per orientation chunk
+  std::vector<spf_points*> sets;   // kept point sets (full, or slice-only), one per orientation chunk
   uint32_t** inv_tab = nullptr;    // device tables of the sets' inverse orders, class sums, counts
   float** cls_tab = nullptr;
   float** cnt_tab = nullptr;
-  spf_points stream_set;           // streaming: one slice-only set, re-sorted per chunk
+  spf_points stream_set;           // streaming: one slice-only set, re-sorted per chunk per call
   float* slices = nullptr;         // orient_chunk x P2, or n_orient x P2 when kept
   float* img32 = nullptr;          // max_images x P2: 16-bit counts converted to FP32 (FP32
                                    // matching or streamed merges only)
@@ -329,7 +332,7 @@ int match_core(spf_mtip* h, const float* A, const ImgIn& img, int n_img, float i
   for (int c = 0, c0 = 0; c0 < M; ++c, c0 += h->orient_chunk) {
     const int m = std::min(h->orient_chunk, M - c0);
     float* out = h->keep_slices ? h->slices + (size_t)c0 * P2 : h->slices;
-    if (h->cache_points) {
+    if (h->cache_points || h->slice_sets) {
       SPF_TRY(slice_points(P, h->sets[c], A, out, s));
     } else {
       spf_points& S = h->stream_set;
@@ -406,7 +409,7 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
   const spf_mtip_config& c = *cfg;
   SPF_CHECK_ARG(c.P2 > 0 && c.max_images >= 1 && c.n_orient >= 1, "P2, max_images and n_orient must be positive");
   SPF_CHECK_ARG(c.orient_chunk >= 0 && c.img_chunk >= 0, "chunk sizes must be >= 0 (0: all at once)");
-  SPF_CHECK_ARG(c.cache_points >= -1 && c.cache_points <= 1, "cache_points must be -1, 0 or 1");
+  SPF_CHECK_ARG(c.cache_points >= -1 && c.cache_points <= 2, "cache_points must be -1, 0, 1 or 2");
   SPF_CHECK_ARG(c.host_image_type >= -1 && c.host_image_type <= SPF_IMAGES_U16, "unknown host image type");
   SPF_CHECK_ARG(c.keep_slices >= -1 && c.keep_slices <= 1, "keep_slices must be -1, 0 or 1");
   const int chunk = std::min(c.n_orient, c.orient_chunk > 0 ? c.orient_chunk : c.n_orient);
@@ -419,6 +422,7 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
   h->orient_chunk = chunk;
   if (c.cache_points >= 0) {
     h->cache_points = c.cache_points == 1;
+    h->slice_sets = c.cache_points == 2;
   } else {
     int64_t budget = c.point_budget_bytes;
     if (budget <= 0) {
@@ -427,6 +431,7 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
       budget = (int64_t)(fr / 2);
     }
     h->cache_points = kPointSetBytes * (int64_t)c.n_orient * P2 <= budget;
+    h->slice_sets = !h->cache_points && kSliceSetBytes * (int64_t)c.n_orient * P2 <= budget;
   }
   if (c.keep_slices >= 0) {
     h->keep_slices = c.keep_slices == 1;
@@ -464,7 +469,7 @@ int spf_mtip_create(spf_mtip** out, const spf_mtip_config* cfg) {
   A((void**)&h->khat, sizeof(float) * std::max<size_t>(PT3, 1), "Toeplitz kernel");
   A((void**)&h->x, sizeof(float) * n3, "merged model");
   A((void**)&h->err, sizeof(int), "driver error word");
-  if (rc == SPF_OK && !h->cache_points) {
+  if (rc == SPF_OK && !h->cache_points && !h->slice_sets) {
     spf_points& S = h->stream_set;
     S.plan = h->plan;
     S.device = c.device;
@@ -528,7 +533,7 @@ int spf_mtip_info(const spf_mtip* h, int* cache_points, int* orient_chunk, int* 
   clear_error();
   SPF_TRY(check_handle(h, false));
   if (keep_slices) *keep_slices = h->keep_slices ? 1 : 0;
-  if (cache_points) *cache_points = h->cache_points ? 1 : 0;
+  if (cache_points) *cache_points = h->cache_points ? 1 : h->slice_sets ? 2 : 0;
   if (orient_chunk) *orient_chunk = h->orient_chunk;
   if (img_chunk) *img_chunk = h->img_chunk;
   return SPF_OK;
@@ -608,6 +613,14 @@ int spf_mtip_set_orientations(spf_mtip* h, const float* quats, const float* q_la
     SPF_CUDA(cudaMemcpyAsync(h->cls_tab, ct.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, s));
     SPF_CUDA(cudaMemcpyAsync(h->cnt_tab, nt.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, s));
     SPF_CUDA(cudaStreamSynchronize(s));
+  } else if (h->slice_sets) {
+    for (int c0 = 0; c0 < M; c0 += h->orient_chunk) {
+      const int m = std::min(h->orient_chunk, M - c0);
+      spf_points* p = nullptr;
+      SPF_TRY(spf_points_create(&p, h->plan, h->quats_sorted + 4 * (size_t)c0, m, h->qlab, P2,
+                                SPF_POINTS_SLICE_ONLY, stream));
+      h->sets.push_back(p);
+    }
   } else {
     h->stream_set.qlab = h->qlab;
   }

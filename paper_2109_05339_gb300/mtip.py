@@ -64,13 +64,18 @@ def _tensor_key(t):
     return (t.data_ptr(), tuple(t.shape), t._version)
 
 
+_POINT_MODES = {None: -1, True: 1, False: 0, "slices": 2}
+
+
 class MTIP:
     def __init__(self, N, qmax, P2, n_img, n_orient, orient_chunk=None, img_chunk=None,
                  eps=1e-6, precision="bf16", topk=8, device=None, cache_points=None,
                  point_budget_bytes=None, process_group=None, host_images=None, keep_slices=None):
-        """cache_points: keep every chunk's sorted points (True), stream them
-        (False), or decide from point_budget_bytes (None; default budget: half
-        of the device's free memory). process_group: the images are one shard
+        """cache_points: keep every chunk's sorted points (True), keep only
+        their sort for slicing and merge image chunks ("slices"), re-sort per
+        chunk on every call (False), or decide from point_budget_bytes (None:
+        the first of these that fits; default budget: half of the device's free
+        memory). process_group: the images are one shard
         of a torch.distributed group. host_images: None, "f32" or "u16" --
         the image type of iteration_host (allocates its two device slots).
         keep_slices: keep every chunk's slices and re-rank once per iteration
@@ -82,7 +87,7 @@ class MTIP:
                          n_orient=int(n_orient), orient_chunk=int(orient_chunk or 0),
                          img_chunk=int(img_chunk or 0),
                          precision=PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                         topk=int(topk), cache_points=-1 if cache_points is None else int(bool(cache_points)),
+                         topk=int(topk), cache_points=_POINT_MODES[cache_points],
                          point_budget_bytes=int(point_budget_bytes or 0),
                          host_image_type={None: -1, "f32": SPF_IMAGES_F32, "u16": SPF_IMAGES_U16}[host_images],
                          device=dev, keep_slices=-1 if keep_slices is None else int(bool(keep_slices)))
@@ -91,7 +96,8 @@ class MTIP:
         self._h = h
         cp, oc, ic, ks = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         check(lib.spf_mtip_info(h, C.byref(cp), C.byref(oc), C.byref(ic), C.byref(ks)))
-        self.cache_points, self.orient_chunk, self.img_chunk = bool(cp.value), oc.value, ic.value
+        self.cache_points, self.orient_chunk, self.img_chunk = cp.value == 1, oc.value, ic.value
+        self.point_mode = {1: "cached", 2: "slice sets kept", 0: "streamed"}[cp.value]
         self.keep_slices = bool(ks.value)
         self.device = dev
         self.N, self.P2, self.n_img, self.n_orient, self.topk = int(N), int(P2), int(n_img), int(n_orient), int(topk)

@@ -1,7 +1,9 @@
 """The M-TIP driver's whole iteration (slice -> match -> merge -> CG) against
-the oracle's iteration, with point sets kept across iterations and streamed
-per orientation chunk (the mode for orientation sets too large to keep
-sorted; ragged chunks): same matches above the margin, same merged model."""
+the oracle's iteration, with point sets kept across iterations, with only
+their slicing sort kept (image chunks merged at their matched orientations),
+and streamed per orientation chunk (the modes for orientation sets too large
+to keep sorted; ragged chunks): same matches above the margin, same merged
+model."""
 import numpy as np
 import pytest
 
@@ -25,15 +27,15 @@ def c1():
 
 
 @pytest.mark.parametrize("cache,chunk,keep", [(True, None, None), (False, 7, False), (True, 7, True),
-                                              (False, 9, True)])
+                                              (False, 9, True), ("slices", 7, False), ("slices", 9, True)])
 def test_iteration_matches_oracle(c1, cache, chunk, keep):
     import torch
     from paper_2109_05339_gb300 import MTIP
     pb, counts, s, ref = c1
     N, P2, M, n = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0], counts.shape[0]
-    drv = MTIP(N, 1.0, P2, n, M, orient_chunk=chunk, img_chunk=5 if not cache else None,
+    drv = MTIP(N, 1.0, P2, n, M, orient_chunk=chunk, img_chunk=5 if cache is not True else None,
                cache_points=cache, keep_slices=keep)
-    assert drv.cache_points == cache
+    assert drv.point_mode == {True: "cached", False: "streamed", "slices": "slice sets kept"}[cache]
     if keep is not None:
         assert drv.keep_slices == keep
     res, x, lam = drv.iteration(to_dev(pb.A.astype(np.float32)), to_dev(pb.quats.astype(np.float32)),
@@ -57,6 +59,20 @@ def test_iteration_matches_oracle(c1, cache, chunk, keep):
     assert rel_l2(x2.cpu().numpy(), ref["x"]) < 1e-5
     if np.all(res["best"].cpu().numpy() == m["best"]):
         assert rel_l2(x.cpu().numpy(), ref["x"]) < 1e-5
+    drv.close()
+
+
+@pytest.mark.parametrize("budget,mode", [(300_000, "cached"), (100_000, "slice sets kept"),
+                                         (30_000, "streamed")])
+def test_point_mode_follows_the_budget(c1, budget, mode):
+    """Left to choose, the driver keeps full point sets (16 B per orientation x
+    pixel) when they fit the budget, else slice-only sets (4 B), else streams:
+    60 orientations x 256 pixels take 245,760 B full and 61,440 B slice-only."""
+    from paper_2109_05339_gb300 import MTIP
+    pb, counts, s, ref = c1
+    N, P2, M, n = pb.cfg.N, pb.q_lab.shape[0], pb.quats.shape[0], counts.shape[0]
+    drv = MTIP(N, 1.0, P2, n, M, point_budget_bytes=budget)
+    assert drv.point_mode == mode
     drv.close()
 
 
