@@ -495,7 +495,7 @@ def match_compare(args, drv, A, quats, qlab, images, img_scale):
     """The matching stage alone (slices precomputed) on a bounded sample of
     the workload -- the first n images against the first n orientations --
     on the FP32 CUDA-core path, BF16 and FP8 cross terms (each with the FP32
-    re-rank of its top 8). Also: per FP32-path margin bin, the share of images
+    re-rank of its top 8), the median of 10 timed matches after 3 warm-up. Also: per FP32-path margin bin, the share of images
     whose BF16 / FP8 argmin equals the FP32 path's."""
     import torch
     from paper_2109_05339_gb300 import Matcher
@@ -507,19 +507,18 @@ def match_compare(args, drv, A, quats, qlab, images, img_scale):
     res = {}
     for prec in ("fp32", "bf16", "fp8"):
         m = Matcher(n_img, m_or, P2, prec, 8, device=X.device)
-        for _ in range(2):
+        for _ in range(3):
             m.match(X, sl, img_scale)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        reps = 3
+        reps = 10
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
+        for e0, e1 in ev:
+            e0.record()
             best, d1, d2 = m.match(X, sl, img_scale)
-        e1.record()
+            e1.record()
         torch.cuda.synchronize()
         m.status()
-        ms = e0.elapsed_time(e1) / reps
+        ms = float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
         res[prec] = {"ms": ms, "matches_per_s": n_img * m_or / (ms / 1e3), "best": best, "d1": d1, "d2": d2}
         m.close()
     # margins of the FP32 path: (d2 - d1) / (|x|^2 + |y_best|^2), FP64 norms
@@ -537,7 +536,7 @@ def match_compare(args, drv, A, quats, qlab, images, img_scale):
             row[f"{prec}_agree"] = float(agree[sel].mean()) if sel.any() else None
         bins.append(row)
     sample = (f"first {n_img} images x first {m_or} orientations of this workload ({P2} pixels), "
-              "slices precomputed; CUDA events over 3 matches after 2 warm-up")
+              "slices precomputed; median of 10 matches timed by CUDA events, after 3 warm-up")
     out = {f"{p}_match": {k: v for k, v in res[p].items() if k in ("ms", "matches_per_s")} for p in res}
     for p in ("bf16", "fp8"):
         out[f"{p}_match"]["speedup_vs_fp32"] = res["fp32"]["ms"] / res[p]["ms"]
