@@ -495,8 +495,9 @@ def match_compare(args, drv, A, quats, qlab, images, img_scale):
     """The matching stage alone (slices precomputed) on a bounded sample of
     the workload -- the first n images against the first n orientations --
     on the FP32 CUDA-core path, BF16 and FP8 cross terms (each with the FP32
-    re-rank of its top 8), the median of 10 timed matches after 3 warm-up. Also: per FP32-path margin bin, the share of images
-    whose BF16 / FP8 argmin equals the FP32 path's."""
+    re-rank of its top 8), the median of 10 timed matches after 3 warm-up.
+    Also: per FP32-path margin bin, the share of images whose BF16 / FP8
+    argmin equals the FP32 path's."""
     import torch
     from paper_2109_05339_gb300 import Matcher
     n_img = min(args.compare_sample, images.shape[0])
