@@ -435,8 +435,9 @@ int spf_match_orientations(spf_matcher* m, const float* images, int n_img, float
  * spf_mtip_status: the plan's, the matcher's and the driver's error words
  *   (waits for the device). spf_mtip_plan / spf_mtip_matcher: the driver's
  *   plan and matcher (owned by the driver) for the other calls of this header.
- * spf_mtip_info: whether point sets are kept, the chunk sizes in use, and
- *   whether all slices are kept (one deferred re-rank per iteration).
+ * spf_mtip_info: the point-set mode in use (cache_points: 1 full sets kept,
+ *   2 slice-only sets kept, 0 streamed), the chunk sizes in use, and whether
+ *   all slices are kept (one deferred re-rank per iteration).
  * ------------------------------------------------------------------------- */
 #define SPF_IMAGES_F32 0
 #define SPF_IMAGES_U16 1
