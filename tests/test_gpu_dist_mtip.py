@@ -5,7 +5,8 @@ summed over a gloo group, and both solve the same system. The merged model,
 lambda and the matches equal one process merging all images, with the
 images on the device and from host buffers (the library's upload into its
 device slots, then the steps with the reduction between merge and solve,
-three calls so that both slots are used). Both processes share one GPU;
+three calls so that both slots are used), and with slice-only point sets
+(the merge spreading each shard's images at their matched orientations). Both processes share one GPU;
 their kernels never wait on each other (the reduction runs on the host
 through gloo)."""
 import os
@@ -43,7 +44,8 @@ A = torch.from_numpy(d["A"]).to(dev)
 q = torch.from_numpy(d["quats"]).to(dev)
 ql = torch.from_numpy(d["qlab"]).to(dev)
 imgs = torch.from_numpy(d["counts"][lo:hi]).to(dev)
-drv = MTIP(A.shape[0], 1.0, ql.shape[0], hi - lo, q.shape[0], orient_chunk=int(d["chunk"]), cache_points=True,
+drv = MTIP(A.shape[0], 1.0, ql.shape[0], hi - lo, q.shape[0], orient_chunk=int(d["chunk"]),
+           cache_points="slices" if mode == "slices" else True,
            process_group=dist.group.WORLD, host_images="f32" if mode == "host" else None)
 if mode == "host":
     # host buffers: the library's upload, then the steps with the reduction
@@ -65,7 +67,7 @@ dist.destroy_process_group()
 '''
 
 
-@pytest.mark.parametrize("mode", ["device", "host"])
+@pytest.mark.parametrize("mode", ["device", "host", "slices"])
 def test_two_image_shards_equal_one_process(mode):
     import torch
     from paper_2109_05339_gb300 import MTIP
@@ -96,7 +98,8 @@ def test_two_image_shards_equal_one_process(mode):
         parts = [np.load(os.path.join(tmp, f"rank{r}.npz")) for r in range(2)]
     # one process over all images
     dev = torch.device("cuda", 0)
-    drv = MTIP(A.shape[0], 1.0, qlab.shape[0], counts.shape[0], quats.shape[0], orient_chunk=32, cache_points=True)
+    drv = MTIP(A.shape[0], 1.0, qlab.shape[0], counts.shape[0], quats.shape[0], orient_chunk=32,
+               cache_points="slices" if mode == "slices" else True)
     res, x, lam = drv.iteration(torch.from_numpy(A).to(dev), torch.from_numpy(quats).to(dev),
                                 torch.from_numpy(qlab).to(dev), torch.from_numpy(counts.astype(np.float32)).to(dev),
                                 float(np.float32(1.0 / s)), cg_iters=3)
