@@ -66,6 +66,30 @@ def test_argument_errors_without_gpu(lib):
     assert L.spf_plan_destroy(None) == 0 and L.spf_matcher_destroy(None) == 0
 
 
+def test_driver_configuration_errors_without_gpu(lib):
+    """spf_mtip_create checks its configuration before any CUDA call: the
+    point-set mode (-1, 0, 1 or 2) and an orientation chunk whose points reach
+    2^31 (the paper's 1.2e6 orientations of 128 x 128 pixels at once)."""
+    L = lib.lib
+
+    def cfg(**kw):
+        base = dict(N=17, qmax=1.0, eps=1e-6, P2=256, max_images=10, n_orient=100, orient_chunk=0, img_chunk=0,
+                    precision=1, topk=8, cache_points=-1, point_budget_bytes=0, host_image_type=-1, device=0,
+                    keep_slices=-1)
+        base.update(kw)
+        return lib.MtipConfig(**base)
+
+    h = C.c_void_p()
+    assert L.spf_mtip_create(C.byref(h), C.byref(cfg(cache_points=3))) == lib.SPF_ERR_ARG
+    assert b"cache_points" in L.spf_last_error_string()
+    assert L.spf_mtip_create(C.byref(h), C.byref(cfg(cache_points=-2))) == lib.SPF_ERR_ARG
+    big = cfg(P2=16384, n_orient=1_200_000)
+    assert L.spf_mtip_create(C.byref(h), C.byref(big)) == lib.SPF_ERR_ARG
+    assert b"2^31" in L.spf_last_error_string()
+    assert L.spf_mtip_create(C.byref(h), C.byref(cfg(orient_chunk=-1))) == lib.SPF_ERR_ARG
+    assert not h.value
+
+
 def test_binding_raises_typed_errors(lib):
     with pytest.raises(lib.SpfError) as e:
         lib.check(lib.SPF_ERR_ARG)
