@@ -67,9 +67,11 @@ def parse():
                     help="images and orientations of the matching comparison sample")
     ap.add_argument("--tc-schedule", choices=["auto", "contiguous", "grid"], default="auto",
                     help="tile schedule of the tensor-core cross term")
-    ap.add_argument("--stage", choices=["iteration", "match"], default="iteration",
+    ap.add_argument("--stage", choices=["iteration", "match", "phasing", "lcurve"], default="iteration",
                     help="match: time the matching stage alone on synthetic rows of the config's detector "
-                         "(--n-img x --n-orient, default 8000 x 4000), e.g. for a kernel profile")
+                         "(--n-img x --n-orient, default 8000 x 4000), e.g. for a kernel profile; phasing: "
+                         "ER / HIO / shrinkwrap on the config's model grid; lcurve: the lambda sweep of "
+                         "CG solves on --n-img (default 2000) merged slices")
     return ap.parse_args()
 
 
@@ -440,6 +442,107 @@ def run_match_stage(args):
             "cross_term_tflops": 2.0 * n_img * M * cfg.P * cfg.P / (ms / 1e3) / 1e12}
 
 
+def run_phasing_stage(args):
+    """Phasing (Sec. II-D) alone on the config's N^3 model grid: the magnitudes
+    of the config's synthetic model (its Gaussian density), a box support and
+    a seeded start inside it; CUDA events over --steps HIO iterations (beta
+    0.9, positivity, FP64 Fourier errors) after --warmup, then over --steps ER
+    iterations and over one shrinkwrap. Work per iterate: six per-axis direct
+    DFT passes of N^3 outputs, N complex multiply-adds each (8 flop)."""
+    import torch
+    from paper_2109_05339_gb300 import build as _build
+    _build.build()
+    from paper_2109_05339_gb300 import Phaser
+    cfg = synth.CONFIGS[args.config]
+    N, M = cfg.N, (cfg.N - 1) // 2
+    rng = np.random.default_rng(cfg.seed)
+    centres, sigmas, weights = synth.gaussian_density(rng, cfg.n_gauss)
+    _, A = synth.model_grid(N, cfg.qmax, centres, sigmas, weights)
+    dev = torch.device("cuda", 0)
+    d = np.arange(-M, M + 1)
+    z, y, x = np.meshgrid(d, d, d, indexing="ij")
+    half = int(0.4 * M)
+    support = (np.abs(x) <= half) & (np.abs(y) <= half) & (np.abs(z) <= half)
+    rho0 = (rng.uniform(0, 1, (N, N, N)) * support).astype(np.float32)
+    ph = Phaser(N, device=dev)
+    ph.amplitudes_from_model(torch.from_numpy(A.astype(np.float32)).to(dev))
+    ph.set_state(torch.from_numpy(rho0).to(dev), torch.from_numpy(support.astype(np.uint8)).to(dev))
+    errs = torch.zeros(max(args.steps, 1), dtype=torch.float64, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        ph.iterate("hio", 1, beta=0.9, errors=errs[:1])
+    out = {"stage": "phasing", "config": args.config, "N": N, "iterations": args.steps}
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    cmac = 6.0 * N ** 4
+    for method in ("hio", "er"):
+        ms = timed(lambda: ph.iterate(method, args.steps, beta=0.9, errors=errs[:args.steps])) / args.steps
+        out[f"{method}_ms_per_iteration"] = ms
+        out[f"{method}_dft_tflops"] = 8.0 * cmac / (ms / 1e3) / 1e12
+    out["shrinkwrap_ms"] = timed(lambda: ph.shrinkwrap(1.5, 0.1))
+    out["last_fourier_error"] = float(errs[args.steps - 1].item())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * 2 * 2.07e9 / 1e12
+    out["fp32_peak_tflops"] = peak
+    out["peak_source"] = f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (maximum SM clock)"
+    out["hio_frac_of_fp32"] = out["hio_dft_tflops"] / peak
+    ph.close()
+    return out
+
+
+def run_lcurve_stage(args):
+    """The L-curve lambda sweep (Sec. II-C) alone on the config's model grid:
+    the right-hand side and Toeplitz kernel of --n-img (default 2,000) slices
+    of the config's model at random orientations with seeded Gaussian noise
+    (0.3 of the mean |slice|), then 8 lambda values (lambda_rel 1e-5 .. 1e-1
+    times the summed weights), each solved by the config's CG steps from
+    x0 = 0, with the residual and penalty norms and the maximum-curvature
+    corner; CUDA events over --steps sweeps after --warmup."""
+    import torch
+    from paper_2109_05339_gb300 import build as _build
+    _build.build()
+    from paper_2109_05339_gb300 import Plan, lcurve
+    cfg = synth.CONFIGS[args.config]
+    n = args.n_img or 2000
+    pb = synth.make_problem(cfg, n_orient=1, n_img=n)
+    dev = torch.device("cuda", 0)
+    P2 = pb.q_lab.shape[0]
+    plan = Plan(cfg.N, cfg.qmax, cfg.eps, max_points=n * P2, device=dev)
+    A = torch.from_numpy(pb.A.astype(np.float32)).to(dev)
+    iq = torch.from_numpy(pb.img_quats.astype(np.float32)).to(dev)
+    qlab = torch.from_numpy(pb.q_lab.astype(np.float32)).to(dev)
+    images = plan.slice_model(A, iq, qlab)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(cfg.seed)
+    images += 0.3 * images.abs().mean() * torch.randn(images.shape, generator=gen, device=dev)
+    x0 = torch.zeros_like(A)
+    rhs, khat = plan.merge_images(images, iq, qlab)
+    b2 = lcurve.weighted_sumsq(plan, images)
+    lams = np.logspace(-5, -1, 8) * n * P2
+    for _ in range(max(args.warmup, 0)):
+        lcurve.sweep(plan, khat, rhs, x0, lams, cfg.cg_iters, b2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        res = lcurve.sweep(plan, khat, rhs, x0, lams, cfg.cg_iters, b2)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.status()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"stage": "lcurve", "config": args.config, "N": cfg.N, "images": n, "lambdas": len(lams),
+            "cg_iters": cfg.cg_iters, "ms_per_sweep": ms,
+            "ms_per_cg_iteration": ms / (len(lams) * max(cfg.cg_iters, 1)),
+            "corner_lambda_rel": float(res["lams"][res["index"]] / (n * P2))}
+
+
 def cufft_compare(drv, quats, qlab, images, img_scale, best, lam, reps=50):
     """The Toeplitz apply y = crop(IFFT(K^ FFT(pad x))) / PT^3 + lam x on the
     iteration's own kernel (merged again at the last matches) and merged
@@ -736,8 +839,9 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args, rank, world)))
         return
-    if args.stage == "match":
-        print(json.dumps(run_match_stage(args)))
+    if args.stage in ("match", "phasing", "lcurve"):
+        run = {"match": run_match_stage, "phasing": run_phasing_stage, "lcurve": run_lcurve_stage}[args.stage]
+        print(json.dumps(run(args)))
         return
     if world > 1:
         import torch
