@@ -65,6 +65,8 @@ def parse():
                     help="skip timing the matching stage on the FP32 / BF16 / FP8 paths on a sample")
     ap.add_argument("--compare-sample", type=int, default=10_000,
                     help="images and orientations of the matching comparison sample")
+    ap.add_argument("--beamstop", type=float, default=0.0,
+                    help="pixel weights D with a central beam stop of this radius in pixels (0: no mask)")
     ap.add_argument("--tc-schedule", choices=["auto", "contiguous", "grid"], default="auto",
                     help="tile schedule of the tensor-core cross term")
     ap.add_argument("--stage", choices=["iteration", "match", "phasing", "lcurve"], default="iteration",
@@ -254,6 +256,11 @@ def run_ours(args, rank, world):
                process_group=torch.distributed.group.WORLD if world > 1 else None,
                host_images=None if args.no_e2e else "u16")
     drv.matcher.set_schedule(args.tc_schedule)
+    mask = None
+    if args.beamstop > 0:
+        # pixel weights for matching, merging and lambda; the driver keeps the pointer
+        mask = torch.from_numpy(synth.beamstop_mask(cfg.P, args.beamstop)).to(dev)
+        drv.set_mask(mask)
     # noise-free slices at the image orientations, chunk by chunk
     gen = torch.Generator(device=dev)
     gen.manual_seed(cfg.seed * 1000 + rank)
@@ -384,6 +391,7 @@ def run_ours(args, rank, world):
                    "l2": (f"inputs larger than L2 (images {Ni * P2 * 4 / 1e6:.0f} MB, slices "
                           f"{drv.orient_chunk * P2 * 4 / 1e6:.0f} MB per chunk)"),
                    "orient_chunk": drv.orient_chunk,
+                   "beamstop_radius_px": args.beamstop,
                    "point_sets": drv.point_mode,
                    "images_on_device": "16-bit photon counts" if counts16 is not None else "FP32",
                    "device_memory_in_use_gb": round((total_b - free_b) / 1e9, 1)},
