@@ -46,7 +46,7 @@ namespace {
 
 constexpr int kTL = 32;      // lines per tile
 constexpr int kThreads = 256;
-constexpr int kMaxN = 401;   // two N x 33 complex tiles + the table in shared memory
+constexpr int kMaxN = 401;   // two N x 33 complex tiles + two twiddle tables in shared memory
 
 enum ZMode { kZForward = 0, kZModulus = 1, kZBlur = 2, kZAmplitude = 3 };
 enum XMode { kXComplex = 0, kXUpdate = 1, kXReal = 2 };
@@ -75,42 +75,53 @@ struct PassArgs {
 };
 
 // out[b][t] = sum_a in[a][t] exp(sign 2 pi i m_b n_a / N) over the staged
-// tile (row stride kTL + 1), m_b = b - M, n_a = a - M. Thread (lane t, group
-// g) computes b = g, g + 8, ... four at a time.
+// tile (row stride kTL + 1), m_b = b - M, n_a = a - M; tw holds
+// exp(sign 2 pi i k / N), k < N. Thread (line group q = tid % 8, row group
+// r = tid / 8) computes lines t = 4q .. 4q + 3 of rows b = r + 32 k, k <
+// kRows, per round of 32 kRows rows: each twiddle, with its index advanced by
+// addition mod N, serves four lines (20 complex multiply-adds per five
+// twiddles and four inputs). Lines past nlines are zero in the tile.
+constexpr int kRows = 5;
 __device__ __forceinline__ void dft_tile(const float2* __restrict__ in, float2* __restrict__ out,
-                                         const float2* __restrict__ tw, int N, int M, float sign, int t,
-                                         int g, int nlines) {
+                                         const float2* __restrict__ tw, int N, int M, int nlines) {
+  const int q = threadIdx.x & 7, r = threadIdx.x >> 3;
+  const int t0 = 4 * q;
   const int nM = N - M;   // -M mod N
-  for (int b0 = g; b0 < N; b0 += 32) {
-    int e[4], st[4];
-    float2 acc[4];
+  for (int b0 = 0; b0 < N; b0 += 32 * kRows) {
+    int e[kRows], st[kRows];
+    float2 acc[kRows][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int b = b0 + 8 * k;
-      const int m = b - M;
+    for (int k = 0; k < kRows; ++k) {
+      const int m = b0 + r + 32 * k - M;
       const int sm = ((m % N) + N) % N;
       st[k] = sm;
       e[k] = (sm * nM) % N;
-      acc[k] = make_float2(0.f, 0.f);
-    }
-    if (t < nlines) {
-      for (int a = 0; a < N; ++a) {
-        const float2 v = in[a * (kTL + 1) + t];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+      for (int j = 0; j < 4; ++j) acc[k][j] = make_float2(0.f, 0.f);
+    }
+    if (t0 < nlines) {
+      for (int a = 0; a < N; ++a) {
+        const float2* row = in + a * (kTL + 1) + t0;
+        const float2 v[4] = {row[0], row[1], row[2], row[3]};
+#pragma unroll
+        for (int k = 0; k < kRows; ++k) {
           const float2 w = tw[e[k]];
-          const float wy = sign * w.y;
-          acc[k].x = fmaf(v.x, w.x, fmaf(-v.y, wy, acc[k].x));
-          acc[k].y = fmaf(v.x, wy, fmaf(v.y, w.x, acc[k].y));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[k][j].x = fmaf(v[j].x, w.x, fmaf(-v[j].y, w.y, acc[k][j].x));
+            acc[k][j].y = fmaf(v[j].x, w.y, fmaf(v[j].y, w.x, acc[k][j].y));
+          }
           e[k] += st[k];
           e[k] -= e[k] >= N ? N : 0;
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int b = b0 + 8 * k;
-      if (b < N) out[b * (kTL + 1) + t] = acc[k];
+    for (int k = 0; k < kRows; ++k) {
+      const int b = b0 + r + 32 * k;
+      if (b < N)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[b * (kTL + 1) + t0 + j] = acc[k][j];
     }
   }
 }
@@ -168,9 +179,13 @@ __global__ void __launch_bounds__(kThreads) dft_pass_kernel(PassArgs p, float si
   const int N = p.N, M = p.M;
   float2* T = sm;                         // input tile  [N][33]
   float2* O = sm + N * (kTL + 1);         // output tile [N][33]
-  float2* W = O + N * (kTL + 1);          // twiddles
-  for (int i = threadIdx.x; i < N; i += kThreads) W[i] = p.tw[i];
-  const int t = threadIdx.x & 31, g = threadIdx.x >> 5;
+  float2* W = O + N * (kTL + 1);          // twiddles with the pass's sign, then with the other
+  float2* Wc = W + N;
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    const float2 w = p.tw[i];
+    W[i] = make_float2(w.x, sign * w.y);
+    Wc[i] = make_float2(w.x, -sign * w.y);
+  }
   double acc_num = 0.0, acc_den = 0.0;
   float vmax = 0.f;
   const int ntiles = tiles_of<AXIS>(N);
@@ -193,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) dft_pass_kernel(PassArgs p, float si
       T[a * (kTL + 1) + tt] = v;
     }
     __syncthreads();
-    dft_tile(T, O, W, N, M, sign, t, g, tl.nlines);
+    dft_tile(T, O, W, N, M, tl.nlines);
     __syncthreads();
     if constexpr (AXIS == 2 && ZM != kZForward) {
       // pointwise step on the forward transform of the 32 lines, then the
@@ -230,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) dft_pass_kernel(PassArgs p, float si
       }
       if constexpr (ZM != kZAmplitude) {
         __syncthreads();
-        dft_tile(O, T, W, N, M, -sign, t, g, tl.nlines);
+        dft_tile(O, T, Wc, N, M, tl.nlines);
         __syncthreads();
         for (int e = threadIdx.x; e < N * kTL; e += kThreads) {
           int a, tt;
@@ -327,7 +342,7 @@ __global__ void threshold_kernel(const float* __restrict__ blur, int64_t n, cons
     support[i] = blur[i] > cut ? 1 : 0;
 }
 
-size_t pass_smem(int N) { return (size_t)(2 * N * (kTL + 1) + N) * sizeof(float2); }
+size_t pass_smem(int N) { return (size_t)(2 * N * (kTL + 1) + 2 * N) * sizeof(float2); }
 
 template <int AXIS, int ZM, int XM>
 int pass(const spf_phaser* ph, const PassArgs& a, float sign, cudaStream_t s, const char* name) {
