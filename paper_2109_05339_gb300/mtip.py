@@ -80,6 +80,8 @@ class MTIP:
         the image type of iteration_host (allocates its two device slots).
         keep_slices: keep every chunk's slices and re-rank once per iteration
         (True), re-rank per chunk (False), or decide from free memory (None)."""
+        if cache_points not in _POINT_MODES:
+            raise ValueError(f"cache_points must be None, True, False or 'slices', not {cache_points!r}")
         self.group = process_group
         self._n_total = {}
         dev = _dev_index(device)

@@ -37,6 +37,11 @@ def test_counts_binding_rejects_wrong_inputs(pkg):
         pkg.counts_to_f32(torch.zeros(8, dtype=torch.int16))   # host tensor
 
 
+def test_driver_binding_rejects_an_unknown_point_mode(pkg):
+    with pytest.raises(ValueError):
+        pkg.MTIP(17, 1.0, 256, 10, 100, cache_points="kept")
+
+
 def test_lcurve_corner_matches_the_oracle(pkg):
     """The library's L-curve corner (host arithmetic behind the C ABI) picks
     the oracle's maximum-curvature point on uneven lambda grids, and its
